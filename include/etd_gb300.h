@@ -1,0 +1,181 @@
+/*
+ * etd_gb300.h -- C ABI of the GB300 (sm_103a) library for exponential time
+ * differencing (ETD2) of reaction-diffusion systems on embedded-boundary
+ * domains with a level-set free boundary, after Liu & Liu, "Integration
+ * factor combined with level set method for reaction-diffusion systems with
+ * free boundary in high spatial dimensions" (arXiv 2209.15095).
+ *
+ * Problem (Eq. free): u_t = div(beta grad u) + f(u) in Omega(t), u = 0 outside,
+ * boundary normal speed mu |grad u| (Stefan condition, Sec. 4.3), on a node
+ * grid x_i = lo + i h (Sec. 2), Omega = {phi < 0}.
+ *
+ * Conventions for every entry point
+ *   - Grids are row-major (C order), the last axis fastest, 2 <= ndim <= 4,
+ *     the same spacing h on every axis, at most 2^31 - 1 nodes.
+ *   - Field arguments (phi, u, beta, x, y, v0..v2) are DEVICE pointers to
+ *     full-grid FP64 arrays owned by the caller; the library never frees or
+ *     keeps them beyond the call, except beta_field, which must stay valid
+ *     until the next etd_init_domain of that species.
+ *   - The workspace is a caller-owned device buffer of etd_workspace_bytes()
+ *     bytes, 256-byte aligned; the library allocates no device memory.
+ *   - Calls are asynchronous on the stream given to etd_create unless they
+ *     take a host output (stats, etd_read_domain, etd_sync), which
+ *     synchronise that stream.  Errors raised on the device (domain too close
+ *     to the box, Krylov tolerance not met, non-finite values, a device wait
+ *     that timed out) are reported by the next synchronising call.
+ *   - Return value: ETD_OK or a negative etd_status; etd_last_error() gives a
+ *     message.  On an error the output fields are unspecified.
+ */
+#ifndef ETD_GB300_H
+#define ETD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ETD_OK = 0,
+  ETD_ERR_ARG = -1,        /* invalid argument, or call out of order          */
+  ETD_ERR_CUDA = -2,       /* a CUDA runtime call failed                      */
+  ETD_ERR_WORKSPACE = -3,  /* workspace missing, misaligned or too small      */
+  ETD_ERR_KRYLOV = -4,     /* Krylov tolerance not met at the smallest substep */
+  ETD_ERR_DOMAIN = -5,     /* an inside node within 3 nodes of the box edge   */
+  ETD_ERR_NONFINITE = -6,  /* NaN or Inf met in a reduction                   */
+  ETD_ERR_TIMEOUT = -7     /* a bounded device wait (grid barrier) gave up    */
+} etd_status;
+
+/* Node grid (Sec. 2: x_ij = (x_L + (i-1) h, y_L + (j-1) h), generalised to ndim
+ * axes): n[d] nodes on [lo[d], hi[d]]; entries beyond ndim are ignored. */
+typedef struct {
+  int ndim;
+  int n[4];
+  double lo[4];
+  double hi[4];
+} etd_grid;
+
+enum { ETD_REACTION_NONE = 0, ETD_REACTION_LOGISTIC = 1, ETD_REACTION_LOGISTIC_AK = 2, ETD_REACTION_COMPETITION = 3 };
+enum { ETD_PRECISION_FP64 = 0, ETD_PRECISION_MIXED = 1 };
+
+/* Method parameters.
+ *   nspecies    1 or 2
+ *   precision   ETD_PRECISION_FP64: every vector and reduction in FP64.
+ *               ETD_PRECISION_MIXED: Krylov vectors and the stencil in FP32,
+ *               dot products / norms accumulated error-free in FP32 pairs and
+ *               summed across the grid in FP64; H, the small exponential, the
+ *               controller, u, F and the level set stay FP64.
+ *   krylov_tol  relative tolerance of the adaptive Krylov evaluation
+ *   m_max       largest Krylov basis, 5 <= m_max <= 61
+ *   reaction    f(u):  NONE 0;  LOGISTIC u(1-u);  LOGISTIC_AK rp[0] u (1 - u/rp[1]);
+ *               COMPETITION (species 0, 1) = (u(1-u-rp[0] v), rp[2] v (1-v-rp[1] u))
+ *   mu[s]       Stefan coefficient of species s (boundary speed mu |grad u|)
+ *   beta[s]     constant diffusion coefficient of species s, used when no
+ *               beta field is given to etd_init_domain */
+typedef struct {
+  int nspecies;
+  int precision;
+  double krylov_tol;
+  int m_max;
+  int reaction;
+  double rp[4];
+  double mu[2];
+  double beta[2];
+} etd_params;
+
+#define ETD_TRACE_MAX 64
+
+/* Per-call statistics of the adaptive Krylov evaluation (decision trace). */
+typedef struct {
+  int ncomp[2];                       /* computational points per species    */
+  int substeps[2];                    /* accepted substeps                   */
+  int rejections[2];                  /* rejected step sizes                 */
+  int krylov_iters[2];                /* basis vectors built, all substeps   */
+  int trace_len[2];
+  int trace_m[2][ETD_TRACE_MAX];      /* basis size of each accepted substep */
+  double trace_tau[2][ETD_TRACE_MAX]; /* step of each accepted substep       */
+} etd_step_stats;
+
+typedef struct etd_ctx etd_ctx;
+
+/* Bytes of device workspace needed for this grid and parameter set. */
+size_t etd_workspace_bytes(const etd_grid* grid, const etd_params* params);
+
+/* Create a context on the current device.  `workspace` (device, >= the size
+ * above, 256-byte aligned) is zeroed on `stream` (a cudaStream_t, NULL for
+ * the legacy default stream) and carved into the library's buffers; the
+ * caller keeps ownership and must keep it alive until etd_destroy. */
+etd_status etd_create(const etd_grid* grid, const etd_params* params, void* workspace, size_t workspace_bytes,
+                      void* stream, etd_ctx** out);
+
+/* Release the host-side context (the workspace is the caller's). */
+void etd_destroy(etd_ctx* ctx);
+
+/* Domain set-up for `species` from the level set phi (Sec. 2): classifies
+ * nodes (inside phi < 0; ghost: inside with an axis neighbour outside;
+ * computational: inside with all 2N neighbours inside), lists the
+ * computational points in grid order and packs per-row metadata: the
+ * diagonal D_p = sum_faces beta_f - sum_ghost faces beta_f w_f, with w_f the
+ * ghost weight of case 2 (Eq. DirichletLineByLine) or case 3 (Eq. rbf_ubp),
+ * clamped to [0, 1].  beta_field: NULL for the constant params->beta[species],
+ * else a full-grid node field (face value = mean of the two nodes). */
+etd_status etd_init_domain(etd_ctx* ctx, int species, const double* phi, const double* beta_field);
+
+/* One ETD2 step (Sec. 3.1) of every species on the current domains:
+ *   U_{n+1} = phi_0(dt C) U_n + dt phi_1(dt C) F_n + dt phi_2(dt C)(F_n - F_{n-1}),
+ * the phi-combination (Eq. 3.9) evaluated by adaptive Krylov time-stepping of
+ * the ODE of Eq. 3.10.  u[s] (device, full grid, in/out): read at the
+ * computational points of species s; on return it holds U_{n+1} there and 0 at
+ * every other node.  F_{n-1} is kept by the context; where a point was not
+ * computational at the previous step (and at the first step) F_{n-1} = F_n.
+ * stats: NULL for an asynchronous call, else filled after synchronising. */
+etd_status etd_step(etd_ctx* ctx, double dt, double* const* u, etd_step_stats* stats);
+
+/* The phi-combination alone (Sec. 3.3, Eq. 3.9 with p = 2):
+ *   y = phi_0(dt C) v0 + phi_1(dt C) v1 + phi_2(dt C) v2
+ * on the computational points of `species`; v0, v1, v2, y are device full-grid
+ * FP64 arrays; y is 0 off the computational set. */
+etd_status etd_phi_combination(etd_ctx* ctx, int species, double dt, const double* v0, const double* v1,
+                               const double* v2, double* y, etd_step_stats* stats);
+
+/* y = dt C x on the computational points (Sec. 2 operator, matrix-free);
+ * y is written at computational points only.  FP64. */
+etd_status etd_apply_operator(etd_ctx* ctx, int species, double dt, const double* x, double* y);
+
+/* Level-set step of the free-boundary algorithm (Sec. 4.3, Steps 1-2) for
+ * `species`, on the domain last given to etd_init_domain:
+ *   1. extend u from the computational points into the tube around the
+ *      interface by quadratic extrapolation along the normal (Aslam 2004);
+ *   2. Stefan speed V = mu |grad u| at the interface, carried to the tube
+ *      along the normal (closest-point extension);
+ *   3. advect phi_t + V |grad phi| = 0 (Godunov HJ-WENO5, TVD-RK3, CFL substeps);
+ *   4. if do_reinit, reinitialise phi_t + S(phi_0)(|grad phi| - 1) = 0;
+ *   5. clamp phi to [-6h, 6h] (local level set: only the tube |phi| < 6h,
+ *      grown by one node, is updated).
+ * phi (in/out) and u (in/out, extended on return) are device full-grid FP64. */
+etd_status levelset_advance(etd_ctx* ctx, int species, double* phi, double* u, double dt, int do_reinit);
+
+/* Clamp phi to [-6h, 6h] and, if do_reinit, reinitialise it (as step 4 above). */
+etd_status levelset_prepare(etd_ctx* ctx, double* phi, int do_reinit);
+
+/* Wait for the stream and report any error raised on the device since the
+ * last report. */
+etd_status etd_sync(etd_ctx* ctx);
+
+/* Synchronise and copy domain data of `species` to host memory: the number
+ * of computational points and of clamped ghost weights, the Gershgorin bound
+ * max_p sum_q |C_pq|, and optionally (non-NULL) the node kinds (grid size
+ * bytes: 0 outside, 1 ghost, 2 computational), the computational points' grid
+ * indices and their diagonals D_p (cap entries each). */
+etd_status etd_read_domain(etd_ctx* ctx, int species, int* ncomp, int* nclamp, double* gersh, uint8_t* kind,
+                           int* idx, double* diag, int cap);
+
+/* Message for the last error of this context (static storage of the ctx). */
+const char* etd_last_error(const etd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ETD_GB300_H */

@@ -1,0 +1,460 @@
+// C ABI: context, workspace carving, argument checks and launches.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "etd_gb300.h"
+#include "kernels.cuh"
+#include "levelset.cuh"
+
+using namespace etd;
+
+struct SpeciesBufs {
+  uint8_t* kind = nullptr;
+  int* idx = nullptr;
+  int* ncomp = nullptr;
+  double* diag = nullptr;
+  float* diagf = nullptr;
+  double* Fprev = nullptr;
+  uint8_t* fvalid = nullptr;
+  void* V = nullptr;
+  void* Yg = nullptr;
+  void* W1g = nullptr;
+  double* Yc = nullptr;
+  void* V1c = nullptr;
+  void* V2c = nullptr;
+  void* Zc = nullptr;
+  const double* beta_field = nullptr;
+  bool ready = false;
+};
+
+struct etd_ctx {
+  etd_grid grid;
+  etd_params par;
+  GridDev g;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  DevStatus* st = nullptr;
+  StatsDev* stats = nullptr;
+  double* part = nullptr;
+  int* tile_count = nullptr;
+  SpeciesBufs sp[2];
+  LevelsetBufs ls;
+  int nblocks = 0;
+  bool fp32 = false;
+  std::string err;
+};
+
+namespace {
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+bool check_grid(const etd_grid* grid, GridDev& g, std::string& why) {
+  if (!grid || grid->ndim < 2 || grid->ndim > 4) {
+    why = "ndim must be 2, 3 or 4";
+    return false;
+  }
+  memset(&g, 0, sizeof(g));
+  g.ndim = grid->ndim;
+  long long size = 1;
+  for (int d = 0; d < grid->ndim; ++d) {
+    if (grid->n[d] < 8) {
+      why = "each axis needs at least 8 nodes";
+      return false;
+    }
+    g.n[d] = grid->n[d];
+    size *= grid->n[d];
+  }
+  if (size > 2147483647LL) {
+    why = "grid larger than 2^31 - 1 nodes";
+    return false;
+  }
+  g.size = size;
+  long long s = 1;
+  for (int d = grid->ndim - 1; d >= 0; --d) {
+    g.stride[d] = s;
+    s *= grid->n[d];
+  }
+  double h0 = (grid->hi[0] - grid->lo[0]) / (grid->n[0] - 1);
+  if (!(h0 > 0.0)) {
+    why = "hi must exceed lo";
+    return false;
+  }
+  for (int d = 0; d < grid->ndim; ++d) {
+    double hd = (grid->hi[d] - grid->lo[d]) / (grid->n[d] - 1);
+    if (fabs(hd - h0) > 1e-12 * h0) {
+      why = "grid spacing must be the same on every axis";
+      return false;
+    }
+    g.lo[d] = grid->lo[d];
+  }
+  g.h = h0;
+  return true;
+}
+
+bool check_params(const etd_params* p, std::string& why) {
+  if (!p) {
+    why = "params is NULL";
+    return false;
+  }
+  if (p->nspecies < 1 || p->nspecies > 2) {
+    why = "nspecies must be 1 or 2";
+    return false;
+  }
+  if (p->precision != ETD_PRECISION_FP64 && p->precision != ETD_PRECISION_MIXED) {
+    why = "unknown precision";
+    return false;
+  }
+  if (p->m_max < 5 || p->m_max > MAX_M) {
+    why = "m_max must be in [5, 61]";
+    return false;
+  }
+  if (!(p->krylov_tol > 0.0)) {
+    why = "krylov_tol must be positive";
+    return false;
+  }
+  if (p->reaction < 0 || p->reaction > 3 || (p->reaction == ETD_REACTION_COMPETITION && p->nspecies != 2)) {
+    why = "unknown reaction, or competition without two species";
+    return false;
+  }
+  for (int s = 0; s < p->nspecies; ++s) {
+    if (!(p->beta[s] > 0.0)) {
+      why = "beta must be positive";
+      return false;
+    }
+  }
+  return true;
+}
+
+size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
+  Carver cv{base};
+  const size_t G = (size_t)g.size;
+  const bool f32 = p.precision == ETD_PRECISION_MIXED;
+  const size_t s = f32 ? 4 : 8;
+  DevStatus* st = cv.take<DevStatus>(1);
+  StatsDev* stats = cv.take<StatsDev>(1);
+  double* part = cv.take<double>(8 * MAX_BLOCKS);
+  int* tiles = cv.take<int>(scan_tiles(g.size) + 1);
+  if (c) {
+    c->st = st;
+    c->stats = stats;
+    c->part = part;
+    c->tile_count = tiles;
+  }
+  for (int sp = 0; sp < p.nspecies; ++sp) {
+    SpeciesBufs b;
+    b.kind = cv.take<uint8_t>(G);
+    b.idx = cv.take<int>(G);
+    b.ncomp = cv.take<int>(1);
+    b.diag = cv.take<double>(G);
+    b.diagf = f32 ? cv.take<float>(G) : nullptr;
+    b.Fprev = cv.take<double>(G);
+    b.fvalid = cv.take<uint8_t>(G);
+    b.V = cv.take<char>(s * G * (p.m_max + 1));
+    b.Yg = cv.take<char>(s * G);
+    b.W1g = cv.take<char>(s * G);
+    b.Yc = cv.take<double>(G);
+    b.V1c = cv.take<char>(s * G);
+    b.V2c = cv.take<char>(s * G);
+    b.Zc = cv.take<char>(s * G);
+    if (c) c->sp[sp] = b;
+  }
+  LevelsetBufs lb = levelset_carve(g, [&](size_t bytes) { return cv.take<char>(bytes); });
+  if (c) c->ls = lb;
+  cv.off = (cv.off + 255) & ~size_t(255);
+  return cv.off;
+}
+
+etd_status fail(etd_ctx* c, etd_status code, const std::string& why) {
+  if (c) c->err = why;
+  return code;
+}
+
+etd_status cuda_fail(etd_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, ETD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+etd_status read_status(etd_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
+  int err = 0;
+  e = cudaMemcpy(&err, &c->st->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+  if (err == 0) return ETD_OK;
+  int zero = 0;
+  cudaMemcpy(&c->st->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  if (err & ERRF_TIMEOUT) return fail(c, ETD_ERR_TIMEOUT, "a bounded device wait timed out");
+  if (err & ERRF_NONFINITE) return fail(c, ETD_ERR_NONFINITE, "non-finite value in a reduction");
+  if (err & ERRF_DOMAIN) return fail(c, ETD_ERR_DOMAIN, "an inside node lies within 3 nodes of the box edge");
+  if (err & ERRF_KRYLOV) return fail(c, ETD_ERR_KRYLOV, "Krylov tolerance not met at the smallest substep");
+  return fail(c, ETD_ERR_ARG, "a device list or trace outgrew its buffer");
+}
+
+template <typename T>
+SpeciesDev<T> species_dev(etd_ctx* c, int s, double* u) {
+  SpeciesBufs& b = c->sp[s];
+  SpeciesDev<T> d;
+  d.idx = b.idx;
+  d.ncomp = b.ncomp;
+  d.diag = b.diag;
+  d.diagf = b.diagf;
+  d.kind = b.kind;
+  d.beta_field = b.beta_field;
+  d.beta_c = c->par.beta[s];
+  d.gersh = &c->st->gersh[s];
+  d.u = u;
+  d.Fprev = b.Fprev;
+  d.fvalid = b.fvalid;
+  d.V = (T*)b.V;
+  d.Yg = (T*)b.Yg;
+  d.W1g = (T*)b.W1g;
+  d.Yc = b.Yc;
+  d.V1c = (T*)b.V1c;
+  d.V2c = (T*)b.V2c;
+  d.Zc = (T*)b.Zc;
+  return d;
+}
+
+template <typename T>
+etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int species, const double* given[3],
+                     etd_step_stats* stats) {
+  PhipmArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  a.g = c->g;
+  a.mode = mode;
+  a.m_max = c->par.m_max;
+  a.dt = dt;
+  a.cfac = dt / (c->g.h * c->g.h);
+  a.tol = c->par.krylov_tol;
+  a.reaction = c->par.reaction;
+  for (int i = 0; i < 4; ++i) a.rp[i] = c->par.rp[i];
+  if (mode == MODE_ETD2) {
+    a.nspecies = c->par.nspecies;
+    for (int s = 0; s < a.nspecies; ++s) a.sp[s] = species_dev<T>(c, s, u[s]);
+  } else {
+    a.nspecies = 1;
+    a.sp[0] = species_dev<T>(c, species, u[0]);
+    for (int i = 0; i < 3; ++i) a.given[i] = given[i];
+  }
+  a.part = c->part;
+  a.st = c->st;
+  a.stats = c->stats;
+  cudaError_t e = cudaMemsetAsync(c->stats, 0, sizeof(StatsDev), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stats reset");
+  e = launch_phipm<T>(a, c->nblocks, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "phipm launch");
+  if (!stats) return ETD_OK;
+  etd_status rs = read_status(c);
+  StatsDev h;
+  e = cudaMemcpy(&h, c->stats, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stats read");
+  memset(stats, 0, sizeof(*stats));
+  for (int s = 0; s < a.nspecies; ++s) {
+    const int so = mode == MODE_ETD2 ? s : species;
+    int nc = 0;
+    cudaMemcpy(&nc, c->sp[so].ncomp, sizeof(int), cudaMemcpyDeviceToHost);
+    stats->ncomp[s] = nc;
+    stats->substeps[s] = h.substeps[s];
+    stats->rejections[s] = h.rejections[s];
+    stats->krylov_iters[s] = h.iters[s];
+    stats->trace_len[s] = h.trace_len[s];
+    for (int i = 0; i < ETD_TRACE_MAX && i < TRACE_MAX; ++i) {
+      stats->trace_m[s][i] = h.trace_m[s][i];
+      stats->trace_tau[s][i] = h.trace_tau[s][i];
+    }
+  }
+  return rs;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t etd_workspace_bytes(const etd_grid* grid, const etd_params* params) {
+  GridDev g;
+  std::string why;
+  if (!check_grid(grid, g, why) || !check_params(params, why)) return 0;
+  return carve(g, *params, nullptr, nullptr);
+}
+
+etd_status etd_create(const etd_grid* grid, const etd_params* params, void* workspace, size_t workspace_bytes,
+                      void* stream, etd_ctx** out) {
+  if (!out) return ETD_ERR_ARG;
+  *out = nullptr;
+  etd_ctx* c = new etd_ctx();
+  std::string why;
+  if (!check_grid(grid, c->g, why) || !check_params(params, why)) {
+    delete c;
+    return ETD_ERR_ARG;
+  }
+  c->grid = *grid;
+  c->par = *params;
+  c->stream = (cudaStream_t)stream;
+  c->fp32 = params->precision == ETD_PRECISION_MIXED;
+  size_t need = carve(c->g, c->par, nullptr, nullptr);
+  if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255u)) {
+    delete c;
+    return ETD_ERR_WORKSPACE;
+  }
+  c->ws = (char*)workspace;
+  c->ws_bytes = workspace_bytes;
+  carve(c->g, c->par, c->ws, c);
+  cudaError_t e = cudaMemsetAsync(c->ws, 0, need, c->stream);
+  if (e != cudaSuccess) {
+    delete c;
+    return ETD_ERR_CUDA;
+  }
+  c->nblocks = phipm_max_blocks(c->g.ndim, c->fp32);
+  if (c->nblocks <= 0 || c->nblocks > MAX_BLOCKS) {
+    delete c;
+    return ETD_ERR_CUDA;
+  }
+  *out = c;
+  return ETD_OK;
+}
+
+void etd_destroy(etd_ctx* ctx) { delete ctx; }
+
+const char* etd_last_error(const etd_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+etd_status etd_init_domain(etd_ctx* c, int species, const double* phi, const double* beta_field) {
+  if (!c) return ETD_ERR_ARG;
+  if (species < 0 || species >= c->par.nspecies || !phi) return fail(c, ETD_ERR_ARG, "bad species or phi");
+  SpeciesBufs& b = c->sp[species];
+  b.beta_field = beta_field;
+  ClassifyArgs ca;
+  memset(&ca, 0, sizeof(ca));
+  ca.g = c->g;
+  ca.phi = phi;
+  ca.kind = b.kind;
+  ca.tile_count = c->tile_count;
+  ca.st = c->st;
+  ca.nzero = 2;
+  if (c->fp32) {
+    ca.zero_f32[0] = (float*)b.Yg;
+    ca.zero_f32[1] = (float*)b.W1g;
+    ca.basis_f32 = (float*)b.V;
+  } else {
+    ca.zero_f64[0] = (double*)b.Yg;
+    ca.zero_f64[1] = (double*)b.W1g;
+    ca.basis_f64 = (double*)b.V;
+  }
+  ca.nbasis = c->par.m_max + 1;
+  MetaArgs ma;
+  memset(&ma, 0, sizeof(ma));
+  ma.g = c->g;
+  ma.phi = phi;
+  ma.kind = b.kind;
+  ma.idx = b.idx;
+  ma.ncomp = b.ncomp;
+  ma.beta_field = beta_field;
+  ma.beta_c = c->par.beta[species];
+  ma.diag = b.diag;
+  ma.diagf = b.diagf;
+  ma.gersh = &c->st->gersh[species];
+  ma.st = c->st;
+  cudaError_t e = launch_init_domain(ca, ma, c->tile_count, b.ncomp, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "init_domain launch");
+  b.ready = true;
+  return ETD_OK;
+}
+
+etd_status etd_step(etd_ctx* c, double dt, double* const* u, etd_step_stats* stats) {
+  if (!c) return ETD_ERR_ARG;
+  if (!u || !(dt > 0.0)) return fail(c, ETD_ERR_ARG, "u missing or dt <= 0");
+  for (int s = 0; s < c->par.nspecies; ++s) {
+    if (!u[s]) return fail(c, ETD_ERR_ARG, "u[s] is NULL");
+    if (!c->sp[s].ready) return fail(c, ETD_ERR_ARG, "etd_init_domain not called for every species");
+  }
+  return c->fp32 ? run_phipm<float>(c, MODE_ETD2, dt, u, 0, nullptr, stats)
+                 : run_phipm<double>(c, MODE_ETD2, dt, u, 0, nullptr, stats);
+}
+
+etd_status etd_phi_combination(etd_ctx* c, int species, double dt, const double* v0, const double* v1,
+                               const double* v2, double* y, etd_step_stats* stats) {
+  if (!c) return ETD_ERR_ARG;
+  if (species < 0 || species >= c->par.nspecies || !v0 || !v1 || !v2 || !y || !(dt > 0.0))
+    return fail(c, ETD_ERR_ARG, "bad arguments");
+  if (!c->sp[species].ready) return fail(c, ETD_ERR_ARG, "etd_init_domain not called");
+  const double* given[3] = {v0, v1, v2};
+  double* out[1] = {y};
+  return c->fp32 ? run_phipm<float>(c, MODE_GIVEN, dt, out, species, given, stats)
+                 : run_phipm<double>(c, MODE_GIVEN, dt, out, species, given, stats);
+}
+
+etd_status etd_apply_operator(etd_ctx* c, int species, double dt, const double* x, double* y) {
+  if (!c) return ETD_ERR_ARG;
+  if (species < 0 || species >= c->par.nspecies || !x || !y) return fail(c, ETD_ERR_ARG, "bad arguments");
+  if (!c->sp[species].ready) return fail(c, ETD_ERR_ARG, "etd_init_domain not called");
+  ApplyArgs a;
+  a.g = c->g;
+  a.idx = c->sp[species].idx;
+  a.ncomp = c->sp[species].ncomp;
+  a.diag = c->sp[species].diag;
+  a.beta_field = c->sp[species].beta_field;
+  a.beta_c = c->par.beta[species];
+  a.cfac = dt / (c->g.h * c->g.h);
+  a.x = x;
+  a.y = y;
+  cudaError_t e = launch_apply(a, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "apply launch");
+  return ETD_OK;
+}
+
+etd_status etd_sync(etd_ctx* c) {
+  if (!c) return ETD_ERR_ARG;
+  return read_status(c);
+}
+
+etd_status etd_read_domain(etd_ctx* c, int species, int* ncomp, int* nclamp, double* gersh, uint8_t* kind, int* idx,
+                           double* diag, int cap) {
+  if (!c) return ETD_ERR_ARG;
+  if (species < 0 || species >= c->par.nspecies) return fail(c, ETD_ERR_ARG, "bad species");
+  etd_status rs = read_status(c);
+  SpeciesBufs& b = c->sp[species];
+  int nc = 0;
+  cudaError_t e = cudaMemcpy(&nc, b.ncomp, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "read ncomp");
+  if (ncomp) *ncomp = nc;
+  if (nclamp) cudaMemcpy(nclamp, &c->st->nclamp, sizeof(int), cudaMemcpyDeviceToHost);
+  if (gersh) cudaMemcpy(gersh, &c->st->gersh[species], sizeof(double), cudaMemcpyDeviceToHost);
+  if (kind) cudaMemcpy(kind, b.kind, (size_t)c->g.size, cudaMemcpyDeviceToHost);
+  const int n = nc < cap ? nc : cap;
+  if (idx && n > 0) cudaMemcpy(idx, b.idx, sizeof(int) * n, cudaMemcpyDeviceToHost);
+  if (diag && n > 0) cudaMemcpy(diag, b.diag, sizeof(double) * n, cudaMemcpyDeviceToHost);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "read domain");
+  return rs;
+}
+
+etd_status levelset_advance(etd_ctx* c, int species, double* phi, double* u, double dt, int do_reinit) {
+  if (!c) return ETD_ERR_ARG;
+  if (species < 0 || species >= c->par.nspecies || !phi || !u || !(dt > 0.0))
+    return fail(c, ETD_ERR_ARG, "bad arguments");
+  if (!c->sp[species].ready) return fail(c, ETD_ERR_ARG, "etd_init_domain not called");
+  cudaError_t e = launch_levelset_advance(c->g, c->ls, c->st, c->sp[species].kind, phi, u, dt, c->par.mu[species],
+                                          do_reinit != 0, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "levelset launch");
+  return ETD_OK;
+}
+
+etd_status levelset_prepare(etd_ctx* c, double* phi, int do_reinit) {
+  if (!c) return ETD_ERR_ARG;
+  if (!phi) return fail(c, ETD_ERR_ARG, "phi is NULL");
+  cudaError_t e = launch_levelset_prepare(c->g, c->ls, c->st, phi, do_reinit != 0, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "levelset launch");
+  return ETD_OK;
+}
+
+}  // extern "C"

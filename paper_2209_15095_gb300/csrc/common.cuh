@@ -1,0 +1,186 @@
+// Shared device utilities: grid descriptor, node kinds, status flags, the
+// bounded grid barrier, deterministic block/grid reductions, FP32
+// error-free accumulation.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace etd {
+
+constexpr int MAXD = 4;
+constexpr int MAX_M = 61;           // largest Krylov basis (m + p + 1 <= 64)
+constexpr int MAX_BLOCKS = 1024;    // partial-sum slots per reduction quantity
+
+struct GridDev {
+  int ndim;
+  int n[MAXD];
+  long long stride[MAXD];
+  long long size;
+  double lo[MAXD];
+  double h;
+};
+
+// node class in the low two bits of a kind byte
+enum : uint8_t { K_OUT = 0, K_GHOST = 1, K_COMP = 2 };
+
+// device status word bits (DevStatus::err)
+enum : int {
+  ERRF_DOMAIN = 1,     // an inside node within 3 nodes of the box edge
+  ERRF_TIMEOUT = 2,    // a bounded device wait gave up
+  ERRF_KRYLOV = 4,     // tolerance not met at tau_min
+  ERRF_NONFINITE = 8,  // NaN / Inf in a reduction
+  ERRF_CAPACITY = 16,  // a list or trace outgrew its buffer
+};
+
+struct DevStatus {
+  int err;
+  int nclamp;           // ghost weights clamped to [0, 1]
+  int timeout_site;
+  int pad;
+  double gersh[2];      // Gershgorin bound of C per species (max row sum of |C|)
+  unsigned int barrier; // grid-barrier arrival counter (reset before each cooperative launch)
+  unsigned int pad2;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for a cooperative launch: a monotonically increasing
+// arrival counter (reset to 0 before the launch).  Barrier number `k`
+// (1-based, identical in every CTA) completes when the counter reaches
+// k * gridDim.x.  Every wait is bounded (~1 s of wall time); on timeout the
+// status word gets ERRF_TIMEOUT and the call returns false, after which the
+// kernel must return.
+constexpr unsigned long long BARRIER_LIMIT_NS = 1000000000ull;
+
+__device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned& k, int site) {
+  __shared__ int s_ok;
+  ++k;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    red_release_add_u32(&st->barrier, 1u);
+    const unsigned target = k * gridDim.x;
+    unsigned long long t0 = 0;
+    unsigned polls = 0;
+    while (ld_acquire_u32(&st->barrier) < target) {
+      if (((++polls) & 255u) == 0u) {
+        unsigned long long now = global_ns();
+        if (t0 == 0) t0 = now;
+        else if (now - t0 > BARRIER_LIMIT_NS) {
+          atomicOr(&st->err, ERRF_TIMEOUT);
+          atomicExch(&st->timeout_site, site);
+          ok = 0;
+          break;
+        }
+      }
+      if (*((volatile int*)&st->err) & ERRF_TIMEOUT) { ok = 0; break; }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of NQ per-thread values over the block; thread 0 writes the block's
+// totals to part[q * MAX_BLOCKS + blockIdx.x].  Fixed order: warp tree, then
+// warps in index order.
+template <int NQ>
+__device__ __forceinline__ void block_partials(const double (&v)[NQ], double* part) {
+  __shared__ double s_red[NQ][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double x = warp_sum(v[q]);
+    if (lane == 0) s_red[q][wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double x = lane < nw ? s_red[q][lane] : 0.0;
+      x = warp_sum(x);
+      if (lane == 0) part[q * MAX_BLOCKS + blockIdx.x] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// After a grid barrier: every CTA sums the per-block partials in the same
+// fixed order (lane-strided, then a warp tree), so every CTA obtains the same
+// bits.  Result broadcast to the whole block.
+template <int NQ>
+__device__ __forceinline__ void grid_totals(const double* part, double (&out)[NQ]) {
+  __shared__ double s_tot[NQ];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double x = 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) x += __ldcg(part + q * MAX_BLOCKS + b);
+      x = warp_sum(x);
+      if (lane == 0) s_tot[q] = x;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) out[q] = s_tot[q];
+  __syncthreads();
+}
+
+// FP32 error-free accumulation of products (TwoProduct via fma + TwoSum,
+// Ogita, Rump & Oishi 2005): s + c carries the sum to about twice single
+// precision.  Intrinsics keep the compiler from contracting or reassociating.
+struct Dot2f {
+  float s, c;
+  __device__ __forceinline__ Dot2f() : s(0.f), c(0.f) {}
+  __device__ __forceinline__ void add(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float pe = __fmaf_rn(a, b, -p);
+    float t = __fadd_rn(s, p);
+    float z = __fsub_rn(t, s);
+    float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, pe));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Acc<float> {
+  Dot2f d;
+  __device__ __forceinline__ void add(float a, float b) { d.add(a, b); }
+  __device__ __forceinline__ double value() const { return d.value(); }
+};
+
+}  // namespace etd

@@ -1,0 +1,603 @@
+// Adaptive Krylov evaluation of y = phi_0(A) v_0 + phi_1(A) v_1 + phi_2(A) v_2
+// (Sec. 3.3, Eq. 3.9) by time-stepping the equivalent ODE of Eq. 3.10
+// (y' = A y + v_1 + t v_2, y(0) = v_0, y = y(1)), A = dt C with C the
+// matrix-free embedded-boundary operator of Sec. 2, and the ETD2 step of
+// Sec. 3.1 built on it.
+//
+// One persistent cooperative kernel runs the whole call: the ETD2 right-hand
+// vectors, every substep (w_1, w_2 matvecs, the IOM2/Lanczos basis with fused
+// dot products, the small augmented-matrix exponential, the error estimate
+// and the step-size controller) and the final combination, with bounded grid
+// barriers between dependent sweeps.  Every CTA sums the per-CTA partials in
+// the same order and runs the same controller on the same bits, so all
+// decisions are identical across CTAs without a broadcast.
+//
+// Substep from t_k with step tau (p = 2):
+//   w_1 = A y + v_1 + t_k v_2,  w_2 = A w_1 + v_2,  beta = |w_2|
+//   IOM2: z = A v_j, h_jj = <z, v_j>, h_{j-1,j} = <z, v_{j-1}>,
+//         z -= h_jj v_j + h_{j-1,j} v_{j-1}, h_{j+1,j} = |z|
+//   check every 5 vectors and at m_max:
+//     err = tau^3 beta h_{m+1,m} |e_m^T phi_3(tau H_m) e_1| <= tol tau |y|
+//   on failure at m_max shrink tau <- tau max(0.2, 0.9 (tol tau |y| / err)^(1/(m+1)))
+//   y <- y + tau w_1 + tau^2 beta V_m phi_2(tau H_m) e_1
+//   tau_next = min(1 - t, tau min(2, 0.9 (tol tau |y| / err)^(1/(m+1))))
+// Basis vectors are stored unnormalised (v_j = V_j / |V_j|) so that the
+// normalisation costs no extra sweep.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace etd {
+
+constexpr int PH_NT = 512;
+constexpr int CHECK_EVERY = 5;
+constexpr double TAU_MIN = 1e-6;
+constexpr double BREAKDOWN_REL = 1e-12;
+constexpr float TAYLOR_THETA = 4.0f;
+constexpr int MAX_SUBSTEPS = 20000;  // bounded work per call
+
+__constant__ double c_inv_fact[64];  // 1/k!
+
+struct Ctl {
+  double alpha[MAX_M + 2];
+  double up[MAX_M + 2];
+  double low[MAX_M + 2];
+  double scale[MAX_M + 2];  // 1 / |V_j|
+  double coef[MAX_M + 2];   // tau^2 beta phi_2(tau H) e_1, times scale
+  double yexp[64];
+  // controller scalars
+  double t, tau, ynorm, beta, err, hn;
+  int m, accepted, breakdown, last, abort, nrej;
+};
+
+// ---------------------------------------------------------------------------
+// small exponential: x = exp(K) e_{M-1} for the augmented matrix
+//   K = [[tau H_m, e_1, 0], [0, 0, I_p], [0, 0, 0]],  M = m + p + 1 <= 64,
+// by Taylor series with scaling (K/s, s steps), unnormalised powers
+// accumulated with 1/k!.  Warp-cooperative: lane owns rows lane and lane+32.
+// On return c.yexp[0..m-1] = phi_{p+1}(tau H_m) e_1.
+__device__ void small_expm_warp(Ctl& c, int m, int p, double tau) {
+  const int lane = threadIdx.x & 31;
+  const int M = m + p + 1;
+  float nb = 0.f;
+  for (int r = lane; r < m; r += 32) {
+    float v = fabsf((float)c.alpha[r]) + (r > 0 ? fabsf((float)c.low[r - 1]) : 0.f) +
+              (r + 1 < m ? fabsf((float)c.up[r + 1]) : 0.f);
+    nb = fmaxf(nb, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) nb = fmaxf(nb, __shfl_xor_sync(0xffffffffu, nb, o));
+  nb = nb * (float)tau + 1.0f;
+  const int s = max(1, (int)ceilf(nb / TAYLOR_THETA));
+  const float th = nb / (float)s;
+  int deg = 1;
+  {
+    float term = th;
+    while (deg < 60 && term > 1e-18f) {
+      ++deg;
+      term *= th / (float)deg;
+    }
+  }
+  const double inv_s = 1.0 / (double)s;
+  double A[2], B[2], C[2], x[2];
+  for (int h = 0; h < 2; ++h) {
+    const int r = lane + 32 * h;
+    if (r < m) {
+      A[h] = tau * c.alpha[r] * inv_s;
+      B[h] = r > 0 ? tau * c.low[r - 1] * inv_s : 0.0;
+      C[h] = r + 1 < m ? tau * c.up[r + 1] * inv_s : 0.0;
+    } else if (r < M - 1) {
+      A[h] = 0.0;
+      B[h] = 0.0;
+      C[h] = inv_s;
+    } else {
+      A[h] = B[h] = C[h] = 0.0;
+    }
+    x[h] = (r == M - 1) ? 1.0 : 0.0;
+  }
+  const double E = inv_s;  // row 0 couples to x_m
+  const bool two = M > 32;
+  for (int it = 0; it < s; ++it) {
+    double P0 = x[0], P1 = x[1], acc0 = x[0], acc1 = x[1];
+    for (int k = 1; k <= deg; ++k) {
+      double dn0 = __shfl_up_sync(0xffffffffu, P0, 1);
+      double up0 = __shfl_down_sync(0xffffffffu, P0, 1);
+      double pm = __shfl_sync(0xffffffffu, m < 32 ? P0 : P1, m & 31);
+      double dn1 = 0.0, up1 = 0.0;
+      if (two) {
+        dn1 = __shfl_up_sync(0xffffffffu, P1, 1);
+        up1 = __shfl_down_sync(0xffffffffu, P1, 1);
+        double b31 = __shfl_sync(0xffffffffu, P0, 31);
+        double b32 = __shfl_sync(0xffffffffu, P1, 0);
+        if (lane == 0) dn1 = b31;
+        if (lane == 31) up0 = b32;
+      }
+      if (lane == 0) dn0 = 0.0;
+      if (lane == 31) {
+        if (!two) up0 = 0.0;
+        up1 = 0.0;
+      }
+      double n0 = fma(A[0], P0, fma(C[0], up0, B[0] * dn0));
+      if (lane == 0) n0 = fma(E, pm, n0);
+      P0 = n0;
+      acc0 = fma(c_inv_fact[k], P0, acc0);
+      if (two) {
+        double n1 = fma(A[1], P1, fma(C[1], up1, B[1] * dn1));
+        P1 = n1;
+        acc1 = fma(c_inv_fact[k], P1, acc1);
+      }
+    }
+    x[0] = acc0;
+    x[1] = acc1;
+  }
+  if (lane < m) c.yexp[lane] = x[0];
+  if (lane + 32 < m) c.yexp[lane + 32] = x[1];
+  __syncwarp();
+}
+
+// After small_expm_warp: err and the combination coefficients (warp 0; the
+// coefficients come from phi_2(X) e_1 = X phi_3(X) e_1 + e_1 / 2).
+__device__ void finish_check(Ctl& c, int m, double tau) {
+  const int lane = threadIdx.x & 31;
+  const double tau2 = tau * tau;
+  for (int r = lane; r < m; r += 32) {
+    double hy = c.alpha[r] * c.yexp[r];
+    if (r > 0) hy = fma(c.low[r - 1], c.yexp[r - 1], hy);
+    if (r + 1 < m) hy = fma(c.up[r + 1], c.yexp[r + 1], hy);
+    double phi2 = fma(tau, hy, r == 0 ? 0.5 : 0.0);
+    c.coef[r] = tau2 * c.beta * phi2 * c.scale[r];
+  }
+  if (lane == 0) c.err = tau2 * tau * c.beta * c.hn * fabs(c.yexp[m - 1]);
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__device__ __forceinline__ T stencil(const T* __restrict__ x, long long p, const GridDev& g, T Dk,
+                                     const double* __restrict__ bfield, T bc, T cfac) {
+  const T xp = __ldcg(x + p);
+  if (bfield == nullptr) {
+    T s = T(0);
+#pragma unroll
+    for (int d = 0; d < N; ++d) s += __ldcg(x + p - g.stride[d]) + __ldcg(x + p + g.stride[d]);
+    return cfac * (bc * s - Dk * xp);
+  }
+  const double bp = __ldg(bfield + p);
+  T s = T(0);
+#pragma unroll
+  for (int d = 0; d < N; ++d) {
+    const long long st = g.stride[d];
+    s += T(0.5 * (bp + __ldg(bfield + p - st))) * __ldcg(x + p - st);
+    s += T(0.5 * (bp + __ldg(bfield + p + st))) * __ldcg(x + p + st);
+  }
+  return cfac * (s - Dk * xp);
+}
+
+__device__ __forceinline__ double reaction(int kind, const double* rp, int species, double u, double v) {
+  switch (kind) {
+    case 1: return u * (1.0 - u);
+    case 2: return rp[0] * u * (1.0 - u / rp[1]);
+    case 3:
+      if (species == 0) return u * (1.0 - u - rp[0] * v);
+      return rp[2] * v * (1.0 - v - rp[1] * u);
+    default: return 0.0;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T diag_of(const SpeciesDev<T>& S, int k);
+template <>
+__device__ __forceinline__ double diag_of<double>(const SpeciesDev<double>& S, int k) { return __ldg(S.diag + k); }
+template <>
+__device__ __forceinline__ float diag_of<float>(const SpeciesDev<float>& S, int k) { return __ldg(S.diagf + k); }
+
+// Runs phipm for one species; returns false if the kernel must stop.
+// Two partial-sum buffers used alternately: between two reductions that use
+// the same buffer every CTA has passed a barrier after reading it.
+__device__ __forceinline__ double* part_buf(double* part, int& red) {
+  double* b = part + (red & 1) * (4 * MAX_BLOCKS);
+  ++red;
+  return b;
+}
+
+template <typename T, int N>
+__device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int sidx, Ctl& c, unsigned& bar,
+                              int& red, double ynorm2) {
+  const GridDev& g = a.g;
+  const int ncomp = *S.ncomp;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gthreads = (long long)gridDim.x * blockDim.x;
+  const T cfac = (T)a.cfac;
+  const T bc = (T)S.beta_c;
+  const double anorm = a.dt * (*S.gersh);
+  const int m_max = a.m_max;
+  const long long vs = g.size;
+  double* pb = nullptr;
+  if (threadIdx.x == 0) {
+    c.t = 0.0;
+    c.tau = 1.0;
+    c.ynorm = fmax(sqrt(ynorm2), 1e-300);
+    c.abort = 0;
+  }
+  __syncthreads();
+  int nsub = 0;
+  while (c.t < 1.0) {
+    if (nsub >= MAX_SUBSTEPS) {
+      if (threadIdx.x == 0) atomicOr(&a.st->err, ERRF_KRYLOV);
+      return false;
+    }
+    if (threadIdx.x == 0) {
+      c.last = c.tau >= 1.0 - c.t;
+      if (c.last) c.tau = 1.0 - c.t;
+      c.nrej = 0;
+    }
+    __syncthreads();
+    const double t = c.t;
+    // w_1 = A y + v_1 + t v_2
+    for (long long k = gtid; k < ncomp; k += gthreads) {
+      const long long p = __ldg(S.idx + k);
+      T ay = stencil<T, N>(S.Yg, p, g, diag_of<T>(S, (int)k), S.beta_field, bc, cfac);
+      T w1 = ay + __ldcg(S.V1c + k) + (T)t * __ldcg(S.V2c + k);
+      S.W1g[p] = w1;
+    }
+    if (!grid_barrier(a.st, bar, 10)) return false;
+    // w_2 = A w_1 + v_2 -> V_0 (unnormalised)
+    {
+      Acc<T> acc;
+      for (long long k = gtid; k < ncomp; k += gthreads) {
+        const long long p = __ldg(S.idx + k);
+        T aw = stencil<T, N>(S.W1g, p, g, diag_of<T>(S, (int)k), S.beta_field, bc, cfac);
+        T w2 = aw + __ldcg(S.V2c + k);
+        S.V[p] = w2;
+        acc.add(w2, w2);
+      }
+      double v[1] = {acc.value()};
+      pb = part_buf(a.part, red);
+      block_partials<1>(v, pb);
+    }
+    if (!grid_barrier(a.st, bar, 11)) return false;
+    {
+      double tot[1];
+      grid_totals<1>(pb, tot);
+      if (threadIdx.x == 0) {
+        c.beta = sqrt(tot[0]);
+        if (!isfinite(c.beta)) {
+          atomicOr(&a.st->err, ERRF_NONFINITE);
+          c.abort = 1;
+        }
+        c.scale[0] = c.beta > 0.0 ? 1.0 / c.beta : 0.0;
+        c.m = 0;
+        c.accepted = 0;
+        c.breakdown = 0;
+      }
+      __syncthreads();
+      if (c.abort) return false;
+    }
+    if (c.beta > 0.0) {
+      for (int j = 0; j < m_max; ++j) {
+        const T sj = (T)c.scale[j];
+        const T sjm1 = j > 0 ? (T)c.scale[j - 1] : T(0);
+        const T* Vj = S.V + (long long)j * vs;
+        const T* Vjm1 = S.V + (long long)(j > 0 ? j - 1 : 0) * vs;
+        T* Vj1 = S.V + (long long)(j + 1) * vs;
+        // z = A v_j, <z, v_j>, <z, v_{j-1}>
+        {
+          Acc<T> da, db;
+          for (long long k = gtid; k < ncomp; k += gthreads) {
+            const long long p = __ldg(S.idx + k);
+            T z = stencil<T, N>(Vj, p, g, diag_of<T>(S, (int)k), S.beta_field, bc, cfac) * sj;
+            T vj = __ldcg(Vj + p) * sj;
+            T vjm1 = j > 0 ? __ldcg(Vjm1 + p) * sjm1 : T(0);
+            S.Zc[k] = z;
+            da.add(z, vj);
+            db.add(z, vjm1);
+          }
+          double v[2] = {da.value(), db.value()};
+          pb = part_buf(a.part, red);
+      block_partials<2>(v, pb);
+        }
+        if (!grid_barrier(a.st, bar, 12)) return false;
+        {
+          double tot[2];
+          grid_totals<2>(pb, tot);
+          if (threadIdx.x == 0) {
+            c.alpha[j] = tot[0];
+            c.up[j] = j > 0 ? tot[1] : 0.0;
+          }
+          __syncthreads();
+        }
+        // z -= h_jj v_j + h_{j-1,j} v_{j-1};  V_{j+1} = z;  |z|^2
+        {
+          const T hjj = (T)c.alpha[j], hjm = (T)c.up[j];
+          Acc<T> dn;
+          for (long long k = gtid; k < ncomp; k += gthreads) {
+            const long long p = __ldg(S.idx + k);
+            T z = __ldcg(S.Zc + k);
+            T vj = __ldcg(Vj + p) * sj;
+            T vjm1 = j > 0 ? __ldcg(Vjm1 + p) * sjm1 : T(0);
+            T w = z - hjj * vj - hjm * vjm1;
+            Vj1[p] = w;
+            dn.add(w, w);
+          }
+          double v[1] = {dn.value()};
+          pb = part_buf(a.part, red);
+      block_partials<1>(v, pb);
+        }
+        if (!grid_barrier(a.st, bar, 13)) return false;
+        {
+          double tot[1];
+          grid_totals<1>(pb, tot);
+          if (threadIdx.x == 0) {
+            const double hn = sqrt(tot[0]);
+            if (!isfinite(hn)) {
+              atomicOr(&a.st->err, ERRF_NONFINITE);
+              c.abort = 1;
+            }
+            c.low[j] = hn;
+            c.hn = hn;
+            c.m = j + 1;
+            c.breakdown = hn < BREAKDOWN_REL * anorm;
+            c.scale[j + 1] = c.breakdown ? 0.0 : 1.0 / hn;
+          }
+          __syncthreads();
+          if (c.abort) return false;
+        }
+        const int m = c.m;
+        if (m % CHECK_EVERY == 0 || m == m_max || c.breakdown) {
+          if (threadIdx.x < 32) {
+            small_expm_warp(c, m, 2, c.tau);
+            finish_check(c, m, c.tau);
+            if (threadIdx.x == 0) {
+              if (c.breakdown) c.err = 0.0;
+              c.accepted = c.err <= a.tol * c.tau * c.ynorm;
+            }
+          }
+          __syncthreads();
+          if (c.accepted) break;
+        }
+      }
+      // rejections at m_max: shrink tau, reuse the basis
+      if (!c.accepted) {
+        const int m = c.m;
+        for (;;) {
+          if (threadIdx.x == 0) {
+            const double tolabs = a.tol * c.tau * c.ynorm;
+            const double fac = fmax(0.2, 0.9 * pow(tolabs / c.err, 1.0 / (m + 1)));
+            c.tau *= fac;
+            c.last = 0;
+            c.nrej += 1;
+            if (c.tau < TAU_MIN) {
+              atomicOr(&a.st->err, ERRF_KRYLOV);
+              c.abort = 1;
+            }
+          }
+          __syncthreads();
+          if (c.abort) return false;
+          if (threadIdx.x < 32) {
+            small_expm_warp(c, m, 2, c.tau);
+            finish_check(c, m, c.tau);
+            if (threadIdx.x == 0) c.accepted = c.err <= a.tol * c.tau * c.ynorm;
+          }
+          __syncthreads();
+          if (c.accepted) break;
+        }
+      }
+    } else {
+      if (threadIdx.x == 0) {
+        c.err = 0.0;
+        c.m = 0;
+      }
+      __syncthreads();
+    }
+    // y <- y + tau w_1 + sum_i coef_i V_i ; |y|^2
+    {
+      const int m = c.m;
+      const double tau = c.tau;
+      Acc<double> yn;
+      for (long long k = gtid; k < ncomp; k += gthreads) {
+        const long long p = __ldg(S.idx + k);
+        double sum = 0.0;
+        for (int i = 0; i < m; ++i) sum = fma(c.coef[i], (double)__ldcg(S.V + (long long)i * vs + p), sum);
+        double y = fma(tau, (double)__ldcg(S.W1g + p), __ldcg(S.Yc + k)) + sum;
+        S.Yc[k] = y;
+        S.Yg[p] = (T)y;
+        yn.add(y, y);
+      }
+      double v[1] = {yn.value()};
+      pb = part_buf(a.part, red);
+      block_partials<1>(v, pb);
+    }
+    if (!grid_barrier(a.st, bar, 14)) return false;
+    {
+      double tot[1];
+      grid_totals<1>(pb, tot);
+      if (threadIdx.x == 0) {
+        const int m = c.m;
+        if (blockIdx.x == 0 && a.stats) {
+          StatsDev* st = a.stats;
+          if (nsub < TRACE_MAX) {
+            st->trace_m[sidx][nsub] = m;
+            st->trace_tau[sidx][nsub] = c.tau;
+          } else {
+            atomicOr(&a.st->err, ERRF_CAPACITY);
+          }
+          st->rejections[sidx] += c.nrej;
+          st->iters[sidx] += m;
+        }
+        double grow;
+        if (c.err == 0.0) grow = 2.0;
+        else grow = fmin(2.0, 0.9 * pow(a.tol * c.tau * c.ynorm / c.err, 1.0 / (m + 1)));
+        c.t = c.last ? 1.0 : c.t + c.tau;
+        if (c.t < 1.0) c.tau = fmin(1.0 - c.t, c.tau * grow);
+        c.ynorm = fmax(sqrt(tot[0]), 1e-300);
+        if (!isfinite(c.ynorm)) {
+          atomicOr(&a.st->err, ERRF_NONFINITE);
+          c.abort = 1;
+        }
+      }
+      __syncthreads();
+      if (c.abort) return false;
+    }
+    ++nsub;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats) {
+    a.stats->substeps[sidx] = nsub;
+    a.stats->trace_len[sidx] = min(nsub, TRACE_MAX);
+  }
+  return true;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
+  __shared__ Ctl c;
+  unsigned bar = 0;
+  int red = 0;
+  double* pb = nullptr;
+  const GridDev& g = a.g;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gthreads = (long long)gridDim.x * blockDim.x;
+  // ---- set-up: y = v_0, v_1, v_2 for every species (reads every species'
+  // field before any is overwritten)
+  double yn[2] = {0.0, 0.0};
+  for (int s = 0; s < a.nspecies; ++s) {
+    const SpeciesDev<T>& S = a.sp[s];
+    const int ncomp = *S.ncomp;
+    Acc<double> acc;
+    for (long long k = gtid; k < ncomp; k += gthreads) {
+      const long long p = __ldg(S.idx + k);
+      double y, v1, v2;
+      if (a.mode == MODE_GIVEN) {
+        y = a.given[0][p];
+        v1 = a.given[1][p];
+        v2 = a.given[2][p];
+      } else {
+        const double u = S.u[p];
+        double other = 0.0;
+        if (a.nspecies == 2) {
+          const SpeciesDev<T>& O = a.sp[1 - s];
+          other = (O.kind[p] & 3) == K_COMP ? O.u[p] : 0.0;
+        }
+        const double F = s == 0 ? reaction(a.reaction, a.rp, 0, u, other) : reaction(a.reaction, a.rp, 1, other, u);
+        const double Fp = S.fvalid[p] ? S.Fprev[p] : F;
+        y = u;
+        v1 = a.dt * F;
+        v2 = a.dt * (F - Fp);
+      }
+      S.Yc[k] = y;
+      S.Yg[p] = (T)y;
+      S.V1c[k] = (T)v1;
+      S.V2c[k] = (T)v2;
+      acc.add(y, y);
+    }
+    yn[s] = acc.value();
+  }
+  // F_{n-1} <- F_n after every species has read the fields
+  double v2p[2] = {yn[0], yn[1]};
+  pb = part_buf(a.part, red);
+      block_partials<2>(v2p, pb);
+  if (!grid_barrier(a.st, bar, 1)) return;
+  double tot[2];
+  grid_totals<2>(pb, tot);
+  if (a.mode == MODE_ETD2) {
+    for (int s = 0; s < a.nspecies; ++s) {
+      const SpeciesDev<T>& S = a.sp[s];
+      const int ncomp = *S.ncomp;
+      for (long long k = gtid; k < ncomp; k += gthreads) {
+        const long long p = __ldg(S.idx + k);
+        // F_n = v_1 / dt recomputed exactly as in the set-up
+        const double u = S.u[p];
+        double other = 0.0;
+        if (a.nspecies == 2) {
+          const SpeciesDev<T>& O = a.sp[1 - s];
+          other = (O.kind[p] & 3) == K_COMP ? O.u[p] : 0.0;
+        }
+        const double F = s == 0 ? reaction(a.reaction, a.rp, 0, u, other) : reaction(a.reaction, a.rp, 1, other, u);
+        S.Fprev[p] = F;
+        S.fvalid[p] = 1;
+      }
+    }
+  }
+  for (int s = 0; s < a.nspecies; ++s) {
+    if (!phipm_species<T, N>(a, a.sp[s], s, c, bar, red, tot[s])) return;
+  }
+  if (!grid_barrier(a.st, bar, 2)) return;
+  // ---- write back: new values at computational points, 0 elsewhere
+  for (int s = 0; s < a.nspecies; ++s) {
+    const SpeciesDev<T>& S = a.sp[s];
+    const int ncomp = *S.ncomp;
+    for (long long k = gtid; k < ncomp; k += gthreads) {
+      const long long p = __ldg(S.idx + k);
+      S.u[p] = __ldcg(S.Yc + k);
+    }
+    for (long long p = gtid; p < g.size; p += gthreads) {
+      if ((__ldg(S.kind + p) & 3) != K_COMP) {
+        if (S.u[p] != 0.0) S.u[p] = 0.0;
+        if (a.mode == MODE_ETD2 && S.fvalid[p]) S.fvalid[p] = 0;
+      }
+    }
+  }
+}
+
+template <typename T>
+static void* phipm_entry(int ndim) {
+  switch (ndim) {
+    case 2: return (void*)phipm_kernel<T, 2>;
+    case 3: return (void*)phipm_kernel<T, 3>;
+    case 4: return (void*)phipm_kernel<T, 4>;
+  }
+  return nullptr;
+}
+
+static bool g_fact_ready = false;
+
+template <typename T>
+cudaError_t launch_phipm(const PhipmArgs<T>& a, int nblocks, cudaStream_t stream) {
+  if (!g_fact_ready) {
+    double f[64];
+    f[0] = 1.0;
+    for (int k = 1; k < 64; ++k) f[k] = f[k - 1] / (double)k;
+    cudaError_t e = cudaMemcpyToSymbol(c_inv_fact, f, sizeof(f));
+    if (e != cudaSuccess) return e;
+    g_fact_ready = true;
+  }
+  void* fn = phipm_entry<T>(a.g.ndim);
+  if (!fn) return cudaErrorInvalidValue;
+  if (nblocks > MAX_BLOCKS) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(&a.st->barrier, 0, sizeof(unsigned), stream);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&a};
+  return cudaLaunchCooperativeKernel(fn, nblocks, PH_NT, args, 0, stream);
+}
+
+int phipm_max_blocks(int ndim, bool fp32) {
+  void* fn = fp32 ? phipm_entry<float>(ndim) : phipm_entry<double>(ndim);
+  if (!fn) return 0;
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, PH_NT, 0) != cudaSuccess) return 0;
+  return min(per, 1) * sms;
+}
+
+template cudaError_t launch_phipm<double>(const PhipmArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_phipm<float>(const PhipmArgs<float>&, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void apply_kernel(const ApplyArgs a) {
+  const int ncomp = *a.ncomp;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < ncomp; k += (long long)gridDim.x * blockDim.x) {
+    const long long p = a.idx[k];
+    a.y[p] = stencil<double, N>(a.x, p, a.g, a.diag[k], a.beta_field, a.beta_c, a.cfac);
+  }
+}
+
+cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t stream) {
+  switch (a.g.ndim) {
+    case 2: apply_kernel<2><<<152 * 4, 256, 0, stream>>>(a); break;
+    case 3: apply_kernel<3><<<152 * 4, 256, 0, stream>>>(a); break;
+    case 4: apply_kernel<4><<<152 * 4, 256, 0, stream>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace etd

@@ -1,0 +1,559 @@
+// Level-set step of the free-boundary algorithm (Sec. 4.3, Algorithm Steps
+// 1-2; Stefan condition of Eq. free), as one persistent cooperative kernel.
+//
+// Local level set (after Peng, Merriman, Osher, Zhao & Kang 1999): phi is
+// clamped to [-G, G], G = 6h; the update set T is {|phi| < G} grown by one
+// node along every axis; the work list holds T grown by three more nodes (the
+// reach of the WENO5 stencil).  Out-of-box neighbours repeat the edge value.
+//
+// Phases of levelset_advance:
+//   1. extension of u (Aslam 2004 quadratic normal extrapolation):
+//      n = grad phi/|grad phi| (central; |grad phi| floored at 1e-12);
+//      u_n = n.grad u on computational points whose neighbours are
+//      computational (valid1), u_nn = n.grad u_n on valid2; three
+//      pseudo-time sweeps q_tau + n.grad q = s (first-order upwind along n,
+//      step h/(2 sqrt N), ceil(12 sqrt N) steps) for u_nn (s = 0) on T minus
+//      valid2, u_n (s = u_nn) on T minus valid1, u (s = u_n) on T minus the
+//      computational points;
+//   2. Stefan speed at every node of T: x_G = x - phi n,
+//      V = mu max(0, (4 u(x_G - h n) - u(x_G - 2h n)) / (2h)), N-linear
+//      interpolation of the extended u (points clamped to the box);
+//   3. phi_t + V |grad phi| = 0: Godunov Hamiltonian on HJ-WENO5 one-sided
+//      derivatives (Jiang & Peng 2000, eps = 1e-6), Shu-Osher TVD-RK3,
+//      max(1, ceil(dt max V N / (0.5 h))) substeps, then clamp;
+//   4. optionally reinitialisation phi_t + S(phi_0)(|grad phi| - 1) = 0,
+//      S = phi_0 / sqrt(phi_0^2 + h^2) (Sussman, Smereka & Osher 1994), same
+//      spatial scheme upwinded by the sign of S, TVD-RK3 with pseudo-step
+//      0.5 h / sqrt N, ceil(12 sqrt N) steps, on a work set rebuilt from the
+//      advected phi, then clamp.
+#include <cmath>
+
+#include "common.cuh"
+#include "levelset.cuh"
+
+namespace etd {
+
+constexpr int LS_NT = 512;
+constexpr double BAND = 6.0;
+constexpr double WENO_EPS = 1e-6;
+constexpr double GRAD_FLOOR = 1e-12;
+
+enum : uint8_t {
+  F_T = 1, F_T1 = 2, F_T2 = 4, F_T3 = 8, F_V0 = 16, F_V1 = 32, F_V2 = 64, F_S = 128
+};
+enum : int { LS_ADVANCE = 0, LS_PREPARE = 1 };
+
+struct LsArgs {
+  GridDev g;
+  LevelsetBufs b;
+  DevStatus* st;
+  const uint8_t* kind;
+  double* phi;
+  double* u;
+  double dt;
+  double mu;
+  int mode;
+  int reinit;
+};
+
+LevelsetBufs levelset_carve(const GridDev& g, const std::function<char*(size_t)>& take) {
+  const size_t G = (size_t)g.size;
+  LevelsetBufs b;
+  b.flags = (uint8_t*)take(G);
+  b.list = (int*)take(G * sizeof(int));
+  b.count = (int*)take(4 * sizeof(int));
+  b.cta_count = (int*)take(MAX_BLOCKS * sizeof(int));
+  b.vmax = (double*)take(sizeof(double));
+  b.nsub = (int*)take(sizeof(int));
+  b.nrm = (double*)take((size_t)g.ndim * G * sizeof(double));
+  b.V = (double*)take(G * sizeof(double));
+  b.S0 = (double*)take(G * sizeof(double));
+  for (int i = 0; i < 6; ++i) b.q[i] = (double*)take(G * sizeof(double));
+  b.p1 = (double*)take(G * sizeof(double));
+  b.p2 = (double*)take(G * sizeof(double));
+  return b;
+}
+
+template <int N>
+__device__ __forceinline__ void coords(const GridDev& g, long long p, int* ix) {
+  long long rem = p;
+#pragma unroll
+  for (int d = 0; d < N; ++d) {
+    ix[d] = (int)(rem / g.stride[d]);
+    rem -= (long long)ix[d] * g.stride[d];
+  }
+}
+
+__device__ __forceinline__ long long nbr(const GridDev& g, long long p, const int* ix, int d, int k) {
+  int i = ix[d] + k;
+  i = i < 0 ? 0 : (i > g.n[d] - 1 ? g.n[d] - 1 : i);
+  return p + (long long)(i - ix[d]) * g.stride[d];
+}
+
+// ------------------------------------------------------------------ WENO5
+__device__ __forceinline__ double weno5(double v1, double v2, double v3, double v4, double v5) {
+  const double p1 = v1 / 3.0 - 7.0 * v2 / 6.0 + 11.0 * v3 / 6.0;
+  const double p2 = -v2 / 6.0 + 5.0 * v3 / 6.0 + v4 / 3.0;
+  const double p3 = v3 / 3.0 + 5.0 * v4 / 6.0 - v5 / 6.0;
+  const double a = v1 - 2.0 * v2 + v3, b = v1 - 4.0 * v2 + 3.0 * v3;
+  const double c = v2 - 2.0 * v3 + v4, d = v2 - v4;
+  const double e = v3 - 2.0 * v4 + v5, f = 3.0 * v3 - 4.0 * v4 + v5;
+  const double s1 = 13.0 / 12.0 * (a * a) + 0.25 * (b * b);
+  const double s2 = 13.0 / 12.0 * (c * c) + 0.25 * (d * d);
+  const double s3 = 13.0 / 12.0 * (e * e) + 0.25 * (f * f);
+  const double e1 = WENO_EPS + s1, e2 = WENO_EPS + s2, e3 = WENO_EPS + s3;
+  const double a1 = 0.1 / (e1 * e1);
+  const double a2 = 0.6 / (e2 * e2);
+  const double a3 = 0.3 / (e3 * e3);
+  return (a1 * p1 + a2 * p2 + a3 * p3) / (a1 + a2 + a3);
+}
+
+// Godunov |grad phi| at node p from array src; positive: outward motion.
+template <int N>
+__device__ double godunov(const GridDev& g, const double* __restrict__ src, long long p, const int* ix, bool positive) {
+  const double h = g.h;
+  double acc = 0.0;
+#pragma unroll
+  for (int d = 0; d < N; ++d) {
+    double f[7];
+#pragma unroll
+    for (int k = -3; k <= 3; ++k) f[k + 3] = __ldcg(src + nbr(g, p, ix, d, k));
+    double q[6];  // q[k+2] = (f(i+k) - f(i+k-1)) / h, k = -2..3
+#pragma unroll
+    for (int k = -2; k <= 3; ++k) q[k + 2] = (f[k + 3] - f[k + 2]) / h;
+    const double dm = weno5(q[0], q[1], q[2], q[3], q[4]);
+    const double dp = weno5(q[5], q[4], q[3], q[2], q[1]);
+    double t;
+    if (positive) {
+      const double x = fmax(dm, 0.0), y = fmin(dp, 0.0);
+      t = fmax(x * x, y * y);
+    } else {
+      const double x = fmin(dm, 0.0), y = fmax(dp, 0.0);
+      t = fmax(x * x, y * y);
+    }
+    acc += t;
+  }
+  return sqrt(acc);
+}
+
+// ------------------------------------------------------------ work lists
+struct LsCtx {
+  unsigned bar;
+  int red;
+  long long chunk_lo, chunk_hi;
+};
+
+// Flags: S, T, T1, T2, T3 (dilations along the axes) and, with `kind`, the
+// validity bits V0 (computational), V1, V2.  Then the ordered list of T3
+// nodes.  Returns false if the kernel must stop.
+template <int N>
+__device__ bool build_work_set(const LsArgs& a, LsCtx& c, bool with_valid) {
+  const GridDev& g = a.g;
+  uint8_t* fl = a.b.flags;
+  const double G = BAND * g.h;
+  // pass A: S and V0
+  for (long long p = c.chunk_lo + threadIdx.x; p < c.chunk_hi; p += blockDim.x) {
+    uint8_t f = 0;
+    if (fabs(a.phi[p]) < G) f |= F_S;
+    if (with_valid && (a.kind[p] & 3) == K_COMP) f |= F_V0;
+    fl[p] = f;
+  }
+  if (!grid_barrier(a.st, c.bar, 20)) return false;
+  // passes B..E: each adds the dilation of the previous bit (and V1, V2)
+  const uint8_t src_bits[4] = {F_S, F_T, F_T1, F_T2};
+  const uint8_t dst_bits[4] = {F_T, F_T1, F_T2, F_T3};
+  for (int pass = 0; pass < 4; ++pass) {
+    const uint8_t sb = src_bits[pass], db = dst_bits[pass];
+    const bool vpass = with_valid && pass < 2;
+    const uint8_t vs = pass == 0 ? F_V0 : F_V1, vd = pass == 0 ? F_V1 : F_V2;
+    int cnt = 0;
+    for (long long p = c.chunk_lo + threadIdx.x; p < c.chunk_hi; p += blockDim.x) {
+      int ix[N];
+      coords<N>(g, p, ix);
+      uint8_t f = fl[p];
+      bool any = (f & sb) != 0;
+      bool all = (f & vs) != 0;
+#pragma unroll
+      for (int d = 0; d < N; ++d) {
+        const uint8_t fm = fl[nbr(g, p, ix, d, -1)], fp = fl[nbr(g, p, ix, d, 1)];
+        any = any || (fm & sb) || (fp & sb);
+        all = all && (fm & vs) && (fp & vs);
+      }
+      uint8_t add = any ? db : 0;
+      if (vpass && all) add |= vd;
+      // other threads only read bits this pass does not write
+      if (add) fl[p] = f | add;
+      if (pass == 3 && any) ++cnt;
+    }
+    if (pass == 3) {
+      for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+      __shared__ int s_c[LS_NT / 32];
+      if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = cnt;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < (int)blockDim.x / 32; ++w) t += s_c[w];
+        a.b.cta_count[blockIdx.x] = t;
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(a.st, c.bar, 21 + pass)) return false;
+  }
+  // ordered compaction of T3
+  __shared__ int s_off;
+  __shared__ int s_w[LS_NT / 32];
+  if (threadIdx.x == 0) {
+    int off = 0, tot = 0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      int v = __ldcg(a.b.cta_count + b);
+      if (b < (int)blockIdx.x) off += v;
+      tot += v;
+    }
+    s_off = off;
+    if (blockIdx.x == 0) a.b.count[0] = tot;
+  }
+  __syncthreads();
+  int run = s_off;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (long long base = c.chunk_lo; base < c.chunk_hi; base += blockDim.x) {
+    const long long p = base + threadIdx.x;
+    const bool f = p < c.chunk_hi && (fl[p] & F_T3);
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    const int before = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) s_w[wid] = __popc(bal);
+    __syncthreads();
+    int woff = 0, tot = 0;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) {
+      const int cc = s_w[w];
+      if (w < wid) woff += cc;
+      tot += cc;
+    }
+    if (f) a.b.list[run + woff + before] = (int)p;
+    run += tot;
+    __syncthreads();
+  }
+  return grid_barrier(a.st, c.bar, 25);
+}
+
+// TVD-RK3 on the nodes of T (list order); L(src, p) supplied by the caller.
+// Stage values p1/p2 hold phi off T (copied when the work set is built).
+template <int N, typename LFn>
+__device__ bool rk3(const LsArgs& a, LsCtx& c, double dt, bool clamp_last, LFn L) {
+  const GridDev& g = a.g;
+  const int n = __ldcg(a.b.count);
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gth = (long long)gridDim.x * blockDim.x;
+  const double G = BAND * g.h;
+  for (int stage = 0; stage < 3; ++stage) {
+    const double* src = stage == 0 ? a.phi : (stage == 1 ? a.b.p1 : a.b.p2);
+    for (long long i = gtid; i < n; i += gth) {
+      const long long p = __ldcg(a.b.list + i);
+      if (!(a.b.flags[p] & F_T)) continue;
+      int ix[N];
+      coords<N>(g, p, ix);
+      const double Lv = L(src, p, ix, i);
+      const double ph = a.phi[p];
+      if (stage == 0) {
+        a.b.p1[p] = ph + dt * Lv;
+      } else if (stage == 1) {
+        a.b.p2[p] = 0.75 * ph + 0.25 * (__ldcg(a.b.p1 + p) + dt * Lv);
+      } else {
+        double v = ph / 3.0 + 2.0 / 3.0 * (__ldcg(a.b.p2 + p) + dt * Lv);
+        if (clamp_last) v = fmin(fmax(v, -G), G);
+        a.phi[p] = v;
+      }
+    }
+    if (!grid_barrier(a.st, c.bar, 30 + stage)) return false;
+  }
+  return true;
+}
+
+// copy phi into the RK stage buffers on the work list
+template <int N>
+__device__ void stage_init(const LsArgs& a) {
+  const int n = __ldcg(a.b.count);
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gth = (long long)gridDim.x * blockDim.x;
+  for (long long i = gtid; i < n; i += gth) {
+    const long long p = __ldcg(a.b.list + i);
+    const double v = a.phi[p];
+    a.b.p1[p] = v;
+    a.b.p2[p] = v;
+  }
+}
+
+template <int N>
+__device__ bool reinitialise(const LsArgs& a, LsCtx& c) {
+  const GridDev& g = a.g;
+  if (!build_work_set<N>(a, c, false)) return false;
+  const int n = __ldcg(a.b.count);
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gth = (long long)gridDim.x * blockDim.x;
+  const double h = g.h;
+  for (long long i = gtid; i < n; i += gth) {
+    const long long p = __ldcg(a.b.list + i);
+    const double ph = a.phi[p];
+    a.b.S0[i] = ph / sqrt(ph * ph + h * h);
+  }
+  stage_init<N>(a);
+  if (!grid_barrier(a.st, c.bar, 40)) return false;
+  const int K = (int)ceil(12.0 * sqrt((double)N));
+  const double dtau = 0.5 * h / sqrt((double)N);
+  auto L = [&](const double* src, long long p, const int* ix, long long i) {
+    const double S = __ldcg(a.b.S0 + i);
+    return -S * (godunov<N>(g, src, p, ix, S > 0.0) - 1.0);
+  };
+  for (int it = 0; it < K; ++it) {
+    if (!rk3<N>(a, c, dtau, it == K - 1, L)) return false;
+  }
+  return true;
+}
+
+template <int N>
+__global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
+  const GridDev& g = a.g;
+  LsCtx c;
+  c.bar = 0;
+  c.red = 0;
+  const long long chunk = (g.size + gridDim.x - 1) / gridDim.x;
+  c.chunk_lo = min((long long)blockIdx.x * chunk, g.size);
+  c.chunk_hi = min(c.chunk_lo + chunk, g.size);
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gth = (long long)gridDim.x * blockDim.x;
+  const double h = g.h;
+  const double G = BAND * h;
+
+  if (a.mode == LS_PREPARE) {
+    for (long long p = gtid; p < g.size; p += gth) a.phi[p] = fmin(fmax(a.phi[p], -G), G);
+    if (!grid_barrier(a.st, c.bar, 50)) return;
+    if (a.reinit) reinitialise<N>(a, c);
+    return;
+  }
+
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.b.vmax = 0.0;
+  if (!build_work_set<N>(a, c, true)) return;
+  const int n = __ldcg(a.b.count);
+  const long long cap = g.size;
+  double* const UNN[2] = {a.b.q[0], a.b.q[1]};
+  double* const UN[2] = {a.b.q[2], a.b.q[3]};
+  double* const U[2] = {a.b.q[4], a.b.q[5]};
+  // normals, u_0, u_n, stage buffers
+  for (long long i = gtid; i < n; i += gth) {
+    const long long p = __ldcg(a.b.list + i);
+    int ix[N];
+    coords<N>(g, p, ix);
+    double gr[N];
+    double s2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < N; ++d) {
+      gr[d] = (a.phi[nbr(g, p, ix, d, 1)] - a.phi[nbr(g, p, ix, d, -1)]) / (2.0 * h);
+      s2 += gr[d] * gr[d];
+    }
+    const double nr = fmax(sqrt(s2), GRAD_FLOOR);
+    double nv[N];
+#pragma unroll
+    for (int d = 0; d < N; ++d) {
+      nv[d] = gr[d] / nr;
+      a.b.nrm[d * cap + i] = nv[d];
+    }
+    const uint8_t f = a.b.flags[p];
+    U[0][p] = (f & F_V0) ? a.u[p] : 0.0;
+    double un = 0.0;
+    if ((f & F_V1) && (f & F_T2)) {
+#pragma unroll
+      for (int d = 0; d < N; ++d)
+        un += nv[d] * (a.u[nbr(g, p, ix, d, 1)] - a.u[nbr(g, p, ix, d, -1)]) / (2.0 * h);
+    }
+    UN[0][p] = un;
+    a.b.p1[p] = a.phi[p];
+    a.b.p2[p] = a.phi[p];
+  }
+  if (!grid_barrier(a.st, c.bar, 51)) return;
+  for (long long i = gtid; i < n; i += gth) {
+    const long long p = __ldcg(a.b.list + i);
+    const uint8_t f = a.b.flags[p];
+    double unn = 0.0;
+    if ((f & F_V2) && (f & F_T1)) {
+      int ix[N];
+      coords<N>(g, p, ix);
+#pragma unroll
+      for (int d = 0; d < N; ++d)
+        unn += __ldcg(a.b.nrm + d * cap + i) *
+               (__ldcg(UN[0] + nbr(g, p, ix, d, 1)) - __ldcg(UN[0] + nbr(g, p, ix, d, -1))) / (2.0 * h);
+    }
+    UNN[0][p] = unn;
+  }
+  if (!grid_barrier(a.st, c.bar, 52)) return;
+  // three extrapolation sweeps
+  const int K = (int)ceil(12.0 * sqrt((double)N));
+  const double dtau = h / (2.0 * sqrt((double)N));
+  const uint8_t vbits[3] = {F_V2, F_V1, F_V0};
+  double* const* bufs[3] = {UNN, UN, U};
+  const double* src = nullptr;
+  for (int sw = 0; sw < 3; ++sw) {
+    double* const* B = bufs[sw];
+    int cur = 0;
+    for (int it = 0; it < K; ++it) {
+      const double* qc = B[cur];
+      double* qn = B[cur ^ 1];
+      for (long long i = gtid; i < n; i += gth) {
+        const long long p = __ldcg(a.b.list + i);
+        const uint8_t f = a.b.flags[p];
+        const double q0 = __ldcg(qc + p);
+        if ((f & F_T) && !(f & vbits[sw])) {
+          int ix[N];
+          coords<N>(g, p, ix);
+          double acc = 0.0;
+#pragma unroll
+          for (int d = 0; d < N; ++d) {
+            const double nd = __ldcg(a.b.nrm + d * cap + i);
+            double dd;
+            if (nd > 0.0) dd = (q0 - __ldcg(qc + nbr(g, p, ix, d, -1))) / h;
+            else dd = (__ldcg(qc + nbr(g, p, ix, d, 1)) - q0) / h;
+            acc += nd * dd;
+          }
+          const double s = src ? __ldcg(src + p) : 0.0;
+          qn[p] = q0 - dtau * (acc - s);
+        } else {
+          qn[p] = q0;
+        }
+      }
+      if (!grid_barrier(a.st, c.bar, 53)) return;
+      cur ^= 1;
+    }
+    src = B[cur];
+  }
+  // extended u back to the caller's array on the work list
+  for (long long i = gtid; i < n; i += gth) {
+    const long long p = __ldcg(a.b.list + i);
+    a.u[p] = __ldcg(src + p);
+  }
+  if (!grid_barrier(a.st, c.bar, 54)) return;
+  // Stefan speed on T
+  {
+    double vm = 0.0;
+    for (long long i = gtid; i < n; i += gth) {
+      const long long p = __ldcg(a.b.list + i);
+      if (!(a.b.flags[p] & F_T)) continue;
+      int ix[N];
+      coords<N>(g, p, ix);
+      double nv[N], xg[N];
+      const double ph = a.phi[p];
+#pragma unroll
+      for (int d = 0; d < N; ++d) {
+        nv[d] = __ldcg(a.b.nrm + d * cap + i);
+        xg[d] = (g.lo[d] + h * ix[d]) - ph * nv[d];
+      }
+      double us[2];
+#pragma unroll
+      for (int sidx = 0; sidx < 2; ++sidx) {
+        const double dist = sidx == 0 ? h : 2.0 * h;
+        int i0[N];
+        double fr[N];
+#pragma unroll
+        for (int d = 0; d < N; ++d) {
+          double s = ((xg[d] - dist * nv[d]) - g.lo[d]) / h;
+          s = fmin(fmax(s, 0.0), (double)(g.n[d] - 1));
+          int ii = (int)floor(s);
+          ii = min(ii, g.n[d] - 2);
+          i0[d] = ii;
+          fr[d] = s - ii;
+        }
+        double out = 0.0;
+        for (int corner = 0; corner < (1 << N); ++corner) {
+          double w = 1.0;
+          long long q = 0;
+#pragma unroll
+          for (int d = 0; d < N; ++d) {
+            const int bit = (corner >> d) & 1;
+            w = w * (bit ? fr[d] : (1.0 - fr[d]));
+            q += (long long)(i0[d] + bit) * g.stride[d];
+          }
+          out += w * a.u[q];
+        }
+        us[sidx] = out;
+      }
+      const double V = a.mu * fmax(0.0, (4.0 * us[0] - us[1]) / (2.0 * h));
+      a.b.V[i] = V;
+      vm = fmax(vm, V);
+    }
+    for (int o = 16; o > 0; o >>= 1) vm = fmax(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+    if ((threadIdx.x & 31) == 0 && vm > 0.0)
+      atomicMax((unsigned long long*)a.b.vmax, (unsigned long long)__double_as_longlong(vm));
+  }
+  if (!grid_barrier(a.st, c.bar, 55)) return;
+  // advection
+  {
+    const double vmax = __ldcg(a.b.vmax);
+    double ns = ceil(a.dt * vmax * N / (0.5 * h));
+    int nsub = ns < 1.0 ? 1 : (int)fmin(ns, 1e6);
+    if (nsub > 100000) {
+      if (threadIdx.x == 0) atomicOr(&a.st->err, ERRF_NONFINITE);
+      return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.b.nsub = nsub;
+    const double dts = a.dt / nsub;
+    auto L = [&](const double* s, long long p, const int* ix, long long i) {
+      return -__ldcg(a.b.V + i) * godunov<N>(g, s, p, ix, true);
+    };
+    for (int sub = 0; sub < nsub; ++sub) {
+      if (!rk3<N>(a, c, dts, sub == nsub - 1, L)) return;
+    }
+  }
+  if (a.reinit) reinitialise<N>(a, c);
+}
+
+static int ls_blocks(int ndim) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  void* fn = ndim == 2 ? (void*)levelset_kernel<2> : ndim == 3 ? (void*)levelset_kernel<3> : (void*)levelset_kernel<4>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, LS_NT, 0) != cudaSuccess || per < 1) return 0;
+  return min(sms, MAX_BLOCKS);
+}
+
+static cudaError_t launch(const LsArgs& a, cudaStream_t stream) {
+  void* fn;
+  switch (a.g.ndim) {
+    case 2: fn = (void*)levelset_kernel<2>; break;
+    case 3: fn = (void*)levelset_kernel<3>; break;
+    case 4: fn = (void*)levelset_kernel<4>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  const int nb = ls_blocks(a.g.ndim);
+  if (nb <= 0) return cudaErrorLaunchOutOfResources;
+  cudaError_t e = cudaMemsetAsync(&a.st->barrier, 0, sizeof(unsigned), stream);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&a};
+  return cudaLaunchCooperativeKernel(fn, nb, LS_NT, args, 0, stream);
+}
+
+cudaError_t launch_levelset_advance(const GridDev& g, const LevelsetBufs& b, DevStatus* st, const uint8_t* kind,
+                                    double* phi, double* u, double dt, double mu, bool reinit, cudaStream_t stream) {
+  LsArgs a;
+  a.g = g;
+  a.b = b;
+  a.st = st;
+  a.kind = kind;
+  a.phi = phi;
+  a.u = u;
+  a.dt = dt;
+  a.mu = mu;
+  a.mode = LS_ADVANCE;
+  a.reinit = reinit ? 1 : 0;
+  return launch(a, stream);
+}
+
+cudaError_t launch_levelset_prepare(const GridDev& g, const LevelsetBufs& b, DevStatus* st, double* phi, bool reinit,
+                                    cudaStream_t stream) {
+  LsArgs a;
+  a.g = g;
+  a.b = b;
+  a.st = st;
+  a.kind = nullptr;
+  a.phi = phi;
+  a.u = nullptr;
+  a.dt = 0.0;
+  a.mu = 0.0;
+  a.mode = LS_PREPARE;
+  a.reinit = reinit ? 1 : 0;
+  return launch(a, stream);
+}
+
+}  // namespace etd

@@ -1,0 +1,31 @@
+// Level-set step buffers and launch entry points.
+#pragma once
+#include <functional>
+
+#include "common.cuh"
+
+namespace etd {
+
+struct LevelsetBufs {
+  uint8_t* flags;   // grid: tube / validity bits
+  int* list;        // grid indices of the work set, grid order
+  int* count;       // [0] list length
+  int* cta_count;   // per-CTA counts for the in-kernel compaction
+  double* vmax;     // [0] max Stefan speed on the tube
+  int* nsub;        // [0] advection substeps of the last call
+  double* nrm;      // N x list capacity: unit normals (compact)
+  double* V;        // list capacity: Stefan speed (compact)
+  double* S0;       // list capacity: sign function of reinitialisation (compact)
+  double* q[6];     // grid: extension ping-pong buffers (u_nn, u_n, u)
+  double* p1;       // grid: RK stage values
+  double* p2;
+};
+
+LevelsetBufs levelset_carve(const GridDev& g, const std::function<char*(size_t)>& take);
+
+cudaError_t launch_levelset_advance(const GridDev& g, const LevelsetBufs& b, DevStatus* st, const uint8_t* kind,
+                                    double* phi, double* u, double dt, double mu, bool reinit, cudaStream_t stream);
+cudaError_t launch_levelset_prepare(const GridDev& g, const LevelsetBufs& b, DevStatus* st, double* phi, bool reinit,
+                                    cudaStream_t stream);
+
+}  // namespace etd

@@ -1,0 +1,258 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bit-exact: node classification and the list of computational points.
+1e-12 relative: row diagonals D_p and the matrix-free operator.
+1e-10 relative (FP64): the phi-combination, the ETD2 step and the level-set
+step, from identical inputs.  Where the two adaptive controllers' error
+estimates straddle a threshold (a different basis size or step), the
+oracle replays the GPU's decision trace and the values are compared again.
+1e-5 relative in u for the FP32-mixed path against the FP64 oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import etd as oetd  # noqa: E402
+from oracle import krylov, levelset  # noqa: E402
+from oracle.eb import EBOperator  # noqa: E402
+from oracle.grid import Grid  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2209_15095_gb300 import build
+
+    build.build()
+    from paper_2209_15095_gb300 import etd
+
+    return etd
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _shape_phi(ndim, n, box, kind):
+    g = Grid((n,) * ndim, (-box,) * ndim, (box,) * ndim)
+    x = g.coords()
+    if kind == "ball":
+        ph = np.sqrt(sum(c * c for c in x)) - 0.62 * box
+    elif kind == "ellipsoid":
+        a = [0.7, 0.55, 0.5, 0.45][:ndim]
+        ph = np.sqrt(sum((x[d] / (a[d] * box)) ** 2 for d in range(ndim))) - 1.0
+    elif kind == "peanut":
+        s = box / 1.0
+        X, Y = x[0] / s, x[1] / s
+        ph = 0.5 - np.exp(-20 * (X ** 2 + (Y - 0.25) ** 2)) - np.exp(-20 * (X ** 2 + (Y + 0.25) ** 2))
+        for d in range(2, ndim):
+            ph = ph + (x[d] / s) ** 2
+    return g, ph
+
+
+CASES = [(2, 40, 1.0, "peanut"), (2, 33, 2.0, "ball"), (3, 20, 2.0, "ellipsoid"), (3, 24, 1.0, "peanut"),
+         (4, 13, 2.0, "ball")]
+
+
+def _ctx(lib, g, **kw):
+    args = dict(nspecies=1, precision="fp64", tol=1e-10, m_max=40, reaction="logistic", mu=(1.0,), beta=(1.0,))
+    args.update(kw)
+    return lib.Context(g.n, g.lo, g.hi, **args)
+
+
+@pytest.mark.parametrize("ndim,n,box,kind", CASES)
+@pytest.mark.parametrize("beta_field", [False, True])
+def test_domain_and_operator(lib, ndim, n, box, kind, beta_field):
+    g, ph = _shape_phi(ndim, n, box, kind)
+    rng = np.random.default_rng(ndim * 100 + n)
+    beta = (1.0 + 0.3 * rng.uniform(-1, 1, size=g.n)) if beta_field else 1.0
+    op = EBOperator(g, ph, beta)
+    ctx = _ctx(lib, g)
+    dph = _dev(ph)
+    dbeta = _dev(beta) if beta_field else None
+    ctx.init_domain(0, dph, dbeta)
+    dom = ctx.read_domain(0)
+    ref_kind = np.where(op.comp, 2, np.where(op.ghost, 1, 0)).astype(np.uint8)
+    assert np.array_equal(dom["kind"], ref_kind)
+    assert dom["ncomp"] == op.ncomp
+    assert np.array_equal(dom["idx"], op.index.astype(np.int32))
+    assert np.max(np.abs(dom["diag"] - op.diag) / np.abs(op.diag)) < 1e-12
+    assert dom["nclamp"] == op.nclamp
+    assert abs(dom["gersh"] - op.gershgorin()) <= 1e-12 * op.gershgorin()
+    # y = dt C x
+    dt = 0.37
+    x = rng.standard_normal(g.n)
+    x_c = op.from_grid(x)
+    x_grid = op.to_grid(x_c)  # zero off the computational set
+    y = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    ctx.apply_operator(0, dt, _dev(x_grid), y)
+    yo = dt * (op.C @ x_c)
+    yg = op.from_grid(y.cpu().numpy())
+    assert np.max(np.abs(yg - yo)) <= 1e-12 * np.max(np.abs(yo))
+
+
+def _compare_phipm(ctx, op, dt, vs, tol, m_max, stats, yg):
+    apply_A = lambda x: dt * (op.C @ x)
+    anorm = dt * op.gershgorin()
+    yo, tr = krylov.phipm(apply_A, vs, tol, m_max, anorm)
+    gtr = [(t, m) for t, m in stats["trace"]]
+    if [m for _, m in gtr] != [m for _, m, _ in tr] or len(gtr) != len(tr):
+        yo, tr = krylov.phipm(apply_A, vs, tol, m_max, anorm, forced_trace=[(t, m, 0) for t, m in gtr])
+    return yo, tr
+
+
+@pytest.mark.parametrize("ndim,n,box,kind", CASES)
+def test_phi_combination_fp64(lib, ndim, n, box, kind):
+    g, ph = _shape_phi(ndim, n, box, kind)
+    op = EBOperator(g, ph, 1.0)
+    ctx = _ctx(lib, g, tol=1e-10, m_max=40)
+    ctx.init_domain(0, _dev(ph))
+    rng = np.random.default_rng(7 + n)
+    vs = [rng.standard_normal(op.ncomp) for _ in range(3)]
+    dt = 0.8 * g.h  # stiff enough for several substeps
+    y = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    st = ctx.phi_combination(0, dt, *[_dev(op.to_grid(v)) for v in vs], y, stats=True)
+    yg = op.from_grid(y.cpu().numpy())
+    yo, tr = _compare_phipm(ctx, op, dt, vs, 1e-10, 40, st, yg)
+    assert np.max(np.abs(yg - yo)) <= 1e-10 * np.max(np.abs(yo)), (st, tr)
+    # off the computational set the output is zero
+    yfull = y.cpu().numpy()
+    assert np.all(yfull[~op.comp] == 0.0)
+
+
+def test_phi_combination_substeps_and_rejections(lib):
+    g, ph = _shape_phi(2, 48, 2.0, "ball")
+    op = EBOperator(g, ph, 1.0)
+    ctx = _ctx(lib, g, tol=1e-8, m_max=10)
+    ctx.init_domain(0, _dev(ph))
+    rng = np.random.default_rng(3)
+    vs = [rng.standard_normal(op.ncomp) for _ in range(3)]
+    dt = 0.3
+    y = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    st = ctx.phi_combination(0, dt, *[_dev(op.to_grid(v)) for v in vs], y, stats=True)
+    assert st["substeps"] > 3 and st["rejections"] > 0
+    yg = op.from_grid(y.cpu().numpy())
+    yo, _ = _compare_phipm(ctx, op, dt, vs, 1e-8, 10, st, yg)
+    assert np.max(np.abs(yg - yo)) <= 1e-10 * np.max(np.abs(yo))
+
+
+@pytest.mark.parametrize("ndim,n,box,kind", [(2, 40, 1.0, "peanut"), (3, 24, 2.0, "ellipsoid")])
+def test_phi_combination_mixed(lib, ndim, n, box, kind):
+    g, ph = _shape_phi(ndim, n, box, kind)
+    op = EBOperator(g, ph, 1.0)
+    ctx = _ctx(lib, g, precision="mixed", tol=1e-7, m_max=40)
+    ctx.init_domain(0, _dev(ph))
+    rng = np.random.default_rng(11)
+    u = rng.uniform(0, 1, op.ncomp)
+    F = u * (1 - u)
+    dt = 0.05
+    vs = [u, dt * F, 0.1 * dt * F]
+    y = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    ctx.phi_combination(0, dt, *[_dev(op.to_grid(v)) for v in vs], y)
+    ctx.sync()
+    yo = oetd.phi.combination_expm(dt * op.C.toarray(), vs) if op.ncomp < 3000 else None
+    if yo is None:
+        yo, _ = krylov.phipm(lambda x: dt * (op.C @ x), vs, 1e-12, 40, dt * op.gershgorin())
+    yg = op.from_grid(y.cpu().numpy())
+    assert np.max(np.abs(yg - yo)) <= 1e-5 * np.max(np.abs(yo))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_etd2_step_from_state(lib, precision, tol):
+    g, ph = _shape_phi(3, 26, 2.0, "ellipsoid")
+    beta = 1.0
+    op = EBOperator(g, ph, beta)
+    ctx = _ctx(lib, g, precision=precision, tol=1e-10 if precision == "fp64" else 1e-6, m_max=40)
+    ctx.init_domain(0, _dev(ph))
+    rng = np.random.default_rng(5)
+    u0 = op.to_grid(rng.uniform(0, 1, op.ncomp))
+    du = torch.tensor(u0, device="cuda")
+    dt = 0.02
+    # step 1 (ETD1: F_prev := F_0), step 2 (ETD2 with the stored F_prev)
+    st1 = ctx.step(dt, [du], stats=True)
+    u1g = du.cpu().numpy()
+    st2 = ctx.step(dt, [du], stats=True)
+    u2g = du.cpu().numpy()
+    F = lambda v: v * (1 - v)
+    uc0 = op.from_grid(u0)
+    u1o, _ = oetd.etd2_step(op, uc0, F(uc0), F(uc0), dt, tol=1e-12, m_max=40)
+    u2o, _ = oetd.etd2_step(op, u1o, F(u1o), F(uc0), dt, tol=1e-12, m_max=40)
+    for ug, uo in ((u1g, u1o), (u2g, u2o)):
+        assert np.max(np.abs(op.from_grid(ug) - uo)) <= tol * np.max(np.abs(uo)) * 10
+        assert np.all(ug[~op.comp] == 0.0)
+
+
+def test_levelset_step_matches(lib):
+    from paper_2209_15095_gb300 import inputs
+
+    w = inputs.disc2d()
+    g = Grid(w.n, w.lo, w.hi)
+    ph = levelset.clamp(w.phi0[0], g.h)
+    op = EBOperator(g, ph, 1.0)
+    u = np.where(op.comp, w.u0[0], 0.0)
+    ctx = _ctx(lib, g, tol=w.tol, m_max=w.m_max, mu=w.mu)
+    dph = _dev(ph)
+    du = _dev(u)
+    ctx.init_domain(0, dph)
+    for reinit in (False, True):
+        ph_o, ue_o, _ = levelset.levelset_advance(ph, u, op.comp, g, w.dt, w.mu[0], reinit)
+        dph2, du2 = dph.clone(), du.clone()
+        ctx.levelset_advance(0, dph2, du2, w.dt, reinit)
+        ctx.sync()
+        assert np.max(np.abs(dph2.cpu().numpy() - ph_o)) <= 1e-10 * g.h
+        assert np.max(np.abs(du2.cpu().numpy() - ue_o)) <= 1e-10 * np.max(np.abs(ue_o))
+
+
+@pytest.mark.parametrize("ndim", [3, 4])
+def test_levelset_step_matches_nd(lib, ndim):
+    n = {3: 28, 4: 22}[ndim]
+    g, ph0 = _shape_phi(ndim, n, 3.0, "ellipsoid")
+    ph = levelset.clamp(ph0, g.h)
+    if ndim == 3:
+        ph = levelset.reinit(ph, g.h)
+    op = EBOperator(g, ph, 1.0)
+    x = g.coords()
+    r = np.sqrt(sum(c * c for c in x))
+    u = np.where(op.comp, np.cos(0.3 * r), 0.0)
+    ctx = _ctx(lib, g, mu=(1.3,))
+    dph, du = _dev(ph), _dev(u)
+    ctx.init_domain(0, dph)
+    reinit = ndim == 3
+    ph_o, ue_o, _ = levelset.levelset_advance(ph, u, op.comp, g, 0.02, 1.3, reinit)
+    ctx.levelset_advance(0, dph, du, 0.02, reinit)
+    ctx.sync()
+    assert np.max(np.abs(dph.cpu().numpy() - ph_o)) <= 1e-10 * g.h
+    assert np.max(np.abs(du.cpu().numpy() - ue_o)) <= 1e-10 * np.max(np.abs(ue_o))
+
+
+def test_free_boundary_disc_multistep(lib):
+    from oracle.freeboundary import FreeBoundary, Species
+    from paper_2209_15095_gb300 import inputs
+
+    w = inputs.disc2d()
+    g = Grid(w.n, w.lo, w.hi)
+    fb = FreeBoundary(g, [Species(w.phi0[0], w.u0[0], 1.0, w.mu[0])], w.reaction, w.rparams, w.tol, w.m_max,
+                      reinit_every=w.reinit_every)
+    ctx = _ctx(lib, g, tol=w.tol, m_max=w.m_max, mu=w.mu)
+    dph = _dev(w.phi0[0])
+    du = _dev(np.where(w.phi0[0] < 0, w.u0[0], 0.0))
+    ctx.levelset_prepare(dph, False)
+    ctx.init_domain(0, dph)
+    nsteps = 12
+    for k in range(nsteps):
+        fb.step(w.dt)
+        ctx.levelset_advance(0, dph, du, w.dt, (k + 1) % w.reinit_every == 0)
+        ctx.init_domain(0, dph)
+        ctx.step(w.dt, [du])
+    ctx.sync()
+    ph_g, u_g = dph.cpu().numpy(), du.cpu().numpy()
+    ph_o, u_o = fb.sp[0].phi, fb.sp[0].u
+    both = (ph_g < 0) == (ph_o < 0)
+    assert both.all()
+    near = np.abs(ph_o) < g.h
+    assert np.max(np.abs(ph_g - ph_o)[near]) <= 1e-2 * g.h
+    assert np.max(np.abs(u_g - u_o)) <= 1e-8 * np.max(np.abs(u_o))
