@@ -149,7 +149,7 @@ def test_phi_combination_mixed(lib, ndim, n, box, kind):
     rng = np.random.default_rng(11)
     u = rng.uniform(0, 1, op.ncomp)
     F = u * (1 - u)
-    dt = 0.05
+    dt = g.h * g.h  # |dt C| about 4N, the stiffness of the workloads
     vs = [u, dt * F, 0.1 * dt * F]
     y = torch.zeros(g.n, dtype=torch.float64, device="cuda")
     ctx.phi_combination(0, dt, *[_dev(op.to_grid(v)) for v in vs], y)
