@@ -159,6 +159,11 @@ etd_status levelset_advance(etd_ctx* ctx, int species, double* phi, double* u, d
 /* Clamp phi to [-6h, 6h] and, if do_reinit, reinitialise it (as step 4 above). */
 etd_status levelset_prepare(etd_ctx* ctx, double* phi, int do_reinit);
 
+/* Synchronise and copy the statistics of the last etd_step or
+ * etd_phi_combination of this context (what a non-NULL stats argument of
+ * that call would have received). */
+etd_status etd_last_stats(etd_ctx* ctx, etd_step_stats* stats);
+
 /* Wait for the stream and report any error raised on the device since the
  * last report. */
 etd_status etd_sync(etd_ctx* ctx);

@@ -43,6 +43,8 @@ struct etd_ctx {
   LevelsetBufs ls;
   int nblocks = 0;
   bool fp32 = false;
+  int last_nspecies = 0;
+  int last_species0 = 0;
   std::string err;
 };
 
@@ -201,6 +203,29 @@ etd_status read_status(etd_ctx* c) {
   return fail(c, ETD_ERR_ARG, "a device list or trace outgrew its buffer");
 }
 
+etd_status copy_stats(etd_ctx* c, etd_step_stats* stats) {
+  etd_status rs = read_status(c);
+  StatsDev h;
+  cudaError_t e = cudaMemcpy(&h, c->stats, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stats read");
+  memset(stats, 0, sizeof(*stats));
+  for (int s = 0; s < c->last_nspecies; ++s) {
+    const int so = c->last_species0 + s;
+    int nc = 0;
+    cudaMemcpy(&nc, c->sp[so].ncomp, sizeof(int), cudaMemcpyDeviceToHost);
+    stats->ncomp[s] = nc;
+    stats->substeps[s] = h.substeps[s];
+    stats->rejections[s] = h.rejections[s];
+    stats->krylov_iters[s] = h.iters[s];
+    stats->trace_len[s] = h.trace_len[s];
+    for (int i = 0; i < ETD_TRACE_MAX && i < TRACE_MAX; ++i) {
+      stats->trace_m[s][i] = h.trace_m[s][i];
+      stats->trace_tau[s][i] = h.trace_tau[s][i];
+    }
+  }
+  return rs;
+}
+
 template <typename T>
 SpeciesDev<T> species_dev(etd_ctx* c, int s, double* u) {
   SpeciesBufs& b = c->sp[s];
@@ -254,27 +279,10 @@ etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int spec
   if (e != cudaSuccess) return cuda_fail(c, e, "stats reset");
   e = launch_phipm<T>(a, c->nblocks, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "phipm launch");
+  c->last_nspecies = a.nspecies;
+  c->last_species0 = mode == MODE_ETD2 ? 0 : species;
   if (!stats) return ETD_OK;
-  etd_status rs = read_status(c);
-  StatsDev h;
-  e = cudaMemcpy(&h, c->stats, sizeof(h), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(c, e, "stats read");
-  memset(stats, 0, sizeof(*stats));
-  for (int s = 0; s < a.nspecies; ++s) {
-    const int so = mode == MODE_ETD2 ? s : species;
-    int nc = 0;
-    cudaMemcpy(&nc, c->sp[so].ncomp, sizeof(int), cudaMemcpyDeviceToHost);
-    stats->ncomp[s] = nc;
-    stats->substeps[s] = h.substeps[s];
-    stats->rejections[s] = h.rejections[s];
-    stats->krylov_iters[s] = h.iters[s];
-    stats->trace_len[s] = h.trace_len[s];
-    for (int i = 0; i < ETD_TRACE_MAX && i < TRACE_MAX; ++i) {
-      stats->trace_m[s][i] = h.trace_m[s][i];
-      stats->trace_tau[s][i] = h.trace_tau[s][i];
-    }
-  }
-  return rs;
+  return copy_stats(c, stats);
 }
 
 }  // namespace
@@ -410,6 +418,11 @@ etd_status etd_apply_operator(etd_ctx* c, int species, double dt, const double* 
   cudaError_t e = launch_apply(a, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "apply launch");
   return ETD_OK;
+}
+
+etd_status etd_last_stats(etd_ctx* c, etd_step_stats* stats) {
+  if (!c || !stats) return ETD_ERR_ARG;
+  return copy_stats(c, stats);
 }
 
 etd_status etd_sync(etd_ctx* c) {

@@ -87,6 +87,7 @@ def library():
         "levelset_advance": (I, [P, I, P, P, D, I]),
         "levelset_prepare": (I, [P, P, I]),
         "etd_sync": (I, [P]),
+        "etd_last_stats": (I, [P, ctypes.POINTER(StepStats)]),
         "etd_read_domain": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), P, P, P, I]),
         "etd_last_error": (ctypes.c_char_p, [P]),
     }
@@ -198,6 +199,11 @@ class Context:
 
     def levelset_prepare(self, phi, reinit):
         self._check(self.lib.levelset_prepare(self.ctx, _ptr(phi, self.n, "phi"), 1 if reinit else 0))
+
+    def last_stats(self):
+        st = StepStats()
+        self._check(self.lib.etd_last_stats(self.ctx, ctypes.byref(st)))
+        return st.as_dict(self.nspecies)
 
     def sync(self):
         self._check(self.lib.etd_sync(self.ctx))
