@@ -71,8 +71,8 @@ bool check_grid(const etd_grid* grid, GridDev& g, std::string& why) {
   g.ndim = grid->ndim;
   long long size = 1;
   for (int d = 0; d < grid->ndim; ++d) {
-    if (grid->n[d] < 8) {
-      why = "each axis needs at least 8 nodes";
+    if (grid->n[d] < 8 || grid->n[d] > 65535) {
+      why = "each axis needs 8 to 65535 nodes";
       return false;
     }
     g.n[d] = grid->n[d];

@@ -87,8 +87,9 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned& k, int sit
           ok = 0;
           break;
         }
+        // another CTA gave up: stop waiting for it
+        if (*((volatile int*)&st->err) & ERRF_TIMEOUT) { ok = 0; break; }
       }
-      if (*((volatile int*)&st->err) & ERRF_TIMEOUT) { ok = 0; break; }
     }
     __threadfence();
     s_ok = ok;

@@ -61,6 +61,7 @@ LevelsetBufs levelset_carve(const GridDev& g, const std::function<char*(size_t)>
   LevelsetBufs b;
   b.flags = (uint8_t*)take(G);
   b.list = (int*)take(G * sizeof(int));
+  b.lcoord = (ushort4*)take(G * sizeof(ushort4));
   b.count = (int*)take(4 * sizeof(int));
   b.cta_count = (int*)take(MAX_BLOCKS * sizeof(int));
   b.vmax = (double*)take(sizeof(double));
@@ -74,14 +75,25 @@ LevelsetBufs levelset_carve(const GridDev& g, const std::function<char*(size_t)>
   return b;
 }
 
+// axis indices of node p (grids hold fewer than 2^31 nodes: 32-bit division)
 template <int N>
 __device__ __forceinline__ void coords(const GridDev& g, long long p, int* ix) {
-  long long rem = p;
+  unsigned rem = (unsigned)p;
 #pragma unroll
   for (int d = 0; d < N; ++d) {
-    ix[d] = (int)(rem / g.stride[d]);
-    rem -= (long long)ix[d] * g.stride[d];
+    const unsigned st = (unsigned)g.stride[d];
+    const unsigned q = rem / st;
+    ix[d] = (int)q;
+    rem -= q * st;
   }
+}
+
+template <int N>
+__device__ __forceinline__ void unpack(ushort4 c, int* ix) {
+  ix[0] = c.x;
+  ix[1] = c.y;
+  if (N > 2) ix[2] = c.z;
+  if (N > 3) ix[3] = c.w;
 }
 
 __device__ __forceinline__ long long nbr(const GridDev& g, long long p, const int* ix, int d, int k) {
@@ -91,10 +103,15 @@ __device__ __forceinline__ long long nbr(const GridDev& g, long long p, const in
 }
 
 // ------------------------------------------------------------------ WENO5
+// The candidate stencils use exact reciprocals of 3 and 6 rounded once, and
+// the nonlinear weights share one division: with d_k = (eps + s_k)^2,
+//   sum_k (g_k/d_k) p_k / sum_k (g_k/d_k)
+//     = (g1 d2 d3 p1 + g2 d1 d3 p2 + g3 d1 d2 p3) / (g1 d2 d3 + g2 d1 d3 + g3 d1 d2).
 __device__ __forceinline__ double weno5(double v1, double v2, double v3, double v4, double v5) {
-  const double p1 = v1 / 3.0 - 7.0 * v2 / 6.0 + 11.0 * v3 / 6.0;
-  const double p2 = -v2 / 6.0 + 5.0 * v3 / 6.0 + v4 / 3.0;
-  const double p3 = v3 / 3.0 + 5.0 * v4 / 6.0 - v5 / 6.0;
+  constexpr double sixth = 1.0 / 6.0;
+  const double p1 = (2.0 * v1 - 7.0 * v2 + 11.0 * v3) * sixth;
+  const double p2 = (-v2 + 5.0 * v3 + 2.0 * v4) * sixth;
+  const double p3 = (2.0 * v3 + 5.0 * v4 - v5) * sixth;
   const double a = v1 - 2.0 * v2 + v3, b = v1 - 4.0 * v2 + 3.0 * v3;
   const double c = v2 - 2.0 * v3 + v4, d = v2 - v4;
   const double e = v3 - 2.0 * v4 + v5, f = 3.0 * v3 - 4.0 * v4 + v5;
@@ -102,16 +119,15 @@ __device__ __forceinline__ double weno5(double v1, double v2, double v3, double 
   const double s2 = 13.0 / 12.0 * (c * c) + 0.25 * (d * d);
   const double s3 = 13.0 / 12.0 * (e * e) + 0.25 * (f * f);
   const double e1 = WENO_EPS + s1, e2 = WENO_EPS + s2, e3 = WENO_EPS + s3;
-  const double a1 = 0.1 / (e1 * e1);
-  const double a2 = 0.6 / (e2 * e2);
-  const double a3 = 0.3 / (e3 * e3);
-  return (a1 * p1 + a2 * p2 + a3 * p3) / (a1 + a2 + a3);
+  const double d1 = e1 * e1, d2 = e2 * e2, d3 = e3 * e3;
+  const double w1 = 0.1 * (d2 * d3), w2 = 0.6 * (d1 * d3), w3 = 0.3 * (d1 * d2);
+  return (w1 * p1 + w2 * p2 + w3 * p3) / (w1 + w2 + w3);
 }
 
 // Godunov |grad phi| at node p from array src; positive: outward motion.
 template <int N>
 __device__ double godunov(const GridDev& g, const double* __restrict__ src, long long p, const int* ix, bool positive) {
-  const double h = g.h;
+  const double inv_h = 1.0 / g.h;
   double acc = 0.0;
 #pragma unroll
   for (int d = 0; d < N; ++d) {
@@ -120,7 +136,7 @@ __device__ double godunov(const GridDev& g, const double* __restrict__ src, long
     for (int k = -3; k <= 3; ++k) f[k + 3] = __ldcg(src + nbr(g, p, ix, d, k));
     double q[6];  // q[k+2] = (f(i+k) - f(i+k-1)) / h, k = -2..3
 #pragma unroll
-    for (int k = -2; k <= 3; ++k) q[k + 2] = (f[k + 3] - f[k + 2]) / h;
+    for (int k = -2; k <= 3; ++k) q[k + 2] = (f[k + 3] - f[k + 2]) * inv_h;
     const double dm = weno5(q[0], q[1], q[2], q[3], q[4]);
     const double dp = weno5(q[5], q[4], q[3], q[2], q[1]);
     double t;
@@ -228,7 +244,14 @@ __device__ bool build_work_set(const LsArgs& a, LsCtx& c, bool with_valid) {
       if (w < wid) woff += cc;
       tot += cc;
     }
-    if (f) a.b.list[run + woff + before] = (int)p;
+    if (f) {
+      int ix[N];
+      coords<N>(g, p, ix);
+      a.b.list[run + woff + before] = (int)p;
+      a.b.lcoord[run + woff + before] =
+          make_ushort4((unsigned short)ix[0], (unsigned short)ix[1], (unsigned short)(N > 2 ? ix[2] : 0),
+                       (unsigned short)(N > 3 ? ix[3] : 0));
+    }
     run += tot;
     __syncthreads();
   }
@@ -249,7 +272,7 @@ __device__ bool rk3(const LsArgs& a, LsCtx& c, double dt, bool clamp_last, LFn L
       const long long p = __ldcg(a.b.list + i);
       if (!(a.b.flags[p] & F_T)) continue;
       int ix[N];
-      coords<N>(g, p, ix);
+      unpack<N>(a.b.lcoord[i], ix);
       const double Lv = L(src, p, ix, i);
       const double ph = a.phi[p];
       if (stage == 0) {
@@ -317,6 +340,7 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
   c.chunk_hi = min(c.chunk_lo + chunk, g.size);
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gth = (long long)gridDim.x * blockDim.x;
   const double h = g.h;
+  const double inv_h = 1.0 / h;
   const double G = BAND * h;
 
   if (a.mode == LS_PREPARE) {
@@ -337,7 +361,7 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
   for (long long i = gtid; i < n; i += gth) {
     const long long p = __ldcg(a.b.list + i);
     int ix[N];
-    coords<N>(g, p, ix);
+    unpack<N>(a.b.lcoord[i], ix);
     double gr[N];
     double s2 = 0.0;
 #pragma unroll
@@ -371,7 +395,7 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
     double unn = 0.0;
     if ((f & F_V2) && (f & F_T1)) {
       int ix[N];
-      coords<N>(g, p, ix);
+      unpack<N>(a.b.lcoord[i], ix);
 #pragma unroll
       for (int d = 0; d < N; ++d)
         unn += __ldcg(a.b.nrm + d * cap + i) *
@@ -398,14 +422,14 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
         const double q0 = __ldcg(qc + p);
         if ((f & F_T) && !(f & vbits[sw])) {
           int ix[N];
-          coords<N>(g, p, ix);
+          unpack<N>(a.b.lcoord[i], ix);
           double acc = 0.0;
 #pragma unroll
           for (int d = 0; d < N; ++d) {
             const double nd = __ldcg(a.b.nrm + d * cap + i);
             double dd;
-            if (nd > 0.0) dd = (q0 - __ldcg(qc + nbr(g, p, ix, d, -1))) / h;
-            else dd = (__ldcg(qc + nbr(g, p, ix, d, 1)) - q0) / h;
+            if (nd > 0.0) dd = (q0 - __ldcg(qc + nbr(g, p, ix, d, -1))) * inv_h;
+            else dd = (__ldcg(qc + nbr(g, p, ix, d, 1)) - q0) * inv_h;
             acc += nd * dd;
           }
           const double s = src ? __ldcg(src + p) : 0.0;
@@ -432,7 +456,7 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
       const long long p = __ldcg(a.b.list + i);
       if (!(a.b.flags[p] & F_T)) continue;
       int ix[N];
-      coords<N>(g, p, ix);
+      unpack<N>(a.b.lcoord[i], ix);
       double nv[N], xg[N];
       const double ph = a.phi[p];
 #pragma unroll

@@ -9,6 +9,7 @@ namespace etd {
 struct LevelsetBufs {
   uint8_t* flags;   // grid: tube / validity bits
   int* list;        // grid indices of the work set, grid order
+  ushort4* lcoord;  // per list entry: the node's axis indices
   int* count;       // [0] list length
   int* cta_count;   // per-CTA counts for the in-kernel compaction
   double* vmax;     // [0] max Stefan speed on the tube
