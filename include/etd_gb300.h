@@ -179,6 +179,36 @@ etd_status etd_read_domain(etd_ctx* ctx, int species, int* ncomp, int* nclamp, d
 /* Message for the last error of this context (static storage of the ctx). */
 const char* etd_last_error(const etd_ctx* ctx);
 
+/* Largest problem etd_phi_combination_noalloc accepts, and the size of the
+ * fixed device array it works in. */
+#define ETD_NOALLOC_MAX_NODES 32768
+#define ETD_NOALLOC_MAX_M 30
+#define ETD_NOALLOC_SCRATCH_BYTES (10u << 20)
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that may not allocate device memory at all: a host that owns every byte of
+ * the GPU through its own allocator and hands a plug-in only its inputs and
+ * outputs, or a deployment that forbids allocation once it is running.  It
+ * computes the same result as etd_init_domain(phi, constant beta) followed by
+ * etd_phi_combination in FP64:
+ *   y = phi_0(dt C) v0 + phi_1(dt C) v1 + phi_2(dt C) v2
+ * on the computational points of {phi < 0}, y = 0 elsewhere.  grid, phi, v0,
+ * v1, v2 and y are as for the context calls (device, full grid, FP64, owned by
+ * the caller); stream is a cudaStream_t (NULL: legacy default stream).
+ * Scratch: one file-scope device array of ETD_NOALLOC_SCRATCH_BYTES (10 MiB)
+ * that every GPU which loads the library holds until the process exits; no
+ * cudaMalloc, cudaFree or other allocating call is made.  Limits: at most
+ * ETD_NOALLOC_MAX_NODES grid nodes and m_max <= ETD_NOALLOC_MAX_M, else
+ * ETD_ERR_WORKSPACE.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  Every call clears the part of the array it
+ * uses, then works in it; calls that overlap on the GPU (two streams, or two
+ * host threads) share the array and race.  The call synchronises `stream` and
+ * returns any device-side error. */
+etd_status etd_phi_combination_noalloc(const etd_grid* grid, const double* phi, double beta, double dt,
+                                       const double* v0, const double* v1, const double* v2, double* y,
+                                       double krylov_tol, int m_max, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
