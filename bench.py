@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--clocks", default="on", choices=["on", "off"])
+    ap.add_argument("--no-stress", action="store_true")
+    ap.add_argument("--stress-steps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -246,13 +248,14 @@ def main():
                 one_step(ctx, phis, us, k)
                 k += 1
             ctx.sync()
-            times, parts, cells, iters, subs = [], [], 0, 0, 0
+            times, parts, cells, iters, subs, ls_flops = [], [], 0, 0, 0, 0.0
             for _ in range(args.steps):
                 flush.zero_()
                 ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
                 one_step(ctx, phis, us, k, ev)
                 k += 1
                 st = ctx.last_stats()  # synchronises; outside the events
+                ls_flops += sum(levelset_flops(ctx.levelset_last_stats(), len(w.n)) for _ in range(nsp))
                 times.append(ev[0].elapsed_time(ev[3]))
                 parts.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
                 cells += sum(s_["ncomp"] for s_ in st)
@@ -260,12 +263,17 @@ def main():
                 subs += sum(s_["substeps"] for s_ in st)
         ctx.sync()
         return {"ctx": ctx, "phis": phis, "us": us, "times": times, "parts": parts, "cells": cells,
-                "iters": iters, "substeps": subs, "k": k}
+                "iters": iters, "substeps": subs, "k": k, "ls_flops": ls_flops}
 
     clocks = ClockSampler(local, enabled=args.clocks == "on" and rank == 0)
     r64 = run("fp64")
     rmx = None if args.no_mixed else run("mixed")
     e2e = None if args.no_e2e else run_e2e(args, w, make_ctx, initial_state, one_step, stream, flush, dev)
+    stress = None
+    if not args.no_stress and rank == 0:
+        del flush
+        torch.cuda.empty_cache()
+        stress = run_stress(etd, stream, dev, args.stress_steps)
     clk = clocks.stop()
 
     t64 = sum(r64["times"]) / 1e3
@@ -306,6 +314,8 @@ def main():
     if e2e is not None:
         out["e2e"] = e2e
     out["roofline"] = roofline(r64, w, avg_parts, names)
+    if stress is not None:
+        out["stress"] = stress
     if clk is not None:
         out["clocks"] = clk
     if not args.no_cpu_baseline:
@@ -332,6 +342,27 @@ def mixed_error(r64, rmx, nsp):
     return max(errs)
 
 
+# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA per clock x 2
+# flops x 2.07 GHz (the measured FMA loop reaches 1.17 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def levelset_flops(info, ndim):
+    """Algorithmic FP64 flops of one level-set launch, counted from the code's
+    arithmetic (add/mul/div/sqrt 1, fma 2): a Godunov/HJ-WENO5 RK stage costs
+    153 flops per axis (6 differences, 2 WENO5 evaluations of 69 flops, the
+    Godunov combination) plus 7 per node; the Stefan speed about 110 per tube
+    node.  Advection: tube x 3 stages x substeps; reinitialisation: tube x 3 x
+    ceil(12 sqrt N) stages.  The extension sweeps and the work-set build are
+    not counted (a conservative count)."""
+    stage = 153 * ndim + 7
+    k = math.ceil(12 * math.sqrt(ndim))
+    f = info["tube"] * (3 * info["nsub"] * stage + 110)
+    if info["reinit"]:
+        f += info["reinit_tube"] * 3 * k * stage
+    return float(f)
+
+
 def roofline(r, w, avg_parts, names):
     """Dominant kernel: the largest share of the step.  The Krylov kernel is
     reported against HBM bandwidth with its algorithmic bytes; the level-set
@@ -346,17 +377,81 @@ def roofline(r, w, avg_parts, names):
     ncomp = r["cells"] / steps
     iters = r["iters"] / steps
     subs = r["substeps"] / steps
-    s = 8.0
-    b = 8.0 + 4.0  # row diagonal + index per node-pass
-    # per node: every Krylov vector (3 vectors + metadata), the two w matvecs,
-    # the combination (m basis vectors + w_1 + y in, y out) and the set-up
-    bytes_step = ncomp * (iters * (3 * s + b) + subs * 2 * (3 * s + b) + (iters + 2 * subs) * s + subs * 16 + 48)
+    bytes_step = krylov_bytes(ncomp, iters, subs, 8)
     t_phipm = avg_parts[2] / 1e3
-    out = {"bound": "hbm", "kernel": names[2], "achieved": bytes_step / t_phipm / 1e9, "peak": hbm,
-           "unit": "GB/s", "frac": bytes_step / t_phipm / 1e9 / hbm, "traffic": None,
-           "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)",
-           "algorithmic_bytes_per_launch": bytes_step, "dominant_share": float(avg_parts[dom] / avg_parts.sum()),
-           "dominant_kernel": names[dom]}
+    krylov = {"bound": "hbm", "kernel": names[2], "achieved": bytes_step / t_phipm / 1e9, "peak": hbm,
+              "unit": "GB/s", "frac": bytes_step / t_phipm / 1e9 / hbm, "traffic": None,
+              "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)",
+              "algorithmic_bytes_per_launch": bytes_step}
+    t_ls = avg_parts[0] / 1e3
+    flops = r["ls_flops"] / steps
+    ls = {"bound": "alu", "kernel": names[0], "achieved": flops / t_ls / 1e12, "peak": FP64_PEAK_TFLOPS,
+          "unit": "TFLOP/s", "frac": flops / t_ls / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+          "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (unit counts and clock)",
+          "algorithmic_flops_per_launch": flops}
+    out = ls if dom == 0 else krylov
+    out = dict(out)
+    out["dominant_share"] = float(avg_parts[dom] / avg_parts.sum())
+    out["dominant_kernel"] = names[dom]
+    out["krylov_kernel"] = krylov if dom == 0 else None
+    return out
+
+
+def krylov_bytes(ncomp, iters, subs, s):
+    """Algorithmic bytes of one Krylov launch: per point, every basis vector
+    (read v_j, v_{j-1}, write v_{j+1}, read D_p and the index: 3s + 8 + 4
+    with the diagonal in FP64, 3s + 4 + 4 in FP32), two matvecs with a vector
+    add per substep (same count each), the combination (m + 2 vectors in T,
+    y read and written in FP64) and the set-up (48 B)."""
+    b = (8.0 if s == 8 else 4.0) + 4.0
+    return ncomp * (iters * (3 * s + b) + subs * 2 * (3 * s + b) + (iters + 2 * subs) * s + subs * 16 + 48)
+
+
+def run_stress(etd, stream, dev, steps):
+    """Bandwidth stress shape: ETD2 steps on a fixed ball of radius 7 in a
+    512^3 grid (vectors far above L2), FP64 and FP32-mixed."""
+    import numpy as np
+    import torch
+
+    from paper_2209_15095_gb300 import inputs
+
+    w = inputs.ball512()
+    phi = torch.tensor(w.phi0[0], dtype=torch.float64, device=dev)
+    u0 = torch.tensor(w.u0[0], dtype=torch.float64, device=dev)
+    del w.phi0, w.u0
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {"workload": "ball512", "grid": list(w.n), "dt": w.dt, "m_max": w.m_max, "steps": steps}
+    for precision in ("fp64", "mixed"):
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(stream):
+            ctx = etd.Context(w.n, w.lo, w.hi, nspecies=1, precision=precision, tol=w.tol, m_max=w.m_max,
+                              reaction=w.reaction, beta=w.beta, device=dev)
+            u = u0.clone()
+            ctx.init_domain(0, phi)
+            ctx.step(w.dt, [u])  # warm-up (first step: ETD1)
+            ctx.sync()
+            t, bytes_, iters, subs, cells = 0.0, 0.0, 0, 0, 0
+            for _ in range(steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.step(w.dt, [u])
+                e1.record(stream)
+                st = ctx.last_stats()[0]
+                dt_ms = e0.elapsed_time(e1)
+                t += dt_ms / 1e3
+                iters += st["krylov_iters"]
+                subs += st["substeps"]
+                cells += st["ncomp"]
+                bytes_ += krylov_bytes(st["ncomp"], st["krylov_iters"], st["substeps"], 8 if precision == "fp64" else 4)
+        del ctx
+        torch.cuda.empty_cache()
+        out[precision] = {"ms_per_step": 1e3 * t / steps, "mcell_updates_per_s": cells / t / 1e6,
+                          "krylov_iters_per_step": iters / steps, "substeps_per_step": subs / steps,
+                          "ncomp": cells // steps, "achieved_gbs": bytes_ / t / 1e9,
+                          "frac_of_hbm": bytes_ / t / 1e9 / hbm}
+    out["peak_gbs"] = hbm
     return out
 
 

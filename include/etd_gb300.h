@@ -159,6 +159,13 @@ etd_status levelset_advance(etd_ctx* ctx, int species, double* phi, double* u, d
 /* Clamp phi to [-6h, 6h] and, if do_reinit, reinitialise it (as step 4 above). */
 etd_status levelset_prepare(etd_ctx* ctx, double* phi, int do_reinit);
 
+/* Synchronise and report the work of the last levelset_advance /
+ * levelset_prepare (for throughput accounting): info[0] work-list length and
+ * info[1] update-set (tube) size of the advection, info[2] advection
+ * substeps, info[3] and info[4] the same two sizes for the
+ * reinitialisation, info[5] 1 if it reinitialised.  info: host, 8 ints. */
+etd_status levelset_last_stats(etd_ctx* ctx, int* info);
+
 /* Synchronise and copy the statistics of the last etd_step or
  * etd_phi_combination of this context (what a non-NULL stats argument of
  * that call would have received). */

@@ -23,7 +23,7 @@ struct SpeciesBufs {
   double* Yc = nullptr;
   void* V1c = nullptr;
   void* V2c = nullptr;
-  void* Zc = nullptr;
+  void* Z[2] = {nullptr, nullptr};
   const double* beta_field = nullptr;
   bool ready = false;
 };
@@ -169,7 +169,8 @@ size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
     b.Yc = cv.take<double>(G);
     b.V1c = cv.take<char>(s * G);
     b.V2c = cv.take<char>(s * G);
-    b.Zc = cv.take<char>(s * G);
+    b.Z[0] = cv.take<char>(s * G);
+    b.Z[1] = cv.take<char>(s * G);
     if (c) c->sp[sp] = b;
   }
   LevelsetBufs lb = levelset_carve(g, [&](size_t bytes) { return cv.take<char>(bytes); });
@@ -247,7 +248,8 @@ SpeciesDev<T> species_dev(etd_ctx* c, int s, double* u) {
   d.Yc = b.Yc;
   d.V1c = (T*)b.V1c;
   d.V2c = (T*)b.V2c;
-  d.Zc = (T*)b.Zc;
+  d.Z[0] = (T*)b.Z[0];
+  d.Z[1] = (T*)b.Z[1];
   return d;
 }
 
@@ -348,14 +350,18 @@ etd_status etd_init_domain(etd_ctx* c, int species, const double* phi, const dou
   ca.kind = b.kind;
   ca.tile_count = c->tile_count;
   ca.st = c->st;
-  ca.nzero = 2;
+  ca.nzero = 4;
   if (c->fp32) {
     ca.zero_f32[0] = (float*)b.Yg;
     ca.zero_f32[1] = (float*)b.W1g;
+    ca.zero_f32[2] = (float*)b.Z[0];
+    ca.zero_f32[3] = (float*)b.Z[1];
     ca.basis_f32 = (float*)b.V;
   } else {
     ca.zero_f64[0] = (double*)b.Yg;
     ca.zero_f64[1] = (double*)b.W1g;
+    ca.zero_f64[2] = (double*)b.Z[0];
+    ca.zero_f64[3] = (double*)b.Z[1];
     ca.basis_f64 = (double*)b.V;
   }
   ca.nbasis = c->par.m_max + 1;
@@ -460,6 +466,14 @@ etd_status levelset_advance(etd_ctx* c, int species, double* phi, double* u, dou
                                           do_reinit != 0, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "levelset launch");
   return ETD_OK;
+}
+
+etd_status levelset_last_stats(etd_ctx* c, int* info) {
+  if (!c || !info) return ETD_ERR_ARG;
+  etd_status rs = read_status(c);
+  cudaError_t e = cudaMemcpy(info, c->ls.info, 8 * sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "levelset stats read");
+  return rs;
 }
 
 etd_status levelset_prepare(etd_ctx* c, double* phi, int do_reinit) {

@@ -73,7 +73,7 @@ struct SpeciesDev {
   double* Yc;
   T* V1c;
   T* V2c;
-  T* Zc;
+  T* Z[2];  // full grid: A V_j of the last two basis vectors (unnormalised)
 };
 
 // mode of the phi-combination kernel

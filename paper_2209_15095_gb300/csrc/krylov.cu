@@ -189,6 +189,14 @@ __device__ __forceinline__ double diag_of<double>(const SpeciesDev<double>& S, i
 template <>
 __device__ __forceinline__ float diag_of<float>(const SpeciesDev<float>& S, int k) { return __ldg(S.diagf + k); }
 
+// w = ca Z + cb V1 + cc V2 at grid node q (zero off the computational set,
+// since all three arrays are).
+template <typename T>
+__device__ __forceinline__ T wval(const T* __restrict__ Z, const T* __restrict__ V1, const T* __restrict__ V2,
+                                  long long q, T ca, T cb, T cc) {
+  return ca * __ldcg(Z + q) + cb * __ldcg(V1 + q) + cc * __ldcg(V2 + q);
+}
+
 // Runs phipm for one species; returns false if the kernel must stop.
 // Two partial-sum buffers used alternately: between two reductions that use
 // the same buffer every CTA has passed a barrier after reading it.
@@ -240,30 +248,41 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
     }
     if (!grid_barrier(a.st, bar, 10)) return false;
     // w_2 = A w_1 + v_2 -> V_0 (unnormalised)
-    {
-      Acc<T> acc;
-      for (long long k = gtid; k < ncomp; k += gthreads) {
-        const long long p = __ldg(S.idx + k);
-        T aw = stencil<T, N>(S.W1g, p, g, diag_of<T>(S, (int)k), S.beta_field, bc, cfac);
-        T w2 = aw + __ldcg(S.V2c + k);
-        S.V[p] = w2;
-        acc.add(w2, w2);
-      }
-      double v[1] = {acc.value()};
-      pb = part_buf(a.part, red);
-      block_partials<1>(v, pb);
+    for (long long k = gtid; k < ncomp; k += gthreads) {
+      const long long p = __ldg(S.idx + k);
+      T aw = stencil<T, N>(S.W1g, p, g, diag_of<T>(S, (int)k), S.beta_field, bc, cfac);
+      S.V[p] = aw + __ldcg(S.V2c + k);
     }
     if (!grid_barrier(a.st, bar, 11)) return false;
+    // P_0: Z_0 = A V_0, |V_0|^2, <Z_0, V_0>
     {
-      double tot[1];
-      grid_totals<1>(pb, tot);
+      Acc<T> d1, d2;
+      for (long long k = gtid; k < ncomp; k += gthreads) {
+        const long long p = __ldg(S.idx + k);
+        const T v = __ldcg(S.V + p);
+        const T z = stencil<T, N>(S.V, p, g, diag_of<T>(S, (int)k), S.beta_field, bc, cfac);
+        S.Z[0][p] = z;
+        d1.add(v, v);
+        d2.add(z, v);
+      }
+      double v[2] = {d1.value(), d2.value()};
+      pb = part_buf(a.part, red);
+      block_partials<2>(v, pb);
+    }
+    if (!grid_barrier(a.st, bar, 12)) return false;
+    {
+      double tot[2];
+      grid_totals<2>(pb, tot);
       if (threadIdx.x == 0) {
         c.beta = sqrt(tot[0]);
-        if (!isfinite(c.beta)) {
+        if (!isfinite(c.beta) || !isfinite(tot[1])) {
           atomicOr(&a.st->err, ERRF_NONFINITE);
           c.abort = 1;
         }
-        c.scale[0] = c.beta > 0.0 ? 1.0 / c.beta : 0.0;
+        const double s0 = c.beta > 0.0 ? 1.0 / c.beta : 0.0;
+        c.scale[0] = s0;
+        c.alpha[0] = tot[1] * s0 * s0;
+        c.up[0] = 0.0;
         c.m = 0;
         c.accepted = 0;
         c.breakdown = 0;
@@ -272,70 +291,75 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
       if (c.abort) return false;
     }
     if (c.beta > 0.0) {
-      for (int j = 0; j < m_max; ++j) {
-        const T sj = (T)c.scale[j];
-        const T sjm1 = j > 0 ? (T)c.scale[j - 1] : T(0);
-        const T* Vj = S.V + (long long)j * vs;
-        const T* Vjm1 = S.V + (long long)(j > 0 ? j - 1 : 0) * vs;
-        T* Vj1 = S.V + (long long)(j + 1) * vs;
-        // z = A v_j, <z, v_j>, <z, v_{j-1}>
+      // Pass P_j (one grid barrier each) rebuilds
+      //   w_j = z_{j-1} - h_{j-1,j-1} v_{j-1} - h_{j-2,j-1} v_{j-2}
+      // at every stencil point from Z_{j-1} = A V_{j-1}, V_{j-1}, V_{j-2}
+      // (all unnormalised), stores V_j = w_j and Z_j = A w_j, and sums
+      // |w_j|^2, <A w_j, w_j>, <A w_j, V_{j-1}>.  After the barrier:
+      //   h_{j,j-1} = |w_j|, h_jj = <A w_j, w_j>/|w_j|^2,
+      //   h_{j-1,j} = <A w_j, V_{j-1}> / (|w_j| |V_{j-1}|),
+      // the same classical Gram-Schmidt coefficients as z = A v_j,
+      // <z, v_j>, <z, v_{j-1}>, with the normalisation deferred.
+      for (int j = 1; j <= m_max; ++j) {
+        const T ca = (T)c.scale[j - 1];                       // coefficient of Z_{j-1}
+        const T cb = (T)(-c.alpha[j - 1] * c.scale[j - 1]);    // of V_{j-1}
+        const T cc = j >= 2 ? (T)(-c.up[j - 1] * c.scale[j - 2]) : T(0);  // of V_{j-2}
+        const T* Zp = S.Z[(j - 1) & 1];
+        T* Zn = S.Z[j & 1];
+        const T* V1 = S.V + (long long)(j - 1) * vs;
+        const T* V2 = S.V + (long long)(j >= 2 ? j - 2 : 0) * vs;
+        T* Vj = S.V + (long long)j * vs;
         {
-          Acc<T> da, db;
+          Acc<T> d1, d2, d3;
           for (long long k = gtid; k < ncomp; k += gthreads) {
             const long long p = __ldg(S.idx + k);
-            T z = stencil<T, N>(Vj, p, g, diag_of<T>(S, (int)k), S.beta_field, bc, cfac) * sj;
-            T vj = __ldcg(Vj + p) * sj;
-            T vjm1 = j > 0 ? __ldcg(Vjm1 + p) * sjm1 : T(0);
-            S.Zc[k] = z;
-            da.add(z, vj);
-            db.add(z, vjm1);
+            const T w = wval<T>(Zp, V1, V2, p, ca, cb, cc);
+            const T v1 = __ldcg(V1 + p);
+            T s = T(0);
+            const double* bf = S.beta_field;
+            if (bf == nullptr) {
+#pragma unroll
+              for (int d = 0; d < N; ++d)
+                s += wval<T>(Zp, V1, V2, p - g.stride[d], ca, cb, cc) + wval<T>(Zp, V1, V2, p + g.stride[d], ca, cb, cc);
+              s = bc * s;
+            } else {
+              const double bp = __ldg(bf + p);
+#pragma unroll
+              for (int d = 0; d < N; ++d) {
+                const long long st = g.stride[d];
+                s += T(0.5 * (bp + __ldg(bf + p - st))) * wval<T>(Zp, V1, V2, p - st, ca, cb, cc);
+                s += T(0.5 * (bp + __ldg(bf + p + st))) * wval<T>(Zp, V1, V2, p + st, ca, cb, cc);
+              }
+            }
+            const T z = cfac * (s - diag_of<T>(S, (int)k) * w);
+            Vj[p] = w;
+            Zn[p] = z;
+            d1.add(w, w);
+            d2.add(z, w);
+            d3.add(z, v1);
           }
-          double v[2] = {da.value(), db.value()};
+          double v[3] = {d1.value(), d2.value(), d3.value()};
           pb = part_buf(a.part, red);
-      block_partials<2>(v, pb);
-        }
-        if (!grid_barrier(a.st, bar, 12)) return false;
-        {
-          double tot[2];
-          grid_totals<2>(pb, tot);
-          if (threadIdx.x == 0) {
-            c.alpha[j] = tot[0];
-            c.up[j] = j > 0 ? tot[1] : 0.0;
-          }
-          __syncthreads();
-        }
-        // z -= h_jj v_j + h_{j-1,j} v_{j-1};  V_{j+1} = z;  |z|^2
-        {
-          const T hjj = (T)c.alpha[j], hjm = (T)c.up[j];
-          Acc<T> dn;
-          for (long long k = gtid; k < ncomp; k += gthreads) {
-            const long long p = __ldg(S.idx + k);
-            T z = __ldcg(S.Zc + k);
-            T vj = __ldcg(Vj + p) * sj;
-            T vjm1 = j > 0 ? __ldcg(Vjm1 + p) * sjm1 : T(0);
-            T w = z - hjj * vj - hjm * vjm1;
-            Vj1[p] = w;
-            dn.add(w, w);
-          }
-          double v[1] = {dn.value()};
-          pb = part_buf(a.part, red);
-      block_partials<1>(v, pb);
+          block_partials<3>(v, pb);
         }
         if (!grid_barrier(a.st, bar, 13)) return false;
         {
-          double tot[1];
-          grid_totals<1>(pb, tot);
+          double tot[3];
+          grid_totals<3>(pb, tot);
           if (threadIdx.x == 0) {
             const double hn = sqrt(tot[0]);
-            if (!isfinite(hn)) {
+            if (!isfinite(hn) || !isfinite(tot[1]) || !isfinite(tot[2])) {
               atomicOr(&a.st->err, ERRF_NONFINITE);
               c.abort = 1;
             }
-            c.low[j] = hn;
+            c.low[j - 1] = hn;
             c.hn = hn;
-            c.m = j + 1;
+            c.m = j;
             c.breakdown = hn < BREAKDOWN_REL * anorm;
-            c.scale[j + 1] = c.breakdown ? 0.0 : 1.0 / hn;
+            const double sj = c.breakdown ? 0.0 : 1.0 / hn;
+            c.scale[j] = sj;
+            c.alpha[j] = tot[1] * sj * sj;
+            c.up[j] = tot[2] * sj * c.scale[j - 1];
           }
           __syncthreads();
           if (c.abort) return false;
@@ -413,11 +437,9 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         const int m = c.m;
         if (blockIdx.x == 0 && a.stats) {
           StatsDev* st = a.stats;
-          if (nsub < TRACE_MAX) {
+          if (nsub < TRACE_MAX) {  // the trace keeps the first TRACE_MAX substeps
             st->trace_m[sidx][nsub] = m;
             st->trace_tau[sidx][nsub] = c.tau;
-          } else {
-            atomicOr(&a.st->err, ERRF_CAPACITY);
           }
           st->rejections[sidx] += c.nrej;
           st->iters[sidx] += m;
@@ -527,10 +549,34 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
       const long long p = __ldg(S.idx + k);
       S.u[p] = __ldcg(S.Yc + k);
     }
-    for (long long p = gtid; p < g.size; p += gthreads) {
-      if ((__ldg(S.kind + p) & 3) != K_COMP) {
-        if (S.u[p] != 0.0) S.u[p] = 0.0;
-        if (a.mode == MODE_ETD2 && S.fvalid[p]) S.fvalid[p] = 0;
+    // 16 nodes per thread and iteration: one 16-byte load of kinds, the
+    // validity flags rewritten from them, unconditional zero stores for u.
+    const long long n16 = g.size >> 4;
+    const uint4* kind16 = reinterpret_cast<const uint4*>(S.kind);
+    uint4* valid16 = reinterpret_cast<uint4*>(S.fvalid);
+    for (long long c = gtid; c <= n16; c += gthreads) {
+      const long long base = c << 4;
+      if (c < n16) {
+        const uint4 kv = __ldg(kind16 + c);
+        const unsigned w[4] = {kv.x, kv.y, kv.z, kv.w};
+        unsigned fv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          fv[q] = 0;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const bool comp = ((w[q] >> (8 * b)) & 3u) == K_COMP;
+            if (comp) fv[q] |= 1u << (8 * b);
+            else S.u[base + 4 * q + b] = 0.0;
+          }
+        }
+        if (a.mode == MODE_ETD2) valid16[c] = make_uint4(fv[0], fv[1], fv[2], fv[3]);
+      } else {
+        for (long long p = base; p < g.size; ++p) {
+          const bool comp = (__ldg(S.kind + p) & 3) == K_COMP;
+          if (!comp) S.u[p] = 0.0;
+          if (a.mode == MODE_ETD2) S.fvalid[p] = comp ? 1 : 0;
+        }
       }
     }
   }

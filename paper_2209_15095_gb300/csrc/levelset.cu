@@ -66,6 +66,7 @@ LevelsetBufs levelset_carve(const GridDev& g, const std::function<char*(size_t)>
   b.cta_count = (int*)take(MAX_BLOCKS * sizeof(int));
   b.vmax = (double*)take(sizeof(double));
   b.nsub = (int*)take(sizeof(int));
+  b.info = (int*)take(8 * sizeof(int));
   b.nrm = (double*)take((size_t)g.ndim * G * sizeof(double));
   b.V = (double*)take(G * sizeof(double));
   b.S0 = (double*)take(G * sizeof(double));
@@ -163,7 +164,7 @@ struct LsCtx {
 // validity bits V0 (computational), V1, V2.  Then the ordered list of T3
 // nodes.  Returns false if the kernel must stop.
 template <int N>
-__device__ bool build_work_set(const LsArgs& a, LsCtx& c, bool with_valid) {
+__device__ bool build_work_set(const LsArgs& a, LsCtx& c, bool with_valid, int slot) {
   const GridDev& g = a.g;
   uint8_t* fl = a.b.flags;
   const double G = BAND * g.h;
@@ -226,14 +227,19 @@ __device__ bool build_work_set(const LsArgs& a, LsCtx& c, bool with_valid) {
       tot += v;
     }
     s_off = off;
-    if (blockIdx.x == 0) a.b.count[0] = tot;
+    if (blockIdx.x == 0) {
+      a.b.count[0] = tot;
+      a.b.info[slot] = tot;
+    }
   }
   __syncthreads();
   int run = s_off;
+  int tcnt = 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (long long base = c.chunk_lo; base < c.chunk_hi; base += blockDim.x) {
     const long long p = base + threadIdx.x;
     const bool f = p < c.chunk_hi && (fl[p] & F_T3);
+    if (f && (fl[p] & F_T)) ++tcnt;
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     const int before = __popc(bal & ((1u << lane) - 1u));
     if (lane == 0) s_w[wid] = __popc(bal);
@@ -255,6 +261,8 @@ __device__ bool build_work_set(const LsArgs& a, LsCtx& c, bool with_valid) {
     run += tot;
     __syncthreads();
   }
+  for (int o = 16; o > 0; o >>= 1) tcnt += __shfl_xor_sync(0xffffffffu, tcnt, o);
+  if (lane == 0 && tcnt) atomicAdd(&a.b.info[slot + 1], tcnt);
   return grid_barrier(a.st, c.bar, 25);
 }
 
@@ -306,7 +314,7 @@ __device__ void stage_init(const LsArgs& a) {
 template <int N>
 __device__ bool reinitialise(const LsArgs& a, LsCtx& c) {
   const GridDev& g = a.g;
-  if (!build_work_set<N>(a, c, false)) return false;
+  if (!build_work_set<N>(a, c, false, 3)) return false;
   const int n = __ldcg(a.b.count);
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gth = (long long)gridDim.x * blockDim.x;
   const double h = g.h;
@@ -343,6 +351,10 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
   const double inv_h = 1.0 / h;
   const double G = BAND * h;
 
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int i = 0; i < 8; ++i) a.b.info[i] = 0;
+    a.b.info[5] = a.reinit;
+  }
   if (a.mode == LS_PREPARE) {
     for (long long p = gtid; p < g.size; p += gth) a.phi[p] = fmin(fmax(a.phi[p], -G), G);
     if (!grid_barrier(a.st, c.bar, 50)) return;
@@ -351,7 +363,7 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
   }
 
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.b.vmax = 0.0;
-  if (!build_work_set<N>(a, c, true)) return;
+  if (!build_work_set<N>(a, c, true, 0)) return;
   const int n = __ldcg(a.b.count);
   const long long cap = g.size;
   double* const UNN[2] = {a.b.q[0], a.b.q[1]};
@@ -511,7 +523,10 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
       if (threadIdx.x == 0) atomicOr(&a.st->err, ERRF_NONFINITE);
       return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.b.nsub = nsub;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      *a.b.nsub = nsub;
+      a.b.info[2] = nsub;
+    }
     const double dts = a.dt / nsub;
     auto L = [&](const double* s, long long p, const int* ix, long long i) {
       return -__ldcg(a.b.V + i) * godunov<N>(g, s, p, ix, true);

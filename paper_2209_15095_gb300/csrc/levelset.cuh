@@ -14,6 +14,7 @@ struct LevelsetBufs {
   int* cta_count;   // per-CTA counts for the in-kernel compaction
   double* vmax;     // [0] max Stefan speed on the tube
   int* nsub;        // [0] advection substeps of the last call
+  int* info;        // last call: list and tube sizes, substeps (see levelset_last_stats)
   double* nrm;      // N x list capacity: unit normals (compact)
   double* V;        // list capacity: Stefan speed (compact)
   double* S0;       // list capacity: sign function of reinitialisation (compact)

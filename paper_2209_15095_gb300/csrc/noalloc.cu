@@ -107,7 +107,8 @@ extern "C" etd_status etd_phi_combination_noalloc(const etd_grid* grid, const do
   double* Yc = cv.take<double>(G);
   double* V1c = cv.take<double>(G);
   double* V2c = cv.take<double>(G);
-  double* Zc = cv.take<double>(G);
+  double* Z0 = cv.take<double>(G);
+  double* Z1 = cv.take<double>(G);
   const size_t used = (cv.off + 255) & ~size_t(255);
   if (used > NA_BYTES) return ETD_ERR_WORKSPACE;
 
@@ -164,7 +165,8 @@ extern "C" etd_status etd_phi_combination_noalloc(const etd_grid* grid, const do
   S.Yc = Yc;
   S.V1c = V1c;
   S.V2c = V2c;
-  S.Zc = Zc;
+  S.Z[0] = Z0;
+  S.Z[1] = Z1;
   a.given[0] = v0;
   a.given[1] = v1;
   a.given[2] = v2;

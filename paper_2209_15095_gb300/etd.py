@@ -88,6 +88,7 @@ def library():
         "levelset_prepare": (I, [P, P, I]),
         "etd_sync": (I, [P]),
         "etd_last_stats": (I, [P, ctypes.POINTER(StepStats)]),
+        "levelset_last_stats": (I, [P, ctypes.POINTER(I)]),
         "etd_read_domain": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), P, P, P, I]),
         "etd_last_error": (ctypes.c_char_p, [P]),
     }
@@ -204,6 +205,12 @@ class Context:
         st = StepStats()
         self._check(self.lib.etd_last_stats(self.ctx, ctypes.byref(st)))
         return st.as_dict(self.nspecies)
+
+    def levelset_last_stats(self):
+        info = (ctypes.c_int * 8)()
+        self._check(self.lib.levelset_last_stats(self.ctx, info))
+        return {"list": info[0], "tube": info[1], "nsub": info[2], "reinit_list": info[3], "reinit_tube": info[4],
+                "reinit": info[5]}
 
     def sync(self):
         self._check(self.lib.etd_sync(self.ctx))
