@@ -72,7 +72,8 @@ enum { ETD_PRECISION_FP64 = 0, ETD_PRECISION_MIXED = 1 };
  *               COMPETITION (species 0, 1) = (u(1-u-rp[0] v), rp[2] v (1-v-rp[1] u))
  *   mu[s]       Stefan coefficient of species s (boundary speed mu |grad u|)
  *   beta[s]     constant diffusion coefficient of species s, used when no
- *               beta field is given to etd_init_domain */
+ *               beta field is given to etd_init_domain
+ *   adjoint     1 to reserve the workspace of etd_adjoint_step (species 0) */
 typedef struct {
   int nspecies;
   int precision;
@@ -82,6 +83,7 @@ typedef struct {
   double rp[4];
   double mu[2];
   double beta[2];
+  int adjoint;
 } etd_params;
 
 #define ETD_TRACE_MAX 64
@@ -138,6 +140,39 @@ etd_status etd_step(etd_ctx* ctx, double dt, double* const* u, etd_step_stats* s
  * FP64 arrays; y is 0 off the computational set. */
 etd_status etd_phi_combination(etd_ctx* ctx, int species, double dt, const double* v0, const double* v1,
                                const double* v2, double* y, etd_step_stats* stats);
+
+/* Replace the reaction kind and parameters of the context (as in
+ * etd_params; rp: host, 4 doubles). */
+etd_status etd_set_reaction(etd_ctx* ctx, int reaction, const double* rp);
+
+/* One ETD2 step (Sec. 3.1) of `species` on its current domain from both
+ * time levels given explicitly (no state kept in the context):
+ *   u_out = phi_0(dt C) u_n + dt phi_1(dt C) F(u_n) + dt phi_2(dt C)(F(u_n) - F(u_nm1));
+ * pass u_nm1 = u_n for the first step.  u_n, u_nm1, u_out: device full-grid
+ * FP64, read at / written to the computational points, u_out = 0 elsewhere;
+ * u_out may alias neither input. */
+etd_status etd_step_explicit(etd_ctx* ctx, int species, double dt, const double* u_n, const double* u_nm1,
+                             double* u_out, etd_step_stats* stats);
+
+/* Adjoint of one etd_step_explicit step on a frozen domain (species 0; needs
+ * params->adjoint).  A = dt C is symmetric (Sec. 2), so with
+ * lambda = dL/du_{n+1} and Phi_k = phi_k(A) lambda (three Krylov evaluations):
+ *   lam  <- Phi_0 + dt F'(u_n)(Phi_1 + Phi_2) + acc        (dL/du_n)
+ *   acc  <- -dt F'(u_nm1) Phi_2                              (to dL/du_{n-1})
+ *   grad_params[0] += dt <Phi_1 + Phi_2, dF/dalpha(u_n)> - dt <Phi_2, dF/dalpha(u_nm1)>
+ *   grad_beta += int_0^1 d(mu(t)^T A y(t))/d beta dt,  mu(t) = e^{(1-t)A} lambda,
+ *                y(t) = phi_0(tA) u_n + phi_1(tA) t v_1 + phi_2(tA) t^2 v_2
+ * (the step is y(1) of y' = A y + v_1 + t v_2, Eq. 3.10; v_1 = dt F(u_n),
+ * v_2 = dt (F(u_n) - F(u_nm1))), by nquad-point Gauss-Legendre in t (2 Krylov
+ * evaluations per point) and the face contraction of the symmetric stencil
+ * (node field beta, face value the mean of the two nodes; ghost nodes
+ * included).  first = 1 for the first step, where u_nm1 = u_n and acc is
+ * folded into lam.  u_n, u_nm1 (in), lam, acc (in/out), grad_beta (accumulated):
+ * device full-grid FP64, zero off the computational set except grad_beta;
+ * grad_params: device, 1 double, accumulated (alpha of ETD_REACTION_LOGISTIC_AK).
+ * 1 <= nquad <= 32. */
+etd_status etd_adjoint_step(etd_ctx* ctx, int species, double dt, const double* u_n, const double* u_nm1, int first,
+                            double* lam, double* acc, double* grad_beta, double* grad_params, int nquad);
 
 /* y = dt C x on the computational points (Sec. 2 operator, matrix-free);
  * y is written at computational points only.  FP64. */

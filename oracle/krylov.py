@@ -21,7 +21,9 @@ The small functions come from the exponential of the augmented matrix
 error estimate is err = tau^{p+1} beta h_{m+1,m} |e_m^T phi_{p+1}(tau H_m) e_1|.
 Control: tau = 1 at the start of a call; the basis grows to m_max with a check
 every 5 vectors and at m_max; a check accepts when err <= tol tau |y(t_k)|_2
-(with |y| floored at 1e-300).  Happy breakdown (h_{j+1,j} < 1e-12 anorm)
+(|y| is replaced by max(|y(t_k)|, |v_1|, ..., |v_p|, 1e-300) so that a
+combination with v_0 = 0, a single phi_k acting on a vector, still has a
+nonzero scale).  Happy breakdown (h_{j+1,j} < 1e-12 anorm)
 accepts at once.  A failed check at m_max shrinks
 tau <- tau max(0.2, 0.9 (tol tau |y| / err)^{1/(m+1)}) reusing the basis,
 until accepted or tau < 1e-6 (error).  After acceptance
@@ -56,6 +58,7 @@ def phipm(apply_A, vs, tol, m_max, anorm, forced_trace=None, dot=None):
     p = len(vs) - 1
     assert p >= 1
     y = np.array(vs[0], dtype=np.float64, copy=True)
+    vscale = max(math.sqrt(dot(v, v)) for v in vs[1:])
     t = 0.0
     tau = 1.0
     trace = []
@@ -74,7 +77,7 @@ def phipm(apply_A, vs, tol, m_max, anorm, forced_trace=None, dot=None):
             for l in range(0, p - j + 1):
                 wj = wj + (t ** l / math.factorial(l)) * vs[j + l]
             w.append(wj)
-        ynorm = max(math.sqrt(dot(y, y)), 1e-300)
+        ynorm = max(math.sqrt(dot(y, y)), vscale, 1e-300)
         beta = math.sqrt(dot(w[p], w[p]))
         if beta == 0.0:
             y = sum((tau ** j / math.factorial(j)) * w[j] for j in range(p))

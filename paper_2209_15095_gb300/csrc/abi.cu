@@ -41,6 +41,9 @@ struct etd_ctx {
   int* tile_count = nullptr;
   SpeciesBufs sp[2];
   LevelsetBufs ls;
+  // adjoint (species 0): phi actions, quadrature vectors, face weights
+  double* adj[8] = {nullptr};
+  double* facew = nullptr;
   int nblocks = 0;
   bool fp32 = false;
   int last_nspecies = 0;
@@ -175,6 +178,14 @@ size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
   }
   LevelsetBufs lb = levelset_carve(g, [&](size_t bytes) { return cv.take<char>(bytes); });
   if (c) c->ls = lb;
+  if (p.adjoint) {
+    for (int i = 0; i < 8; ++i) {
+      double* b = cv.take<double>(G);
+      if (c) c->adj[i] = b;
+    }
+    double* fw = cv.take<double>(G * 2 * (size_t)g.ndim);
+    if (c) c->facew = fw;
+  }
   cv.off = (cv.off + 255) & ~size_t(255);
   return cv.off;
 }
@@ -273,6 +284,10 @@ etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int spec
     a.nspecies = 1;
     a.sp[0] = species_dev<T>(c, species, u[0]);
     for (int i = 0; i < 3; ++i) a.given[i] = given[i];
+  }
+  if (mode == MODE_EXPLICIT) {
+    a.reaction = c->par.reaction;
+    for (int i = 0; i < 4; ++i) a.rp[i] = c->par.rp[i];
   }
   a.part = c->part;
   a.st = c->st;
@@ -376,6 +391,7 @@ etd_status etd_init_domain(etd_ctx* c, int species, const double* phi, const dou
   ma.beta_c = c->par.beta[species];
   ma.diag = b.diag;
   ma.diagf = b.diagf;
+  ma.facew = species == 0 ? c->facew : nullptr;
   ma.gersh = &c->st->gersh[species];
   ma.st = c->st;
   cudaError_t e = launch_init_domain(ca, ma, c->tile_count, b.ncomp, c->stream);
@@ -405,6 +421,122 @@ etd_status etd_phi_combination(etd_ctx* c, int species, double dt, const double*
   double* out[1] = {y};
   return c->fp32 ? run_phipm<float>(c, MODE_GIVEN, dt, out, species, given, stats)
                  : run_phipm<double>(c, MODE_GIVEN, dt, out, species, given, stats);
+}
+
+etd_status etd_set_reaction(etd_ctx* c, int reaction, const double* rp) {
+  if (!c) return ETD_ERR_ARG;
+  if (reaction < 0 || reaction > 3 || !rp) return fail(c, ETD_ERR_ARG, "bad reaction");
+  if (reaction == ETD_REACTION_COMPETITION && c->par.nspecies != 2) return fail(c, ETD_ERR_ARG, "competition needs 2 species");
+  c->par.reaction = reaction;
+  for (int i = 0; i < 4; ++i) c->par.rp[i] = rp[i];
+  return ETD_OK;
+}
+
+etd_status etd_step_explicit(etd_ctx* c, int species, double dt, const double* u_n, const double* u_nm1,
+                             double* u_out, etd_step_stats* stats) {
+  if (!c) return ETD_ERR_ARG;
+  if (species < 0 || species >= c->par.nspecies || !u_n || !u_nm1 || !u_out || !(dt > 0.0) || u_out == u_n ||
+      u_out == u_nm1)
+    return fail(c, ETD_ERR_ARG, "bad arguments");
+  if (c->par.reaction == ETD_REACTION_COMPETITION) return fail(c, ETD_ERR_ARG, "explicit step is single-species");
+  if (!c->sp[species].ready) return fail(c, ETD_ERR_ARG, "etd_init_domain not called");
+  const double* given[3] = {u_n, u_nm1, nullptr};
+  double* out[1] = {u_out};
+  return c->fp32 ? run_phipm<float>(c, MODE_EXPLICIT, dt, out, species, given, stats)
+                 : run_phipm<double>(c, MODE_EXPLICIT, dt, out, species, given, stats);
+}
+
+static void gauss_legendre01(int n, double* t, double* w) {
+  // roots of P_n by Newton from the Chebyshev-like initial guesses
+  for (int i = 0; i < n; ++i) {
+    double x = cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+      const double dx = p1 / dp;
+      x -= dx;
+      if (fabs(dx) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+    }
+    t[i] = 0.5 * (x + 1.0);
+    w[i] = 1.0 / ((1.0 - x * x) * dp * dp);  // half of the [-1, 1] weight
+  }
+}
+
+etd_status etd_adjoint_step(etd_ctx* c, int species, double dt, const double* u_n, const double* u_nm1, int first,
+                            double* lam, double* acc, double* grad_beta, double* grad_params, int nquad) {
+  if (!c) return ETD_ERR_ARG;
+  if (!c->par.adjoint || !c->facew) return fail(c, ETD_ERR_ARG, "context created without params.adjoint");
+  if (species != 0 || !u_n || !u_nm1 || !lam || !acc || !grad_beta || !grad_params || !(dt > 0.0) || nquad < 1 ||
+      nquad > 32)
+    return fail(c, ETD_ERR_ARG, "bad arguments");
+  if (c->par.reaction == ETD_REACTION_COMPETITION) return fail(c, ETD_ERR_ARG, "adjoint is single-species");
+  if (!c->sp[0].ready) return fail(c, ETD_ERR_ARG, "etd_init_domain not called");
+  double* P0 = c->adj[0];
+  double* P1 = c->adj[1];
+  double* P2 = c->adj[2];
+  double* B1 = c->adj[3];
+  double* B2 = c->adj[4];
+  double* Yq = c->adj[5];
+  double* Mu = c->adj[6];
+  const double* Zero = c->adj[7];  // never written: zero since etd_create
+  auto phi = [&](double s, const double* v0, const double* v1, const double* v2, double* out) {
+    const double* given[3] = {v0, v1, v2};
+    double* o[1] = {out};
+    return c->fp32 ? run_phipm<float>(c, MODE_GIVEN, s, o, 0, given, nullptr)
+                   : run_phipm<double>(c, MODE_GIVEN, s, o, 0, given, nullptr);
+  };
+  etd_status rs;
+  if ((rs = phi(dt, lam, Zero, Zero, P0)) != ETD_OK) return rs;
+  if ((rs = phi(dt, Zero, lam, Zero, P1)) != ETD_OK) return rs;
+  if ((rs = phi(dt, Zero, Zero, lam, P2)) != ETD_OK) return rs;
+  AdjointArgs a;
+  memset(&a, 0, sizeof(a));
+  a.g = c->g;
+  a.idx = c->sp[0].idx;
+  a.ncomp = c->sp[0].ncomp;
+  a.kind = c->sp[0].kind;
+  a.facew = c->facew;
+  a.reaction = c->par.reaction;
+  for (int i = 0; i < 4; ++i) a.rp[i] = c->par.rp[i];
+  a.dt = dt;
+  a.first = first ? 1 : 0;
+  a.un = u_n;
+  a.unm1 = u_nm1;
+  a.P0 = P0;
+  a.P1 = P1;
+  a.P2 = P2;
+  a.lam = lam;
+  a.acc = acc;
+  a.part = c->part;
+  a.grad_params = grad_params;
+  double t[32], w[32];
+  gauss_legendre01(nquad, t, w);
+  for (int i = 0; i < nquad; ++i) {
+    cudaError_t e = launch_adjoint_rhs(a, t[i], t[i] * t[i], B1, B2, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint rhs");
+    if ((rs = phi(t[i] * dt, u_n, B1, B2, Yq)) != ETD_OK) return rs;
+    if ((rs = phi((1.0 - t[i]) * dt, lam, Zero, Zero, Mu)) != ETD_OK) return rs;
+    e = launch_beta_contract(a, Mu, Yq, w[i] * dt, grad_beta, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "beta contraction");
+  }
+  cudaError_t e = launch_adjoint_combine(a, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint combine");
+  return ETD_OK;
 }
 
 etd_status etd_apply_operator(etd_ctx* c, int species, double dt, const double* x, double* y) {

@@ -247,6 +247,7 @@ __global__ void __launch_bounds__(256) metadata_kernel(MetaArgs a) {
         const int iq = ip[d] + (si == 0 ? -1 : 1);
         const double bf = a.beta_field ? 0.5 * (bp + a.beta_field[q]) : a.beta_c;
         D = __dadd_rn(D, bf);
+        double gw = 0.0;  // 1 - w on a ghost face, 0 on a face to a computational point
         if ((a.kind[q] & 3) == K_COMP) {
           offsum += bf;
         } else if (iq <= 0 || iq >= g.n[d] - 1) {
@@ -265,7 +266,9 @@ __global__ void __launch_bounds__(256) metadata_kernel(MetaArgs a) {
           double wc = fmin(fmax(w, 0.0), 1.0);
           if (!(wc == w)) ++nclamp;
           D = __dsub_rn(D, __dmul_rn(bf, wc));
+          gw = 1.0 - wc;
         }
+        if (a.facew) a.facew[(long long)k * (2 * N) + 2 * d + si] = gw;
       }
     }
     a.diag[k] = D;

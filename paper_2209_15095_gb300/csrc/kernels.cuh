@@ -30,6 +30,7 @@ struct MetaArgs {
   double beta_c;
   double* diag;
   float* diagf;  // nullptr unless FP32 vectors are in use
+  double* facew; // nullptr, or per point and face: 1 - w on ghost faces, 0 otherwise
   double* gersh;
   DevStatus* st;
 };
@@ -78,8 +79,10 @@ struct SpeciesDev {
 
 // mode of the phi-combination kernel
 enum : int {
-  MODE_ETD2 = 0,   // v0 = u, v1 = dt F(u), v2 = dt (F(u) - F_prev); writes u
-  MODE_GIVEN = 1,  // v0, v1, v2 given on the grid (Yg/Yc preset by the host path); writes Yc
+  MODE_ETD2 = 0,      // v0 = u, v1 = dt F(u), v2 = dt (F(u) - F_prev); writes u
+  MODE_GIVEN = 1,     // v0, v1, v2 given on the grid; writes the output field
+  MODE_EXPLICIT = 2,  // given[0] = u_n, given[1] = u_{n-1}: v0 = u_n, v1 = dt F(u_n),
+                      // v2 = dt (F(u_n) - F(u_{n-1})); writes the output field
 };
 
 template <typename T>
@@ -117,5 +120,33 @@ struct ApplyArgs {
   double* y;
 };
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t stream);
+
+// ---------------------------------------------------------------- adjoint
+struct AdjointArgs {
+  GridDev g;
+  const int* idx;
+  const int* ncomp;
+  const uint8_t* kind;
+  const double* facew;
+  int reaction;
+  double rp[4];
+  double dt;
+  int first;
+  const double* un;
+  const double* unm1;
+  const double* P0;
+  const double* P1;
+  const double* P2;
+  double* lam;   // in: dL/du_{n+1}; out: dL/du_n
+  double* acc;   // in: contribution to dL/du_n from the later step; out: to dL/du_{n-1}
+  double* part;  // per-block partial sums of the alpha gradient
+  double* grad_params;
+};
+cudaError_t launch_adjoint_combine(const AdjointArgs& a, cudaStream_t stream);
+// v1 = dt F(u_n), v2 = dt (F(u_n) - F(u_{n-1})) scaled by (s1, s2) on the computational set
+cudaError_t launch_adjoint_rhs(const AdjointArgs& a, double s1, double s2, double* v1, double* v2, cudaStream_t stream);
+// grad_beta += coef * d(mu^T C y)/d beta (node field, face mean)
+cudaError_t launch_beta_contract(const AdjointArgs& a, const double* mu, const double* y, double coef,
+                                 double* grad_beta, cudaStream_t stream);
 
 }  // namespace etd

@@ -17,7 +17,8 @@
 //   IOM2: z = A v_j, h_jj = <z, v_j>, h_{j-1,j} = <z, v_{j-1}>,
 //         z -= h_jj v_j + h_{j-1,j} v_{j-1}, h_{j+1,j} = |z|
 //   check every 5 vectors and at m_max:
-//     err = tau^3 beta h_{m+1,m} |e_m^T phi_3(tau H_m) e_1| <= tol tau |y|
+//     err = tau^3 beta h_{m+1,m} |e_m^T phi_3(tau H_m) e_1| <= tol tau s,
+//     s = max(|y(t_k)|, |v_1|, |v_2|)
 //   on failure at m_max shrink tau <- tau max(0.2, 0.9 (tol tau |y| / err)^(1/(m+1)))
 //   y <- y + tau w_1 + tau^2 beta V_m phi_2(tau H_m) e_1
 //   tau_next = min(1 - t, tau min(2, 0.9 (tol tau |y| / err)^(1/(m+1))))
@@ -208,7 +209,7 @@ __device__ __forceinline__ double* part_buf(double* part, int& red) {
 
 template <typename T, int N>
 __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int sidx, Ctl& c, unsigned& bar,
-                              int& red, double ynorm2) {
+                              int& red, double ynorm2, double vscale) {
   const GridDev& g = a.g;
   const int ncomp = *S.ncomp;
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -222,7 +223,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   if (threadIdx.x == 0) {
     c.t = 0.0;
     c.tau = 1.0;
-    c.ynorm = fmax(sqrt(ynorm2), 1e-300);
+    c.ynorm = fmax(fmax(sqrt(ynorm2), vscale), 1e-300);
     c.abort = 0;
   }
   __syncthreads();
@@ -449,7 +450,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         else grow = fmin(2.0, 0.9 * pow(a.tol * c.tau * c.ynorm / c.err, 1.0 / (m + 1)));
         c.t = c.last ? 1.0 : c.t + c.tau;
         if (c.t < 1.0) c.tau = fmin(1.0 - c.t, c.tau * grow);
-        c.ynorm = fmax(sqrt(tot[0]), 1e-300);
+        c.ynorm = fmax(fmax(sqrt(tot[0]), vscale), 1e-300);
         if (!isfinite(c.ynorm)) {
           atomicOr(&a.st->err, ERRF_NONFINITE);
           c.abort = 1;
@@ -478,11 +479,11 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
   const long long gthreads = (long long)gridDim.x * blockDim.x;
   // ---- set-up: y = v_0, v_1, v_2 for every species (reads every species'
   // field before any is overwritten)
-  double yn[2] = {0.0, 0.0};
+  double sums[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
   for (int s = 0; s < a.nspecies; ++s) {
     const SpeciesDev<T>& S = a.sp[s];
     const int ncomp = *S.ncomp;
-    Acc<double> acc;
+    Acc<double> acc, acc1, acc2;
     for (long long k = gtid; k < ncomp; k += gthreads) {
       const long long p = __ldg(S.idx + k);
       double y, v1, v2;
@@ -490,6 +491,13 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
         y = a.given[0][p];
         v1 = a.given[1][p];
         v2 = a.given[2][p];
+      } else if (a.mode == MODE_EXPLICIT) {
+        const double u = a.given[0][p], um = a.given[1][p];
+        const double F = reaction(a.reaction, a.rp, 0, u, 0.0);
+        const double Fm = reaction(a.reaction, a.rp, 0, um, 0.0);
+        y = u;
+        v1 = a.dt * F;
+        v2 = a.dt * (F - Fm);
       } else {
         const double u = S.u[p];
         double other = 0.0;
@@ -508,16 +516,23 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
       S.V1c[k] = (T)v1;
       S.V2c[k] = (T)v2;
       acc.add(y, y);
+      acc1.add(v1, v1);
+      acc2.add(v2, v2);
     }
-    yn[s] = acc.value();
+    sums[s][0] = acc.value();
+    sums[s][1] = acc1.value();
+    sums[s][2] = acc2.value();
+  }
+  // |y(0)|^2, |v_1|^2, |v_2|^2 per species (one reduction each)
+  double tot[2][3];
+  for (int s = 0; s < a.nspecies; ++s) {
+    double v[3] = {sums[s][0], sums[s][1], sums[s][2]};
+    pb = part_buf(a.part, red);
+    block_partials<3>(v, pb);
+    if (!grid_barrier(a.st, bar, 1)) return;
+    grid_totals<3>(pb, tot[s]);
   }
   // F_{n-1} <- F_n after every species has read the fields
-  double v2p[2] = {yn[0], yn[1]};
-  pb = part_buf(a.part, red);
-      block_partials<2>(v2p, pb);
-  if (!grid_barrier(a.st, bar, 1)) return;
-  double tot[2];
-  grid_totals<2>(pb, tot);
   if (a.mode == MODE_ETD2) {
     for (int s = 0; s < a.nspecies; ++s) {
       const SpeciesDev<T>& S = a.sp[s];
@@ -538,7 +553,8 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
     }
   }
   for (int s = 0; s < a.nspecies; ++s) {
-    if (!phipm_species<T, N>(a, a.sp[s], s, c, bar, red, tot[s])) return;
+    const double vscale = fmax(sqrt(tot[s][1]), sqrt(tot[s][2]));
+    if (!phipm_species<T, N>(a, a.sp[s], s, c, bar, red, tot[s][0], vscale)) return;
   }
   if (!grid_barrier(a.st, bar, 2)) return;
   // ---- write back: new values at computational points, 0 elsewhere

@@ -43,7 +43,7 @@ class Grid(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("nspecies", ctypes.c_int), ("precision", ctypes.c_int), ("krylov_tol", ctypes.c_double),
                 ("m_max", ctypes.c_int), ("reaction", ctypes.c_int), ("rp", ctypes.c_double * 4),
-                ("mu", ctypes.c_double * 2), ("beta", ctypes.c_double * 2)]
+                ("mu", ctypes.c_double * 2), ("beta", ctypes.c_double * 2), ("adjoint", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
@@ -84,6 +84,9 @@ def library():
         "etd_step": (I, [P, D, ctypes.POINTER(P), ctypes.POINTER(StepStats)]),
         "etd_phi_combination": (I, [P, I, D, P, P, P, P, ctypes.POINTER(StepStats)]),
         "etd_apply_operator": (I, [P, I, D, P, P]),
+        "etd_set_reaction": (I, [P, I, ctypes.POINTER(D)]),
+        "etd_step_explicit": (I, [P, I, D, P, P, P, ctypes.POINTER(StepStats)]),
+        "etd_adjoint_step": (I, [P, I, D, P, P, I, P, P, P, P, I]),
         "levelset_advance": (I, [P, I, P, P, D, I]),
         "levelset_prepare": (I, [P, P, I]),
         "etd_sync": (I, [P]),
@@ -118,7 +121,7 @@ class Context:
     """One library context: grid, parameters, workspace and stream."""
 
     def __init__(self, n, lo, hi, nspecies=1, precision="fp64", tol=1e-8, m_max=30, reaction="logistic",
-                 rparams=(), mu=(1.0, 1.0), beta=(1.0, 1.0), device=None):
+                 rparams=(), mu=(1.0, 1.0), beta=(1.0, 1.0), device=None, adjoint=False):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
         self.lib = library()
@@ -140,6 +143,7 @@ class Context:
         p.reaction = REACTIONS[reaction]
         for i, v in enumerate(rparams):
             p.rp[i] = float(v)
+        p.adjoint = 1 if adjoint else 0
         for s in range(2):
             p.mu[s] = float(mu[s] if s < len(mu) else mu[-1])
             p.beta[s] = float(beta[s] if s < len(beta) else beta[-1])
@@ -158,6 +162,7 @@ class Context:
             raise EtdError(rc, "etd_create failed")
         self.ctx = ctx
         self._beta_fields = [None, None]
+        self.adjoint_enabled = bool(adjoint)
 
     def __del__(self):
         ctx = getattr(self, "ctx", None)
@@ -189,6 +194,27 @@ class Context:
                                                  _ptr(y, self.n, "y"),
                                                  ctypes.byref(st) if st is not None else None))
         return st.as_dict(1)[0] if st is not None else None
+
+    def set_reaction(self, reaction, rparams):
+        rp = (ctypes.c_double * 4)(*([float(v) for v in rparams] + [0.0] * (4 - len(rparams))))
+        self._check(self.lib.etd_set_reaction(self.ctx, REACTIONS[reaction], rp))
+
+    def step_explicit(self, species, dt, u_n, u_nm1, u_out, stats=False):
+        st = StepStats() if stats else None
+        self._check(self.lib.etd_step_explicit(self.ctx, species, float(dt), _ptr(u_n, self.n, "u_n"),
+                                               _ptr(u_nm1, self.n, "u_nm1"), _ptr(u_out, self.n, "u_out"),
+                                               ctypes.byref(st) if st is not None else None))
+        return st.as_dict(1)[0] if st is not None else None
+
+    def adjoint_step(self, species, dt, u_n, u_nm1, first, lam, acc, grad_beta, grad_params, nquad=8):
+        gp = grad_params
+        if not (isinstance(gp, torch.Tensor) and gp.is_cuda and gp.dtype == torch.float64 and gp.numel() >= 1):
+            raise TypeError("grad_params must be a CUDA float64 tensor")
+        self._check(self.lib.etd_adjoint_step(self.ctx, species, float(dt), _ptr(u_n, self.n, "u_n"),
+                                              _ptr(u_nm1, self.n, "u_nm1"), 1 if first else 0,
+                                              _ptr(lam, self.n, "lam"), _ptr(acc, self.n, "acc"),
+                                              _ptr(grad_beta, self.n, "grad_beta"), ctypes.c_void_p(gp.data_ptr()),
+                                              int(nquad)))
 
     def apply_operator(self, species, dt, x, y):
         self._check(self.lib.etd_apply_operator(self.ctx, species, float(dt), _ptr(x, self.n, "x"),
