@@ -256,3 +256,43 @@ def test_free_boundary_disc_multistep(lib):
     near = np.abs(ph_o) < g.h
     assert np.max(np.abs(ph_g - ph_o)[near]) <= 1e-2 * g.h
     assert np.max(np.abs(u_g - u_o)) <= 1e-8 * np.max(np.abs(u_o))
+
+
+def test_two_species_competition_multistep(lib):
+    """Row a9: two species with their own level sets, coupled through the
+    competition reaction, several free-boundary steps against the oracle."""
+    from oracle.freeboundary import FreeBoundary, Species
+
+    n = 36
+    g = Grid((n,) * 3, (-3.0,) * 3, (3.0,) * 3)
+    x, y, z = g.coords()
+    phis, us = [], []
+    for cx in (-1.0, 1.0):
+        r = np.sqrt((x - cx) ** 2 + y * y + z * z)
+        phis.append(r - 0.9)
+        us.append(np.where(r < 0.9, np.cos(np.pi * r / 1.8), 0.0))
+    beta, mu, rp = (1.0, 0.5), (1.0, 0.8), (0.5, 0.8, 1.2)
+    dt, tol, m_max, nsteps = 5e-3, 1e-8, 30, 6
+    fb = FreeBoundary(g, [Species(phis[s], us[s], beta[s], mu[s]) for s in range(2)], "competition", rp, tol, m_max,
+                      reinit_every=5)
+    ctx = lib.Context(g.n, g.lo, g.hi, nspecies=2, precision="fp64", tol=tol, m_max=m_max, reaction="competition",
+                      rparams=rp, mu=mu, beta=beta)
+    dph = [_dev(p) for p in phis]
+    du = [_dev(np.where(phis[s] < 0, us[s], 0.0)) for s in range(2)]
+    for s in range(2):
+        ctx.levelset_prepare(dph[s], False)
+        ctx.init_domain(s, dph[s])
+    for k in range(nsteps):
+        fb.step(dt)
+        for s in range(2):
+            ctx.levelset_advance(s, dph[s], du[s], dt, (k + 1) % 5 == 0)
+        for s in range(2):
+            ctx.init_domain(s, dph[s])
+        ctx.step(dt, du)
+    ctx.sync()
+    for s in range(2):
+        ph_g, u_g = dph[s].cpu().numpy(), du[s].cpu().numpy()
+        ph_o, u_o = fb.sp[s].phi, fb.sp[s].u
+        assert ((ph_g < 0) == (ph_o < 0)).all()
+        assert np.max(np.abs(ph_g - ph_o)) <= 1e-9 * g.h
+        assert np.max(np.abs(u_g - u_o)) <= 1e-8 * np.max(np.abs(u_o))
