@@ -595,7 +595,7 @@ etd_status levelset_advance(etd_ctx* c, int species, double* phi, double* u, dou
     return fail(c, ETD_ERR_ARG, "bad arguments");
   if (!c->sp[species].ready) return fail(c, ETD_ERR_ARG, "etd_init_domain not called");
   cudaError_t e = launch_levelset_advance(c->g, c->ls, c->st, c->sp[species].kind, phi, u, dt, c->par.mu[species],
-                                          do_reinit != 0, c->stream);
+                                          do_reinit != 0, c->fp32, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "levelset launch");
   return ETD_OK;
 }
@@ -611,7 +611,7 @@ etd_status levelset_last_stats(etd_ctx* c, int* info) {
 etd_status levelset_prepare(etd_ctx* c, double* phi, int do_reinit) {
   if (!c) return ETD_ERR_ARG;
   if (!phi) return fail(c, ETD_ERR_ARG, "phi is NULL");
-  cudaError_t e = launch_levelset_prepare(c->g, c->ls, c->st, phi, do_reinit != 0, c->stream);
+  cudaError_t e = launch_levelset_prepare(c->g, c->ls, c->st, phi, do_reinit != 0, c->fp32, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "levelset launch");
   return ETD_OK;
 }

@@ -54,6 +54,7 @@ struct LsArgs {
   double mu;
   int mode;
   int reinit;
+  int mixed;  // FP32 WENO/Godunov arithmetic away from the interface
 };
 
 LevelsetBufs levelset_carve(const GridDev& g, const std::function<char*(size_t)>& take) {
@@ -108,49 +109,53 @@ __device__ __forceinline__ long long nbr(const GridDev& g, long long p, const in
 // the nonlinear weights share one division: with d_k = (eps + s_k)^2,
 //   sum_k (g_k/d_k) p_k / sum_k (g_k/d_k)
 //     = (g1 d2 d3 p1 + g2 d1 d3 p2 + g3 d1 d2 p3) / (g1 d2 d3 + g2 d1 d3 + g3 d1 d2).
-__device__ __forceinline__ double weno5(double v1, double v2, double v3, double v4, double v5) {
-  constexpr double sixth = 1.0 / 6.0;
-  const double p1 = (2.0 * v1 - 7.0 * v2 + 11.0 * v3) * sixth;
-  const double p2 = (-v2 + 5.0 * v3 + 2.0 * v4) * sixth;
-  const double p3 = (2.0 * v3 + 5.0 * v4 - v5) * sixth;
-  const double a = v1 - 2.0 * v2 + v3, b = v1 - 4.0 * v2 + 3.0 * v3;
-  const double c = v2 - 2.0 * v3 + v4, d = v2 - v4;
-  const double e = v3 - 2.0 * v4 + v5, f = 3.0 * v3 - 4.0 * v4 + v5;
-  const double s1 = 13.0 / 12.0 * (a * a) + 0.25 * (b * b);
-  const double s2 = 13.0 / 12.0 * (c * c) + 0.25 * (d * d);
-  const double s3 = 13.0 / 12.0 * (e * e) + 0.25 * (f * f);
-  const double e1 = WENO_EPS + s1, e2 = WENO_EPS + s2, e3 = WENO_EPS + s3;
-  const double d1 = e1 * e1, d2 = e2 * e2, d3 = e3 * e3;
-  const double w1 = 0.1 * (d2 * d3), w2 = 0.6 * (d1 * d3), w3 = 0.3 * (d1 * d2);
+template <typename C>
+__device__ __forceinline__ C weno5(C v1, C v2, C v3, C v4, C v5) {
+  constexpr C sixth = C(1.0 / 6.0);
+  const C p1 = (C(2) * v1 - C(7) * v2 + C(11) * v3) * sixth;
+  const C p2 = (-v2 + C(5) * v3 + C(2) * v4) * sixth;
+  const C p3 = (C(2) * v3 + C(5) * v4 - v5) * sixth;
+  const C a = v1 - C(2) * v2 + v3, b = v1 - C(4) * v2 + C(3) * v3;
+  const C c = v2 - C(2) * v3 + v4, d = v2 - v4;
+  const C e = v3 - C(2) * v4 + v5, f = C(3) * v3 - C(4) * v4 + v5;
+  const C s1 = C(13.0 / 12.0) * (a * a) + C(0.25) * (b * b);
+  const C s2 = C(13.0 / 12.0) * (c * c) + C(0.25) * (d * d);
+  const C s3 = C(13.0 / 12.0) * (e * e) + C(0.25) * (f * f);
+  const C e1 = C(WENO_EPS) + s1, e2 = C(WENO_EPS) + s2, e3 = C(WENO_EPS) + s3;
+  const C d1 = e1 * e1, d2 = e2 * e2, d3 = e3 * e3;
+  const C w1 = C(0.1) * (d2 * d3), w2 = C(0.6) * (d1 * d3), w3 = C(0.3) * (d1 * d2);
   return (w1 * p1 + w2 * p2 + w3 * p3) / (w1 + w2 + w3);
 }
 
 // Godunov |grad phi| at node p from array src; positive: outward motion.
-template <int N>
-__device__ double godunov(const GridDev& g, const double* __restrict__ src, long long p, const int* ix, bool positive) {
+// The divided differences are formed in FP64; C is the type of the WENO5
+// and Godunov arithmetic (double, or float on the FP32-mixed path).
+template <typename C, int N>
+__device__ double godunov(const GridDev& g, const double* __restrict__ src, long long p, const int* ix,
+                          bool positive) {
   const double inv_h = 1.0 / g.h;
-  double acc = 0.0;
+  C acc = C(0);
 #pragma unroll
   for (int d = 0; d < N; ++d) {
     double f[7];
 #pragma unroll
     for (int k = -3; k <= 3; ++k) f[k + 3] = __ldcg(src + nbr(g, p, ix, d, k));
-    double q[6];  // q[k+2] = (f(i+k) - f(i+k-1)) / h, k = -2..3
+    C q[6];  // q[k+2] = (f(i+k) - f(i+k-1)) / h, k = -2..3
 #pragma unroll
-    for (int k = -2; k <= 3; ++k) q[k + 2] = (f[k + 3] - f[k + 2]) * inv_h;
-    const double dm = weno5(q[0], q[1], q[2], q[3], q[4]);
-    const double dp = weno5(q[5], q[4], q[3], q[2], q[1]);
-    double t;
+    for (int k = -2; k <= 3; ++k) q[k + 2] = C((f[k + 3] - f[k + 2]) * inv_h);
+    const C dm = weno5<C>(q[0], q[1], q[2], q[3], q[4]);
+    const C dp = weno5<C>(q[5], q[4], q[3], q[2], q[1]);
+    C t;
     if (positive) {
-      const double x = fmax(dm, 0.0), y = fmin(dp, 0.0);
+      const C x = dm > C(0) ? dm : C(0), y = dp < C(0) ? dp : C(0);
       t = fmax(x * x, y * y);
     } else {
-      const double x = fmin(dm, 0.0), y = fmax(dp, 0.0);
+      const C x = dm < C(0) ? dm : C(0), y = dp > C(0) ? dp : C(0);
       t = fmax(x * x, y * y);
     }
     acc += t;
   }
-  return sqrt(acc);
+  return (double)sqrt(acc);
 }
 
 // ------------------------------------------------------------ work lists
@@ -327,9 +332,14 @@ __device__ bool reinitialise(const LsArgs& a, LsCtx& c) {
   if (!grid_barrier(a.st, c.bar, 40)) return false;
   const int K = (int)ceil(12.0 * sqrt((double)N));
   const double dtau = 0.5 * h / sqrt((double)N);
+  // mixed path: FP64 within 3h of the interface (|phi_0| < 3h, i.e.
+  // |S| < 3/sqrt(10)), FP32 WENO/Godunov arithmetic further out
+  const double near_s = 3.0 / sqrt(10.0);
   auto L = [&](const double* src, long long p, const int* ix, long long i) {
     const double S = __ldcg(a.b.S0 + i);
-    return -S * (godunov<N>(g, src, p, ix, S > 0.0) - 1.0);
+    const double gr = (a.mixed && fabs(S) >= near_s) ? godunov<float, N>(g, src, p, ix, S > 0.0)
+                                                     : godunov<double, N>(g, src, p, ix, S > 0.0);
+    return -S * (gr - 1.0);
   };
   for (int it = 0; it < K; ++it) {
     if (!rk3<N>(a, c, dtau, it == K - 1, L)) return false;
@@ -416,39 +426,83 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
     UNN[0][p] = unn;
   }
   if (!grid_barrier(a.st, c.bar, 52)) return;
-  // three extrapolation sweeps
+  // three extrapolation sweeps.  Values off the sweep region never change,
+  // so both ping-pong buffers get them once; each pass then touches only the
+  // region.  Each thread keeps the state of its first SW_CACHE list entries
+  // (node, region flag, normal, own value, source) in registers.
   const int K = (int)ceil(12.0 * sqrt((double)N));
   const double dtau = h / (2.0 * sqrt((double)N));
   const uint8_t vbits[3] = {F_V2, F_V1, F_V0};
   double* const* bufs[3] = {UNN, UN, U};
   const double* src = nullptr;
+  constexpr int SW_CACHE = 2;
   for (int sw = 0; sw < 3; ++sw) {
     double* const* B = bufs[sw];
+    for (long long i = gtid; i < n; i += gth) {
+      const long long p = __ldcg(a.b.list + i);
+      B[1][p] = __ldcg(B[0] + p);
+    }
+    long long cp[SW_CACHE];
+    bool creg[SW_CACHE];
+    double cq[SW_CACHE], cs[SW_CACHE], cn[SW_CACHE][N];
+    int cix[SW_CACHE][N];
+#pragma unroll
+    for (int r = 0; r < SW_CACHE; ++r) {
+      const long long i = gtid + r * gth;
+      creg[r] = false;
+      cp[r] = 0;
+      cq[r] = cs[r] = 0.0;
+      if (i < n) {
+        const long long p = __ldcg(a.b.list + i);
+        const uint8_t f = a.b.flags[p];
+        cp[r] = p;
+        creg[r] = (f & F_T) && !(f & vbits[sw]);
+        cq[r] = __ldcg(B[0] + p);
+        cs[r] = src ? __ldcg(src + p) : 0.0;
+        unpack<N>(a.b.lcoord[i], cix[r]);
+#pragma unroll
+        for (int d = 0; d < N; ++d) cn[r][d] = __ldcg(a.b.nrm + d * cap + i);
+      }
+    }
+    if (!grid_barrier(a.st, c.bar, 53)) return;
     int cur = 0;
     for (int it = 0; it < K; ++it) {
       const double* qc = B[cur];
       double* qn = B[cur ^ 1];
-      for (long long i = gtid; i < n; i += gth) {
+#pragma unroll
+      for (int r = 0; r < SW_CACHE; ++r) {
+        if (!creg[r]) continue;
+        const long long p = cp[r];
+        double acc = 0.0;
+#pragma unroll
+        for (int d = 0; d < N; ++d) {
+          const double nd = cn[r][d];
+          double dd;
+          if (nd > 0.0) dd = (cq[r] - __ldcg(qc + nbr(g, p, cix[r], d, -1))) * inv_h;
+          else dd = (__ldcg(qc + nbr(g, p, cix[r], d, 1)) - cq[r]) * inv_h;
+          acc += nd * dd;
+        }
+        cq[r] = cq[r] - dtau * (acc - cs[r]);
+        qn[p] = cq[r];
+      }
+      for (long long i = gtid + SW_CACHE * gth; i < n; i += gth) {
         const long long p = __ldcg(a.b.list + i);
         const uint8_t f = a.b.flags[p];
+        if (!((f & F_T) && !(f & vbits[sw]))) continue;
         const double q0 = __ldcg(qc + p);
-        if ((f & F_T) && !(f & vbits[sw])) {
-          int ix[N];
-          unpack<N>(a.b.lcoord[i], ix);
-          double acc = 0.0;
+        int ix[N];
+        unpack<N>(a.b.lcoord[i], ix);
+        double acc = 0.0;
 #pragma unroll
-          for (int d = 0; d < N; ++d) {
-            const double nd = __ldcg(a.b.nrm + d * cap + i);
-            double dd;
-            if (nd > 0.0) dd = (q0 - __ldcg(qc + nbr(g, p, ix, d, -1))) * inv_h;
-            else dd = (__ldcg(qc + nbr(g, p, ix, d, 1)) - q0) * inv_h;
-            acc += nd * dd;
-          }
-          const double s = src ? __ldcg(src + p) : 0.0;
-          qn[p] = q0 - dtau * (acc - s);
-        } else {
-          qn[p] = q0;
+        for (int d = 0; d < N; ++d) {
+          const double nd = __ldcg(a.b.nrm + d * cap + i);
+          double dd;
+          if (nd > 0.0) dd = (q0 - __ldcg(qc + nbr(g, p, ix, d, -1))) * inv_h;
+          else dd = (__ldcg(qc + nbr(g, p, ix, d, 1)) - q0) * inv_h;
+          acc += nd * dd;
         }
+        const double sv = src ? __ldcg(src + p) : 0.0;
+        qn[p] = q0 - dtau * (acc - sv);
       }
       if (!grid_barrier(a.st, c.bar, 53)) return;
       cur ^= 1;
@@ -529,7 +583,8 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
     }
     const double dts = a.dt / nsub;
     auto L = [&](const double* s, long long p, const int* ix, long long i) {
-      return -__ldcg(a.b.V + i) * godunov<N>(g, s, p, ix, true);
+      const double gr = a.mixed ? godunov<float, N>(g, s, p, ix, true) : godunov<double, N>(g, s, p, ix, true);
+      return -__ldcg(a.b.V + i) * gr;
     };
     for (int sub = 0; sub < nsub; ++sub) {
       if (!rk3<N>(a, c, dts, sub == nsub - 1, L)) return;
@@ -564,8 +619,10 @@ static cudaError_t launch(const LsArgs& a, cudaStream_t stream) {
 }
 
 cudaError_t launch_levelset_advance(const GridDev& g, const LevelsetBufs& b, DevStatus* st, const uint8_t* kind,
-                                    double* phi, double* u, double dt, double mu, bool reinit, cudaStream_t stream) {
+                                    double* phi, double* u, double dt, double mu, bool reinit, bool mixed,
+                                    cudaStream_t stream) {
   LsArgs a;
+  a.mixed = mixed ? 1 : 0;
   a.g = g;
   a.b = b;
   a.st = st;
@@ -580,8 +637,9 @@ cudaError_t launch_levelset_advance(const GridDev& g, const LevelsetBufs& b, Dev
 }
 
 cudaError_t launch_levelset_prepare(const GridDev& g, const LevelsetBufs& b, DevStatus* st, double* phi, bool reinit,
-                                    cudaStream_t stream) {
+                                    bool mixed, cudaStream_t stream) {
   LsArgs a;
+  a.mixed = mixed ? 1 : 0;
   a.g = g;
   a.b = b;
   a.st = st;

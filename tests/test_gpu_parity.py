@@ -296,3 +296,26 @@ def test_two_species_competition_multistep(lib):
         assert ((ph_g < 0) == (ph_o < 0)).all()
         assert np.max(np.abs(ph_g - ph_o)) <= 1e-9 * g.h
         assert np.max(np.abs(u_g - u_o)) <= 1e-8 * np.max(np.abs(u_o))
+
+
+def test_levelset_step_mixed_precision(lib):
+    """FP32-mixed path: WENO5/Godunov arithmetic in FP32 except the
+    reinitialisation within 3h of the interface; against the FP64 oracle."""
+    g, ph0 = _shape_phi(3, 28, 3.0, "ellipsoid")
+    ph = levelset.reinit(levelset.clamp(ph0, g.h), g.h)
+    op = EBOperator(g, ph, 1.0)
+    x = g.coords()
+    r = np.sqrt(sum(c * c for c in x))
+    u = np.where(op.comp, np.cos(0.3 * r), 0.0)
+    ctx = _ctx(lib, g, precision="mixed", tol=1e-6, mu=(1.3,))
+    dph, du = _dev(ph), _dev(u)
+    ctx.init_domain(0, dph)
+    ph_o, ue_o, _ = levelset.levelset_advance(ph, u, op.comp, g, 0.02, 1.3, True)
+    ctx.levelset_advance(0, dph, du, 0.02, True)
+    ctx.sync()
+    ph_g = dph.cpu().numpy()
+    near = np.abs(ph_o) < 2 * g.h
+    assert ((ph_g < 0) == (ph_o < 0)).all()
+    assert np.max(np.abs(ph_g - ph_o)[near]) <= 1e-6 * g.h
+    assert np.max(np.abs(ph_g - ph_o)) <= 1e-4 * g.h
+    assert np.max(np.abs(du.cpu().numpy() - ue_o)) <= 1e-10 * np.max(np.abs(ue_o))
