@@ -61,7 +61,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Grid-wide barrier for a cooperative launch: a monotonically increasing
 // arrival counter (reset to 0 before the launch).  Barrier number `k`
 // (1-based, identical in every CTA) completes when the counter reaches
-// k * gridDim.x.  Every wait is bounded (~1 s of wall time); on timeout the
+// k * gridDim.x.  Ordering: __syncthreads orders the CTA's accesses before
+// thread 0's gpu-scope release add; the waiting thread's gpu-scope acquire
+// load and the following __syncthreads order them before every later access
+// of its CTA.  Every wait is bounded (~1 s of wall time); on timeout the
 // status word gets ERRF_TIMEOUT and the call returns false, after which the
 // kernel must return.
 constexpr unsigned long long BARRIER_LIMIT_NS = 1000000000ull;
@@ -72,7 +75,6 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned& k, int sit
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
     red_release_add_u32(&st->barrier, 1u);
     const unsigned target = k * gridDim.x;
     unsigned long long t0 = 0;
@@ -91,7 +93,6 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned& k, int sit
         if (*((volatile int*)&st->err) & ERRF_TIMEOUT) { ok = 0; break; }
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();

@@ -62,6 +62,7 @@ LevelsetBufs levelset_carve(const GridDev& g, const std::function<char*(size_t)>
   LevelsetBufs b;
   b.flags = (uint8_t*)take(G);
   b.list = (int*)take(G * sizeof(int));
+  b.slist = (int*)take(G * sizeof(int));
   b.lcoord = (ushort4*)take(G * sizeof(ushort4));
   b.count = (int*)take(4 * sizeof(int));
   b.cta_count = (int*)take(MAX_BLOCKS * sizeof(int));
@@ -273,20 +274,35 @@ __device__ bool build_work_set(const LsArgs& a, LsCtx& c, bool with_valid, int s
 
 // TVD-RK3 on the nodes of T (list order); L(src, p) supplied by the caller.
 // Stage values p1/p2 hold phi off T (copied when the work set is built).
+// The stage list holds the work-list positions of the update set T: entries
+// pushed to the front first, then those pushed to the back (read in that
+// order), so that warps see one kind of entry (FP64 or FP32 arithmetic).
+__device__ __forceinline__ void stage_push(const LsArgs& a, int i, bool front) {
+  if (front) a.b.slist[atomicAdd(&a.b.count[1], 1)] = i;
+  else a.b.slist[a.g.size - 1 - atomicAdd(&a.b.count[2], 1)] = i;
+}
+
 template <int N, typename LFn>
 __device__ bool rk3(const LsArgs& a, LsCtx& c, double dt, bool clamp_last, LFn L) {
   const GridDev& g = a.g;
-  const int n = __ldcg(a.b.count);
-  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gth = (long long)gridDim.x * blockDim.x;
+  const int nf = __ldcg(a.b.count + 1), nb = __ldcg(a.b.count + 2);
   const double G = BAND * g.h;
+  // 32-entry chunks dealt round-robin over the CTAs: every SM gets its share
+  // of both kinds while a warp reads 32 consecutive entries
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5);
+  const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
   for (int stage = 0; stage < 3; ++stage) {
     const double* src = stage == 0 ? a.phi : (stage == 1 ? a.b.p1 : a.b.p2);
-    for (long long i = gtid; i < n; i += gth) {
+    for (long long chunk = warp0; 32 * chunk < nf + nb; chunk += wstride) {
+      const long long j = 32 * chunk + lane;
+      if (j >= nf + nb) continue;
+      const bool front = j < nf;
+      const long long i = __ldcg(a.b.slist + (front ? j : g.size - 1 - (j - nf)));
       const long long p = __ldcg(a.b.list + i);
-      if (!(a.b.flags[p] & F_T)) continue;
       int ix[N];
       unpack<N>(a.b.lcoord[i], ix);
-      const double Lv = L(src, p, ix, i);
+      const double Lv = L(src, p, ix, i, front);
       const double ph = a.phi[p];
       if (stage == 0) {
         a.b.p1[p] = ph + dt * Lv;
@@ -319,26 +335,32 @@ __device__ void stage_init(const LsArgs& a) {
 template <int N>
 __device__ bool reinitialise(const LsArgs& a, LsCtx& c) {
   const GridDev& g = a.g;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.b.count[1] = 0;
+    a.b.count[2] = 0;
+  }
   if (!build_work_set<N>(a, c, false, 3)) return false;
   const int n = __ldcg(a.b.count);
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gth = (long long)gridDim.x * blockDim.x;
   const double h = g.h;
+  // mixed path: FP64 within 3h of the interface (|phi_0| < 3h, i.e.
+  // |S| < 3/sqrt(10)), FP32 WENO/Godunov arithmetic further out; the two
+  // kinds go to the two ends of the stage list
+  const double near_s = 3.0 / sqrt(10.0);
   for (long long i = gtid; i < n; i += gth) {
     const long long p = __ldcg(a.b.list + i);
     const double ph = a.phi[p];
-    a.b.S0[i] = ph / sqrt(ph * ph + h * h);
+    const double S = ph / sqrt(ph * ph + h * h);
+    a.b.S0[i] = S;
+    if (a.b.flags[p] & F_T) stage_push(a, (int)i, !a.mixed || fabs(S) < near_s);
   }
   stage_init<N>(a);
   if (!grid_barrier(a.st, c.bar, 40)) return false;
   const int K = (int)ceil(12.0 * sqrt((double)N));
   const double dtau = 0.5 * h / sqrt((double)N);
-  // mixed path: FP64 within 3h of the interface (|phi_0| < 3h, i.e.
-  // |S| < 3/sqrt(10)), FP32 WENO/Godunov arithmetic further out
-  const double near_s = 3.0 / sqrt(10.0);
-  auto L = [&](const double* src, long long p, const int* ix, long long i) {
+  auto L = [&](const double* src, long long p, const int* ix, long long i, bool fp64) {
     const double S = __ldcg(a.b.S0 + i);
-    const double gr = (a.mixed && fabs(S) >= near_s) ? godunov<float, N>(g, src, p, ix, S > 0.0)
-                                                     : godunov<double, N>(g, src, p, ix, S > 0.0);
+    const double gr = fp64 ? godunov<double, N>(g, src, p, ix, S > 0.0) : godunov<float, N>(g, src, p, ix, S > 0.0);
     return -S * (gr - 1.0);
   };
   for (int it = 0; it < K; ++it) {
@@ -372,7 +394,11 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
     return;
   }
 
-  if (blockIdx.x == 0 && threadIdx.x == 0) *a.b.vmax = 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.b.vmax = 0.0;
+    a.b.count[1] = 0;
+    a.b.count[2] = 0;
+  }
   if (!build_work_set<N>(a, c, true, 0)) return;
   const int n = __ldcg(a.b.count);
   const long long cap = g.size;
@@ -561,6 +587,7 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
       }
       const double V = a.mu * fmax(0.0, (4.0 * us[0] - us[1]) / (2.0 * h));
       a.b.V[i] = V;
+      stage_push(a, (int)i, true);
       vm = fmax(vm, V);
     }
     for (int o = 16; o > 0; o >>= 1) vm = fmax(vm, __shfl_xor_sync(0xffffffffu, vm, o));
@@ -582,7 +609,7 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
       a.b.info[2] = nsub;
     }
     const double dts = a.dt / nsub;
-    auto L = [&](const double* s, long long p, const int* ix, long long i) {
+    auto L = [&](const double* s, long long p, const int* ix, long long i, bool) {
       const double gr = a.mixed ? godunov<float, N>(g, s, p, ix, true) : godunov<double, N>(g, s, p, ix, true);
       return -__ldcg(a.b.V + i) * gr;
     };

@@ -10,7 +10,8 @@ struct LevelsetBufs {
   uint8_t* flags;   // grid: tube / validity bits
   int* list;        // grid indices of the work set, grid order
   ushort4* lcoord;  // per list entry: the node's axis indices
-  int* count;       // [0] list length
+  int* slist;       // RK stage list: work-list positions of the update set
+  int* count;       // [0] list length, [1] [2] stage-list front / back counts
   int* cta_count;   // per-CTA counts for the in-kernel compaction
   double* vmax;     // [0] max Stefan speed on the tube
   int* nsub;        // [0] advection substeps of the last call
