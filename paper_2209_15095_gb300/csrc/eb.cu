@@ -24,25 +24,31 @@ namespace etd {
 constexpr int SCAN_TILE = 2048;   // nodes per block in the compaction
 constexpr int SCAN_NT = 256;
 
-__device__ __forceinline__ bool inside_at(const double* phi, long long p) { return phi[p] < 0.0; }
+// x < 0 decided on the bit pattern (integer pipe; FP64 compares are costly
+// over the whole grid): sign bit set, and x is neither -0 nor NaN.
+__device__ __forceinline__ bool negative(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (long long)b < 0 && (b << 1) - 1ull < 0xFFE0000000000000ull;
+}
 
 // Class of node p from phi; nodes on the box boundary cannot be computational.
+// Grids hold fewer than 2^31 nodes: 32-bit index arithmetic.
 __device__ __forceinline__ uint8_t classify_node(const GridDev& g, const double* __restrict__ phi, long long p,
                                                  bool& near_edge) {
-  long long rem = p;
+  unsigned rem = (unsigned)p;
   bool edge = false;
   near_edge = false;
-  int idx[MAXD];
   for (int d = 0; d < g.ndim; ++d) {
-    idx[d] = (int)(rem / g.stride[d]);
-    rem -= (long long)idx[d] * g.stride[d];
-    if (idx[d] == 0 || idx[d] == g.n[d] - 1) edge = true;
-    if (idx[d] < 3 || idx[d] > g.n[d] - 4) near_edge = true;
+    const unsigned st = (unsigned)g.stride[d];
+    const int i = (int)(rem / st);
+    rem -= (unsigned)i * st;
+    if (i == 0 || i == g.n[d] - 1) edge = true;
+    if (i < 3 || i > g.n[d] - 4) near_edge = true;
   }
-  if (!(phi[p] < 0.0)) return K_OUT;
+  if (!negative(phi[p])) return K_OUT;
   if (edge) return K_GHOST;
   for (int d = 0; d < g.ndim; ++d) {
-    if (!(phi[p - g.stride[d]] < 0.0) || !(phi[p + g.stride[d]] < 0.0)) return K_GHOST;
+    if (!negative(phi[p - g.stride[d]]) || !negative(phi[p + g.stride[d]])) return K_GHOST;
   }
   return K_COMP;
 }
@@ -141,18 +147,16 @@ __global__ void __launch_bounds__(SCAN_NT) scatter_kernel(const GridDev g, const
 }
 
 // Case-3 ghost weight (reading for Eq. rbf_ubp, see the header comment).
+// p has axis indices ip; q = p + s * e_dq, s = +-1.
 template <int N>
-__device__ double case3_weight(const GridDev& g, const double* __restrict__ phi, long long p, long long q) {
+__device__ double case3_weight(const GridDev& g, const double* __restrict__ phi, long long p, const int* ip,
+                               long long q, int dq, int s) {
   const double h = g.h;
   double xp[N], xq[N], gp[N], gq[N];
-  long long rp = p, rq = q;
+#pragma unroll
   for (int d = 0; d < N; ++d) {
-    int ip = (int)(rp / g.stride[d]);
-    rp -= (long long)ip * g.stride[d];
-    int iq = (int)(rq / g.stride[d]);
-    rq -= (long long)iq * g.stride[d];
-    xp[d] = g.lo[d] + h * ip;
-    xq[d] = g.lo[d] + h * iq;
+    xp[d] = g.lo[d] + h * ip[d];
+    xq[d] = g.lo[d] + h * (ip[d] + (d == dq ? s : 0));
     gp[d] = (phi[p + g.stride[d]] - phi[p - g.stride[d]]) / (2.0 * h);
     gq[d] = (phi[q + g.stride[d]] - phi[q - g.stride[d]]) / (2.0 * h);
   }
@@ -220,66 +224,84 @@ __device__ __forceinline__ void atomic_max_pos(double* a, double v) {
   atomicMax((unsigned long long*)a, (unsigned long long)__double_as_longlong(v));
 }
 
-// Pass 4: per computational row, D_p and the Gershgorin row sum.
+// Pass 4: per computational row, D_p and the Gershgorin row sum.  One thread
+// per face: a warp holds 32 / (2N) rows with their 2N faces on consecutive
+// lanes; the row's first lane sums the face terms in face order.
 template <int N>
 __global__ void __launch_bounds__(256) metadata_kernel(MetaArgs a) {
+  constexpr int FPR = 2 * N, RPW = 32 / FPR;
   const GridDev g = a.g;
   const int ncomp = *a.ncomp;
   const double h2 = g.h * g.h;
+  const int lane = threadIdx.x & 31;
+  const int slot = lane / FPR, f = lane % FPR, d = f / 2, si = f % 2;
+  const int lead = slot * FPR;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   double gmax = 0.0;
   int nclamp = 0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncomp; k += gridDim.x * blockDim.x) {
-    const long long p = a.idx[k];
-    int ip[N];
-    {
-      long long rem = p;
-      for (int d = 0; d < N; ++d) {
-        ip[d] = (int)(rem / g.stride[d]);
-        rem -= (long long)ip[d] * g.stride[d];
-      }
-    }
-    double D = 0.0, offsum = 0.0;
-    const double bp = a.beta_field ? a.beta_field[p] : a.beta_c;
-    for (int d = 0; d < N; ++d) {
-      for (int si = 0; si < 2; ++si) {
-        const long long s = si == 0 ? -g.stride[d] : g.stride[d];
-        const long long q = p + s;
-        const int iq = ip[d] + (si == 0 ? -1 : 1);
-        const double bf = a.beta_field ? 0.5 * (bp + a.beta_field[q]) : a.beta_c;
-        D = __dadd_rn(D, bf);
-        double gw = 0.0;  // 1 - w on a ghost face, 0 on a face to a computational point
-        if ((a.kind[q] & 3) == K_COMP) {
-          offsum += bf;
-        } else if (iq <= 0 || iq >= g.n[d] - 1) {
-          // ghost on the box boundary: the domain-margin error is already
-          // flagged by the classification; keep every access in bounds
-          D = __dsub_rn(D, 0.0);
-        } else {
-          const long long r = q + s;
-          double w;
-          if (!(a.phi[r] < 0.0)) {
-            const double theta = a.phi[q] / (a.phi[q] - a.phi[r]);
-            w = theta / (1.0 + theta);
-          } else {
-            w = case3_weight<N>(g, a.phi, p, q);
-          }
-          double wc = fmin(fmax(w, 0.0), 1.0);
-          if (!(wc == w)) ++nclamp;
-          D = __dsub_rn(D, __dmul_rn(bf, wc));
-          gw = 1.0 - wc;
+  for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * RPW < ncomp; w += nwarps) {
+    const long long k = w * RPW + slot;
+    const bool act = slot < RPW && k < ncomp;
+    double cD = 0.0, cOff = 0.0;
+    if (act) {
+      const long long p = a.idx[k];
+      int ip[N];
+      {
+        unsigned rem = (unsigned)p;
+#pragma unroll
+        for (int e = 0; e < N; ++e) {
+          const unsigned st = (unsigned)g.stride[e];
+          ip[e] = (int)(rem / st);
+          rem -= (unsigned)ip[e] * st;
         }
-        if (a.facew) a.facew[(long long)k * (2 * N) + 2 * d + si] = gw;
       }
+      const long long s = si == 0 ? -g.stride[d] : g.stride[d];
+      const long long q = p + s;
+      const int iq = ip[d] + (si == 0 ? -1 : 1);
+      const double bf = a.beta_field ? 0.5 * (a.beta_field[p] + a.beta_field[q]) : a.beta_c;
+      double gw = 0.0;  // 1 - w on a ghost face, 0 on a face to a computational point
+      if ((a.kind[q] & 3) == K_COMP) {
+        cD = bf;
+        cOff = bf;
+      } else if (iq <= 0 || iq >= g.n[d] - 1) {
+        // ghost on the box boundary: the domain-margin error is already
+        // flagged by the classification; keep every access in bounds
+        cD = bf;
+      } else {
+        const long long r = q + s;
+        double wv;
+        if (!negative(a.phi[r])) {
+          const double theta = a.phi[q] / (a.phi[q] - a.phi[r]);
+          wv = theta / (1.0 + theta);
+        } else {
+          wv = case3_weight<N>(g, a.phi, p, ip, q, d, si == 0 ? -1 : 1);
+        }
+        const double wc = fmin(fmax(wv, 0.0), 1.0);
+        if (!(wc == wv)) ++nclamp;
+        cD = fma(-bf, wc, bf);
+        gw = 1.0 - wc;
+      }
+      if (a.facew) a.facew[k * FPR + f] = gw;
     }
-    a.diag[k] = D;
-    if (a.diagf) a.diagf[k] = (float)D;
-    gmax = fmax(gmax, (D + offsum) / h2);
+    double D = 0.0, off = 0.0;
+#pragma unroll
+    for (int j = 0; j < FPR; ++j) {
+      const double vD = __shfl_sync(0xffffffffu, cD, lead + j);
+      const double vO = __shfl_sync(0xffffffffu, cOff, lead + j);
+      D += vD;
+      off += vO;
+    }
+    if (act && f == 0) {
+      a.diag[k] = D;
+      if (a.diagf) a.diagf[k] = (float)D;
+      gmax = fmax(gmax, (D + off) / h2);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
     nclamp += __shfl_xor_sync(0xffffffffu, nclamp, o);
   }
-  if ((threadIdx.x & 31) == 0) {
+  if (lane == 0) {
     atomic_max_pos(a.gersh, gmax);
     if (nclamp) atomicAdd(&a.st->nclamp, nclamp);
   }

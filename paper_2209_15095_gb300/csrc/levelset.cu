@@ -43,6 +43,26 @@ enum : uint8_t {
 };
 enum : int { LS_ADVANCE = 0, LS_PREPARE = 1 };
 
+// Bit planes of the work-set build: one bit per node, rows along the last
+// (contiguous) axis padded to whole 32-bit words.
+enum : int { P_S = 0, P_T, P_T1, P_T2, P_T3, P_V0, P_V1, P_V2, NPLANES };
+
+struct BitGeo {
+  int nx;        // nodes per row (last axis)
+  int W;         // words per row
+  long long R;   // rows
+  long long nw;  // words per plane
+};
+
+__host__ __device__ __forceinline__ BitGeo bit_geo(const GridDev& g) {
+  BitGeo b;
+  b.nx = g.n[g.ndim - 1];
+  b.W = (b.nx + 31) / 32;
+  b.R = g.size / b.nx;
+  b.nw = b.R * b.W;
+  return b;
+}
+
 struct LsArgs {
   GridDev g;
   LevelsetBufs b;
@@ -60,7 +80,8 @@ struct LsArgs {
 LevelsetBufs levelset_carve(const GridDev& g, const std::function<char*(size_t)>& take) {
   const size_t G = (size_t)g.size;
   LevelsetBufs b;
-  b.flags = (uint8_t*)take(G);
+  b.lflag = (uint8_t*)take(G);
+  b.bits = (uint32_t*)take((size_t)NPLANES * (size_t)bit_geo(g).nw * sizeof(uint32_t));
   b.list = (int*)take(G * sizeof(int));
   b.slist = (int*)take(G * sizeof(int));
   b.lcoord = (ushort4*)take(G * sizeof(ushort4));
@@ -163,108 +184,204 @@ __device__ double godunov(const GridDev& g, const double* __restrict__ src, long
 struct LsCtx {
   unsigned bar;
   int red;
-  long long chunk_lo, chunk_hi;
+  long long wlo, whi;  // this CTA's words of the bit planes
 };
 
-// Flags: S, T, T1, T2, T3 (dilations along the axes) and, with `kind`, the
-// validity bits V0 (computational), V1, V2.  Then the ordered list of T3
-// nodes.  Returns false if the kernel must stop.
+// valid-node mask of word wi of a row
+__device__ __forceinline__ unsigned tail_mask(const BitGeo& bg, int wi) {
+  const int left = bg.nx - 32 * wi;
+  return left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
+}
+
+// |x| < G decided on the bit patterns (G > 0 finite): non-negative doubles
+// order like their bits, and NaN compares false
+__device__ __forceinline__ bool abs_below(double x, unsigned long long Gbits) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) < Gbits;
+}
+
+// Planes S (|phi| < G), T, T1, T2, T3 (each the previous dilated by one
+// node along every axis) and, with `kind`, V0 (computational), V1, V2 (each
+// the previous eroded the same way); out-of-box neighbours repeat the edge
+// node.  Then the ordered list of T3 nodes with their axis indices and
+// flags.  Returns false if the kernel must stop.
 template <int N>
 __device__ bool build_work_set(const LsArgs& a, LsCtx& c, bool with_valid, int slot) {
   const GridDev& g = a.g;
-  uint8_t* fl = a.b.flags;
-  const double G = BAND * g.h;
-  // pass A: S and V0
-  for (long long p = c.chunk_lo + threadIdx.x; p < c.chunk_hi; p += blockDim.x) {
-    uint8_t f = 0;
-    if (fabs(a.phi[p]) < G) f |= F_S;
-    if (with_valid && (a.kind[p] & 3) == K_COMP) f |= F_V0;
-    fl[p] = f;
+  const BitGeo bg = bit_geo(g);
+  uint32_t* const pl = a.b.bits;
+  const unsigned long long Gbits = (unsigned long long)__double_as_longlong(BAND * g.h);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  // row strides in words and row extents of the first N - 1 axes
+  long long rsw[N > 1 ? N - 1 : 1];
+  unsigned rstr[N > 1 ? N - 1 : 1];
+#pragma unroll
+  for (int d = 0; d < N - 1; ++d) {
+    rstr[d] = (unsigned)(g.stride[d] / bg.nx);
+    rsw[d] = (long long)rstr[d] * bg.W;
+  }
+  // pass A: one warp per word, a lane per node
+  for (long long w = c.wlo + wid; w < c.whi; w += nwarp) {
+    const unsigned r = (unsigned)w / (unsigned)bg.W;
+    const int x = (int)((unsigned)w - r * (unsigned)bg.W) * 32 + lane;
+    bool sb = false, vb = false;
+    if (x < bg.nx) {
+      const long long p = (long long)r * bg.nx + x;
+      sb = abs_below(a.phi[p], Gbits);
+      vb = with_valid && (a.kind[p] & 3) == K_COMP;
+    }
+    const unsigned ws = __ballot_sync(0xffffffffu, sb), wv = __ballot_sync(0xffffffffu, vb);
+    if (lane == 0) {
+      pl[P_S * bg.nw + w] = ws;
+      if (with_valid) pl[P_V0 * bg.nw + w] = wv;
+    }
   }
   if (!grid_barrier(a.st, c.bar, 20)) return false;
-  // passes B..E: each adds the dilation of the previous bit (and V1, V2)
-  const uint8_t src_bits[4] = {F_S, F_T, F_T1, F_T2};
-  const uint8_t dst_bits[4] = {F_T, F_T1, F_T2, F_T3};
+  // passes B..E: dilation S -> T -> T1 -> T2 -> T3; erosion V0 -> V1 -> V2
+  int cnt = 0;
   for (int pass = 0; pass < 4; ++pass) {
-    const uint8_t sb = src_bits[pass], db = dst_bits[pass];
+    const uint32_t* src = pl + (P_S + pass) * bg.nw;
+    uint32_t* dst = pl + (P_T + pass) * bg.nw;
     const bool vpass = with_valid && pass < 2;
-    const uint8_t vs = pass == 0 ? F_V0 : F_V1, vd = pass == 0 ? F_V1 : F_V2;
-    int cnt = 0;
-    for (long long p = c.chunk_lo + threadIdx.x; p < c.chunk_hi; p += blockDim.x) {
-      int ix[N];
-      coords<N>(g, p, ix);
-      uint8_t f = fl[p];
-      bool any = (f & sb) != 0;
-      bool all = (f & vs) != 0;
+    const uint32_t* vsrc = pl + (P_V0 + pass) * bg.nw;
+    uint32_t* vdst = pl + (P_V1 + pass) * bg.nw;
+    for (long long w = c.wlo + threadIdx.x; w < c.whi; w += blockDim.x) {
+      unsigned r = (unsigned)w / (unsigned)bg.W;
+      const int wi = (int)((unsigned)w - r * (unsigned)bg.W);
+      int ir[N > 1 ? N - 1 : 1];
 #pragma unroll
-      for (int d = 0; d < N; ++d) {
-        const uint8_t fm = fl[nbr(g, p, ix, d, -1)], fp = fl[nbr(g, p, ix, d, 1)];
-        any = any || (fm & sb) || (fp & sb);
-        all = all && (fm & vs) && (fp & vs);
+      for (int d = 0; d < N - 1; ++d) {
+        ir[d] = (int)(r / rstr[d]);
+        r -= (unsigned)ir[d] * rstr[d];
       }
-      uint8_t add = any ? db : 0;
-      if (vpass && all) add |= vd;
-      // other threads only read bits this pass does not write
-      if (add) fl[p] = f | add;
-      if (pass == 3 && any) ++cnt;
+      const unsigned tm = tail_mask(bg, wi);
+      const unsigned sv = __ldcg(src + w);
+      unsigned any = sv | (sv << 1) | (sv >> 1);
+      if (wi > 0) any |= __ldcg(src + w - 1) >> 31;
+      if (wi + 1 < bg.W) any |= __ldcg(src + w + 1) << 31;
+#pragma unroll
+      for (int d = 0; d < N - 1; ++d) {
+        if (ir[d] > 0) any |= __ldcg(src + w - rsw[d]);
+        if (ir[d] < g.n[d] - 1) any |= __ldcg(src + w + rsw[d]);
+      }
+      any &= tm;
+      dst[w] = any;
+      if (pass == 3) cnt += __popc(any);
+      if (vpass) {
+        const unsigned v = __ldcg(vsrc + w);
+        const unsigned lft = (v << 1) | (wi > 0 ? __ldcg(vsrc + w - 1) >> 31 : (v & 1u));
+        const unsigned rgt =
+            (v >> 1) | (wi + 1 < bg.W ? __ldcg(vsrc + w + 1) << 31 : (v & (1u << ((bg.nx - 1) & 31))));
+        unsigned all = v & lft & rgt;
+#pragma unroll
+        for (int d = 0; d < N - 1; ++d) {
+          all &= ir[d] > 0 ? __ldcg(vsrc + w - rsw[d]) : v;
+          all &= ir[d] < g.n[d] - 1 ? __ldcg(vsrc + w + rsw[d]) : v;
+        }
+        vdst[w] = all & tm;
+      }
     }
     if (pass == 3) {
       for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
       __shared__ int s_c[LS_NT / 32];
-      if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = cnt;
+      if (lane == 0) s_c[wid] = cnt;
       __syncthreads();
       if (threadIdx.x == 0) {
         int t = 0;
-        for (int w = 0; w < (int)blockDim.x / 32; ++w) t += s_c[w];
+        for (int k = 0; k < nwarp; ++k) t += s_c[k];
         a.b.cta_count[blockIdx.x] = t;
       }
       __syncthreads();
     }
     if (!grid_barrier(a.st, c.bar, 21 + pass)) return false;
   }
-  // ordered compaction of T3
-  __shared__ int s_off;
+  // ordered compaction of T3: this CTA's offset, then a block scan of the
+  // per-word counts, then each thread expands its word
+  __shared__ int s_off, s_tot;
   __shared__ int s_w[LS_NT / 32];
-  if (threadIdx.x == 0) {
+  if (wid == 0) {
     int off = 0, tot = 0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      int v = __ldcg(a.b.cta_count + b);
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+      const int v = __ldcg(a.b.cta_count + b);
       if (b < (int)blockIdx.x) off += v;
       tot += v;
     }
-    s_off = off;
-    if (blockIdx.x == 0) {
-      a.b.count[0] = tot;
-      a.b.info[slot] = tot;
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (lane == 0) {
+      s_off = off;
+      if (blockIdx.x == 0) {
+        a.b.count[0] = tot;
+        a.b.info[slot] = tot;
+      }
     }
   }
   __syncthreads();
   int run = s_off;
   int tcnt = 0;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (long long base = c.chunk_lo; base < c.chunk_hi; base += blockDim.x) {
-    const long long p = base + threadIdx.x;
-    const bool f = p < c.chunk_hi && (fl[p] & F_T3);
-    if (f && (fl[p] & F_T)) ++tcnt;
-    const unsigned bal = __ballot_sync(0xffffffffu, f);
-    const int before = __popc(bal & ((1u << lane) - 1u));
-    if (lane == 0) s_w[wid] = __popc(bal);
+  const uint32_t* T3 = pl + P_T3 * bg.nw;
+  for (long long base = c.wlo; base < c.whi; base += blockDim.x) {
+    const long long w = base + threadIdx.x;
+    const unsigned v = w < c.whi ? __ldcg(T3 + w) : 0u;
+    const int cw = __popc(v);
+    int incl = cw;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_w[wid] = incl;
     __syncthreads();
-    int woff = 0, tot = 0;
-    for (int w = 0; w < (int)blockDim.x / 32; ++w) {
-      const int cc = s_w[w];
-      if (w < wid) woff += cc;
-      tot += cc;
+    int woff = 0;
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int k = 0; k < nwarp; ++k) t += s_w[k];
+      s_tot = t;
     }
-    if (f) {
+    for (int k = 0; k < wid; ++k) woff += s_w[k];
+    if (v) {
+      unsigned r = (unsigned)w / (unsigned)bg.W;
+      const int wi = (int)((unsigned)w - r * (unsigned)bg.W);
       int ix[N];
-      coords<N>(g, p, ix);
-      a.b.list[run + woff + before] = (int)p;
-      a.b.lcoord[run + woff + before] =
-          make_ushort4((unsigned short)ix[0], (unsigned short)ix[1], (unsigned short)(N > 2 ? ix[2] : 0),
-                       (unsigned short)(N > 3 ? ix[3] : 0));
+#pragma unroll
+      for (int d = 0; d < N - 1; ++d) {
+        ix[d] = (int)(r / rstr[d]);
+        r -= (unsigned)ix[d] * rstr[d];
+      }
+      const long long row0 = (long long)((unsigned)w / (unsigned)bg.W) * bg.nx;
+      const unsigned wT = __ldcg(pl + P_T * bg.nw + w), wT1 = __ldcg(pl + P_T1 * bg.nw + w),
+                     wT2 = __ldcg(pl + P_T2 * bg.nw + w);
+      unsigned wV0 = 0, wV1 = 0, wV2 = 0;
+      if (with_valid) {
+        wV0 = __ldcg(pl + P_V0 * bg.nw + w);
+        wV1 = __ldcg(pl + P_V1 * bg.nw + w);
+        wV2 = __ldcg(pl + P_V2 * bg.nw + w);
+      }
+      tcnt += __popc(wT);
+      int pos = run + woff + incl - cw;
+      unsigned rest = v;
+      while (rest) {
+        const int b = __ffs(rest) - 1;
+        rest &= rest - 1u;
+        ix[N - 1] = 32 * wi + b;
+        const unsigned m = 1u << b;
+        uint8_t f = F_T3;
+        if (wT & m) f |= F_T;
+        if (wT1 & m) f |= F_T1;
+        if (wT2 & m) f |= F_T2;
+        if (wV0 & m) f |= F_V0;
+        if (wV1 & m) f |= F_V1;
+        if (wV2 & m) f |= F_V2;
+        a.b.list[pos] = (int)(row0 + ix[N - 1]);
+        a.b.lcoord[pos] = make_ushort4((unsigned short)ix[0], (unsigned short)ix[1],
+                                       (unsigned short)(N > 2 ? ix[2] : 0), (unsigned short)(N > 3 ? ix[3] : 0));
+        a.b.lflag[pos] = f;
+        ++pos;
+      }
     }
-    run += tot;
+    __syncthreads();
+    run += s_tot;
     __syncthreads();
   }
   for (int o = 16; o > 0; o >>= 1) tcnt += __shfl_xor_sync(0xffffffffu, tcnt, o);
@@ -352,7 +469,7 @@ __device__ bool reinitialise(const LsArgs& a, LsCtx& c) {
     const double ph = a.phi[p];
     const double S = ph / sqrt(ph * ph + h * h);
     a.b.S0[i] = S;
-    if (a.b.flags[p] & F_T) stage_push(a, (int)i, !a.mixed || fabs(S) < near_s);
+    if (a.b.lflag[i] & F_T) stage_push(a, (int)i, !a.mixed || fabs(S) < near_s);
   }
   stage_init<N>(a);
   if (!grid_barrier(a.st, c.bar, 40)) return false;
@@ -375,9 +492,12 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
   LsCtx c;
   c.bar = 0;
   c.red = 0;
-  const long long chunk = (g.size + gridDim.x - 1) / gridDim.x;
-  c.chunk_lo = min((long long)blockIdx.x * chunk, g.size);
-  c.chunk_hi = min(c.chunk_lo + chunk, g.size);
+  {
+    const long long nw = bit_geo(g).nw;
+    const long long chunk = (nw + gridDim.x - 1) / gridDim.x;
+    c.wlo = min((long long)blockIdx.x * chunk, nw);
+    c.whi = min(c.wlo + chunk, nw);
+  }
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gth = (long long)gridDim.x * blockDim.x;
   const double h = g.h;
   const double inv_h = 1.0 / h;
@@ -424,7 +544,7 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
       nv[d] = gr[d] / nr;
       a.b.nrm[d * cap + i] = nv[d];
     }
-    const uint8_t f = a.b.flags[p];
+    const uint8_t f = a.b.lflag[i];
     U[0][p] = (f & F_V0) ? a.u[p] : 0.0;
     double un = 0.0;
     if ((f & F_V1) && (f & F_T2)) {
@@ -439,7 +559,7 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
   if (!grid_barrier(a.st, c.bar, 51)) return;
   for (long long i = gtid; i < n; i += gth) {
     const long long p = __ldcg(a.b.list + i);
-    const uint8_t f = a.b.flags[p];
+    const uint8_t f = a.b.lflag[i];
     double unn = 0.0;
     if ((f & F_V2) && (f & F_T1)) {
       int ix[N];
@@ -454,10 +574,16 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
   if (!grid_barrier(a.st, c.bar, 52)) return;
   // three extrapolation sweeps.  Values off the sweep region never change,
   // so both ping-pong buffers get them once; each pass then touches only the
-  // region.  Each thread keeps the state of its first SW_CACHE list entries
-  // (node, region flag, normal, own value, source) in registers.
+  // region.  The first-order upwind step
+  //   q' = q - dtau (sum_d n_d D_d q - s),  D_d backward where n_d > 0,
+  // is used in the rearranged form q' = c0 q + sum_d a_d q(up_d) + dtau s,
+  // a_d = dtau |n_d| / h, c0 = 1 - sum_d a_d (equal up to rounding).  Each
+  // thread keeps its first SW_CACHE region entries (node, upwind nodes,
+  // coefficients, own value, dtau s) in registers, so a pass issues its N
+  // neighbour loads at once and does N + 1 FMAs.
   const int K = (int)ceil(12.0 * sqrt((double)N));
   const double dtau = h / (2.0 * sqrt((double)N));
+  const double dth = dtau * inv_h;
   const uint8_t vbits[3] = {F_V2, F_V1, F_V0};
   double* const* bufs[3] = {UNN, UN, U};
   const double* src = nullptr;
@@ -468,26 +594,40 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
       const long long p = __ldcg(a.b.list + i);
       B[1][p] = __ldcg(B[0] + p);
     }
-    long long cp[SW_CACHE];
+    int cp[SW_CACHE], cup[SW_CACHE][N];
     bool creg[SW_CACHE];
-    double cq[SW_CACHE], cs[SW_CACHE], cn[SW_CACHE][N];
-    int cix[SW_CACHE][N];
+    double cq[SW_CACHE], cds[SW_CACHE], cc0[SW_CACHE], ca[SW_CACHE][N];
 #pragma unroll
     for (int r = 0; r < SW_CACHE; ++r) {
       const long long i = gtid + r * gth;
       creg[r] = false;
       cp[r] = 0;
-      cq[r] = cs[r] = 0.0;
+      cq[r] = cds[r] = cc0[r] = 0.0;
+#pragma unroll
+      for (int d = 0; d < N; ++d) {
+        cup[r][d] = 0;
+        ca[r][d] = 0.0;
+      }
       if (i < n) {
         const long long p = __ldcg(a.b.list + i);
-        const uint8_t f = a.b.flags[p];
-        cp[r] = p;
+        const uint8_t f = a.b.lflag[i];
         creg[r] = (f & F_T) && !(f & vbits[sw]);
-        cq[r] = __ldcg(B[0] + p);
-        cs[r] = src ? __ldcg(src + p) : 0.0;
-        unpack<N>(a.b.lcoord[i], cix[r]);
+        if (creg[r]) {
+          cp[r] = (int)p;
+          cq[r] = __ldcg(B[0] + p);
+          cds[r] = src ? dtau * __ldcg(src + p) : 0.0;
+          int ix[N];
+          unpack<N>(a.b.lcoord[i], ix);
+          double asum = 0.0;
 #pragma unroll
-        for (int d = 0; d < N; ++d) cn[r][d] = __ldcg(a.b.nrm + d * cap + i);
+          for (int d = 0; d < N; ++d) {
+            const double nd = __ldcg(a.b.nrm + d * cap + i);
+            cup[r][d] = (int)nbr(g, p, ix, d, nd > 0.0 ? -1 : 1);
+            ca[r][d] = dth * fabs(nd);
+            asum += ca[r][d];
+          }
+          cc0[r] = 1.0 - asum;
+        }
       }
     }
     if (!grid_barrier(a.st, c.bar, 53)) return;
@@ -498,37 +638,34 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
 #pragma unroll
       for (int r = 0; r < SW_CACHE; ++r) {
         if (!creg[r]) continue;
-        const long long p = cp[r];
-        double acc = 0.0;
+        double qu[N];
 #pragma unroll
-        for (int d = 0; d < N; ++d) {
-          const double nd = cn[r][d];
-          double dd;
-          if (nd > 0.0) dd = (cq[r] - __ldcg(qc + nbr(g, p, cix[r], d, -1))) * inv_h;
-          else dd = (__ldcg(qc + nbr(g, p, cix[r], d, 1)) - cq[r]) * inv_h;
-          acc += nd * dd;
-        }
-        cq[r] = cq[r] - dtau * (acc - cs[r]);
-        qn[p] = cq[r];
+        for (int d = 0; d < N; ++d) qu[d] = __ldcg(qc + cup[r][d]);
+        double t = fma(cc0[r], cq[r], cds[r]);
+#pragma unroll
+        for (int d = 0; d < N; ++d) t = fma(ca[r][d], qu[d], t);
+        cq[r] = t;
+        qn[cp[r]] = t;
       }
       for (long long i = gtid + SW_CACHE * gth; i < n; i += gth) {
         const long long p = __ldcg(a.b.list + i);
-        const uint8_t f = a.b.flags[p];
+        const uint8_t f = a.b.lflag[i];
         if (!((f & F_T) && !(f & vbits[sw]))) continue;
-        const double q0 = __ldcg(qc + p);
         int ix[N];
         unpack<N>(a.b.lcoord[i], ix);
-        double acc = 0.0;
+        double asum = 0.0, qu[N], ad[N];
 #pragma unroll
         for (int d = 0; d < N; ++d) {
           const double nd = __ldcg(a.b.nrm + d * cap + i);
-          double dd;
-          if (nd > 0.0) dd = (q0 - __ldcg(qc + nbr(g, p, ix, d, -1))) * inv_h;
-          else dd = (__ldcg(qc + nbr(g, p, ix, d, 1)) - q0) * inv_h;
-          acc += nd * dd;
+          qu[d] = __ldcg(qc + nbr(g, p, ix, d, nd > 0.0 ? -1 : 1));
+          ad[d] = dth * fabs(nd);
+          asum += ad[d];
         }
-        const double sv = src ? __ldcg(src + p) : 0.0;
-        qn[p] = q0 - dtau * (acc - sv);
+        const double ds = src ? dtau * __ldcg(src + p) : 0.0;
+        double t = fma(1.0 - asum, __ldcg(qc + p), ds);
+#pragma unroll
+        for (int d = 0; d < N; ++d) t = fma(ad[d], qu[d], t);
+        qn[p] = t;
       }
       if (!grid_barrier(a.st, c.bar, 53)) return;
       cur ^= 1;
@@ -546,7 +683,7 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
     double vm = 0.0;
     for (long long i = gtid; i < n; i += gth) {
       const long long p = __ldcg(a.b.list + i);
-      if (!(a.b.flags[p] & F_T)) continue;
+      if (!(a.b.lflag[i] & F_T)) continue;
       int ix[N];
       unpack<N>(a.b.lcoord[i], ix);
       double nv[N], xg[N];

@@ -7,7 +7,8 @@
 namespace etd {
 
 struct LevelsetBufs {
-  uint8_t* flags;   // grid: tube / validity bits
+  uint8_t* lflag;   // per list entry: tube / validity bits
+  uint32_t* bits;   // bit planes of the work-set build (one bit per node)
   int* list;        // grid indices of the work set, grid order
   ushort4* lcoord;  // per list entry: the node's axis indices
   int* slist;       // RK stage list: work-list positions of the update set
