@@ -106,45 +106,52 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Sum of NQ per-thread values over the block; thread 0 writes the block's
-// totals to part[q * MAX_BLOCKS + blockIdx.x].  Fixed order: warp tree, then
-// warps in index order.
+// Staging area of the block reductions: up to 3 quantities of up to 512
+// threads, one instance per kernel.
+constexpr int RED_MAX_NQ = 3, RED_MAX_NT = 512;
+__device__ __forceinline__ double* red_stage() {
+  __shared__ double s_stage[RED_MAX_NQ * RED_MAX_NT];
+  return s_stage;
+}
+
+// Sum of NQ per-thread values over the block (blockDim.x <= 512); thread 0
+// of warp q writes the block's total of quantity q to
+// part[q * MAX_BLOCKS + blockIdx.x].  The values go through shared memory
+// and warp q sums quantity q (lane-strided, then a warp tree): FP64 adds run
+// on NQ warps instead of every warp's shuffle tree, and the order is fixed.
 template <int NQ>
 __device__ __forceinline__ void block_partials(const double (&v)[NQ], double* part) {
-  __shared__ double s_red[NQ][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  static_assert(NQ <= RED_MAX_NQ, "too many quantities");
+  double* st = red_stage();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nt = blockDim.x;
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    double x = warp_sum(v[q]);
-    if (lane == 0) s_red[q][wid] = x;
-  }
+  for (int q = 0; q < NQ; ++q) st[q * RED_MAX_NT + threadIdx.x] = v[q];
   __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      double x = lane < nw ? s_red[q][lane] : 0.0;
-      x = warp_sum(x);
-      if (lane == 0) part[q * MAX_BLOCKS + blockIdx.x] = x;
+  if (wid < NQ) {
+    const double* row = st + wid * RED_MAX_NT;
+    double x0 = 0.0, x1 = 0.0;
+    for (int t = lane; t < nt; t += 64) {
+      x0 += row[t];
+      if (t + 32 < nt) x1 += row[t + 32];
     }
+    const double x = warp_sum(x0 + x1);
+    if (lane == 0) part[wid * MAX_BLOCKS + blockIdx.x] = x;
   }
   __syncthreads();
 }
 
 // After a grid barrier: every CTA sums the per-block partials in the same
-// fixed order (lane-strided, then a warp tree), so every CTA obtains the same
-// bits.  Result broadcast to the whole block.
+// fixed order (warp q sums quantity q: lane-strided, then a warp tree), so
+// every CTA obtains the same bits.  Result broadcast to the whole block.
 template <int NQ>
 __device__ __forceinline__ void grid_totals(const double* part, double (&out)[NQ]) {
   __shared__ double s_tot[NQ];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (wid == 0) {
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      double x = 0.0;
-      for (int b = lane; b < (int)gridDim.x; b += 32) x += __ldcg(part + q * MAX_BLOCKS + b);
-      x = warp_sum(x);
-      if (lane == 0) s_tot[q] = x;
-    }
+  if (wid < NQ) {
+    double x = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) x += __ldcg(part + wid * MAX_BLOCKS + b);
+    x = warp_sum(x);
+    if (lane == 0) s_tot[wid] = x;
   }
   __syncthreads();
 #pragma unroll

@@ -33,7 +33,7 @@ constexpr int PH_NT = 512;
 constexpr int CHECK_EVERY = 5;
 constexpr double TAU_MIN = 1e-6;
 constexpr double BREAKDOWN_REL = 1e-12;
-constexpr float TAYLOR_THETA = 4.0f;
+constexpr float TAYLOR_THETA = 8.0f;
 constexpr int MAX_SUBSTEPS = 20000;  // bounded work per call
 
 __constant__ double c_inv_fact[64];  // 1/k!
@@ -53,20 +53,72 @@ struct Ctl {
 // ---------------------------------------------------------------------------
 // small exponential: x = exp(K) e_{M-1} for the augmented matrix
 //   K = [[tau H_m, e_1, 0], [0, 0, I_p], [0, 0, 0]],  M = m + p + 1 <= 64,
-// by Taylor series with scaling (K/s, s steps), unnormalised powers
-// accumulated with 1/k!.  Warp-cooperative: lane owns rows lane and lane+32.
+// by Taylor series with a shift and scaling, exp(K) = e^mu exp((K - mu I)/s)^s,
+// unnormalised powers accumulated with 1/k!.  Warp-cooperative: lane owns
+// rows lane and lane+32.
 // On return c.yexp[0..m-1] = phi_{p+1}(tau H_m) e_1.
+// s steps of the degree-deg Taylor polynomial of the tridiagonal-plus-
+// coupling matrix held as (A, B, C) per row (lane r: rows r and r + 32).
+// TWO is a template argument so that the second half's FP64 work is absent,
+// not predicated off, when M <= 32: a predicated-off FP64 instruction still
+// takes its issue slot.
+template <bool TWO>
+__device__ __forceinline__ void taylor_steps(int m, int s, int deg, const double (&A)[2], const double (&B)[2],
+                                             const double (&C)[2], double (&x)[2]) {
+  const int lane = threadIdx.x & 31;
+  for (int it = 0; it < s; ++it) {
+    double P0 = x[0], P1 = x[1], acc0 = x[0], acc1 = x[1];
+    for (int k = 1; k <= deg; ++k) {
+      double dn0 = __shfl_up_sync(0xffffffffu, P0, 1);
+      double up0 = __shfl_down_sync(0xffffffffu, P0, 1);
+      const double pm = __shfl_sync(0xffffffffu, (!TWO || m < 32) ? P0 : P1, m & 31);
+      if (lane == 0) dn0 = pm;
+      if (TWO) {
+        double dn1 = __shfl_up_sync(0xffffffffu, P1, 1);
+        double up1 = __shfl_down_sync(0xffffffffu, P1, 1);
+        const double b31 = __shfl_sync(0xffffffffu, P0, 31);
+        const double b32 = __shfl_sync(0xffffffffu, P1, 0);
+        if (lane == 0) dn1 = b31;
+        if (lane == 31) {
+          up0 = b32;
+          up1 = 0.0;
+        }
+        P1 = fma(C[1], up1, fma(B[1], dn1, A[1] * P1));
+        acc1 = fma(c_inv_fact[k], P1, acc1);
+      } else {
+        if (lane == 31) up0 = 0.0;
+      }
+      P0 = fma(C[0], up0, fma(B[0], dn0, A[0] * P0));
+      acc0 = fma(c_inv_fact[k], P0, acc0);
+    }
+    x[0] = acc0;
+    x[1] = acc1;
+  }
+}
+
 __device__ void small_expm_warp(Ctl& c, int m, int p, double tau) {
   const int lane = threadIdx.x & 31;
   const int M = m + p + 1;
-  float nb = 0.f;
+  // Gershgorin interval [L, U] of the augmented matrix (rows m.. have centre
+  // 0 and radius at most 1); FP32 suffices, it only picks the shift and the
+  // scaling.  exp(K) = e^mu exp(K - mu I) for any mu: mu is the interval's
+  // midpoint (floored at -300 so that neither factor overflows), which
+  // about halves the norm bound that sets the number of Taylor terms.
+  const float ft = (float)tau;
+  float L = -1.f, U = 1.f;
   for (int r = lane; r < m; r += 32) {
-    float v = fabsf((float)c.alpha[r]) + (r > 0 ? fabsf((float)c.low[r - 1]) : 0.f) +
-              (r + 1 < m ? fabsf((float)c.up[r + 1]) : 0.f);
-    nb = fmaxf(nb, v);
+    const float cr = ft * (float)c.alpha[r];
+    const float rr = ft * ((r > 0 ? fabsf((float)c.low[r - 1]) : 0.f) + (r + 1 < m ? fabsf((float)c.up[r + 1]) : 0.f)) +
+                     (r == 0 ? 1.f : 0.f);
+    L = fminf(L, cr - rr);
+    U = fmaxf(U, cr + rr);
   }
-  for (int o = 16; o > 0; o >>= 1) nb = fmaxf(nb, __shfl_xor_sync(0xffffffffu, nb, o));
-  nb = nb * (float)tau + 1.0f;
+  for (int o = 16; o > 0; o >>= 1) {
+    L = fminf(L, __shfl_xor_sync(0xffffffffu, L, o));
+    U = fmaxf(U, __shfl_xor_sync(0xffffffffu, U, o));
+  }
+  const float mu = fmaxf(0.5f * (L + U), -300.f);
+  const float nb = fmaxf(U - mu, mu - L);
   const int s = max(1, (int)ceilf(nb / TAYLOR_THETA));
   const float th = nb / (float)s;
   int deg = 1;
@@ -74,63 +126,34 @@ __device__ void small_expm_warp(Ctl& c, int m, int p, double tau) {
     float term = th;
     while (deg < 60 && term > 1e-18f) {
       ++deg;
-      term *= th / (float)deg;
+      term *= __fdividef(th, (float)deg);
     }
   }
   const double inv_s = 1.0 / (double)s;
+  const double dmu = (double)mu;
   double A[2], B[2], C[2], x[2];
   for (int h = 0; h < 2; ++h) {
     const int r = lane + 32 * h;
     if (r < m) {
-      A[h] = tau * c.alpha[r] * inv_s;
+      A[h] = (tau * c.alpha[r] - dmu) * inv_s;
       B[h] = r > 0 ? tau * c.low[r - 1] * inv_s : 0.0;
       C[h] = r + 1 < m ? tau * c.up[r + 1] * inv_s : 0.0;
-    } else if (r < M - 1) {
-      A[h] = 0.0;
+    } else if (r < M) {
+      A[h] = -dmu * inv_s;
       B[h] = 0.0;
-      C[h] = inv_s;
+      C[h] = r < M - 1 ? inv_s : 0.0;
     } else {
       A[h] = B[h] = C[h] = 0.0;
     }
     x[h] = (r == M - 1) ? 1.0 : 0.0;
   }
-  const double E = inv_s;  // row 0 couples to x_m
-  const bool two = M > 32;
-  for (int it = 0; it < s; ++it) {
-    double P0 = x[0], P1 = x[1], acc0 = x[0], acc1 = x[1];
-    for (int k = 1; k <= deg; ++k) {
-      double dn0 = __shfl_up_sync(0xffffffffu, P0, 1);
-      double up0 = __shfl_down_sync(0xffffffffu, P0, 1);
-      double pm = __shfl_sync(0xffffffffu, m < 32 ? P0 : P1, m & 31);
-      double dn1 = 0.0, up1 = 0.0;
-      if (two) {
-        dn1 = __shfl_up_sync(0xffffffffu, P1, 1);
-        up1 = __shfl_down_sync(0xffffffffu, P1, 1);
-        double b31 = __shfl_sync(0xffffffffu, P0, 31);
-        double b32 = __shfl_sync(0xffffffffu, P1, 0);
-        if (lane == 0) dn1 = b31;
-        if (lane == 31) up0 = b32;
-      }
-      if (lane == 0) dn0 = 0.0;
-      if (lane == 31) {
-        if (!two) up0 = 0.0;
-        up1 = 0.0;
-      }
-      double n0 = fma(A[0], P0, fma(C[0], up0, B[0] * dn0));
-      if (lane == 0) n0 = fma(E, pm, n0);
-      P0 = n0;
-      acc0 = fma(c_inv_fact[k], P0, acc0);
-      if (two) {
-        double n1 = fma(A[1], P1, fma(C[1], up1, B[1] * dn1));
-        P1 = n1;
-        acc1 = fma(c_inv_fact[k], P1, acc1);
-      }
-    }
-    x[0] = acc0;
-    x[1] = acc1;
-  }
-  if (lane < m) c.yexp[lane] = x[0];
-  if (lane + 32 < m) c.yexp[lane + 32] = x[1];
+  // row 0 has no lower neighbour: that slot carries its coupling to x_m
+  if (lane == 0) B[0] = inv_s;
+  if (M > 32) taylor_steps<true>(m, s, deg, A, B, C, x);
+  else taylor_steps<false>(m, s, deg, A, B, C, x);
+  const double emu = exp(dmu);
+  if (lane < m) c.yexp[lane] = x[0] * emu;
+  if (lane + 32 < m) c.yexp[lane + 32] = x[1] * emu;
   __syncwarp();
 }
 
@@ -207,12 +230,21 @@ __device__ __forceinline__ double* part_buf(double* part, int& red) {
   return b;
 }
 
+// Index of this thread in the node loops: 32-index chunks dealt round-robin
+// over the CTAs (chunk j to warp j / gridDim of CTA j % gridDim), a
+// bijection onto [0, gridDim * blockDim).  A problem smaller than the grid
+// then spreads over every SM instead of filling the first CTAs, whose FP64
+// pipes are shared by all of their warps.
+__device__ __forceinline__ long long dealt_tid() {
+  return (long long)(threadIdx.x & 31) + 32ll * ((long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5));
+}
+
 template <typename T, int N>
 __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int sidx, Ctl& c, unsigned& bar,
                               int& red, double ynorm2, double vscale) {
   const GridDev& g = a.g;
   const int ncomp = *S.ncomp;
-  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gtid = dealt_tid();
   const long long gthreads = (long long)gridDim.x * blockDim.x;
   const T cfac = (T)a.cfac;
   const T bc = (T)S.beta_c;
@@ -475,7 +507,7 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
   int red = 0;
   double* pb = nullptr;
   const GridDev& g = a.g;
-  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gtid = dealt_tid();
   const long long gthreads = (long long)gridDim.x * blockDim.x;
   // ---- set-up: y = v_0, v_1, v_2 for every species (reads every species'
   // field before any is overwritten)

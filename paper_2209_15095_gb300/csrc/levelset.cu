@@ -127,26 +127,49 @@ __device__ __forceinline__ long long nbr(const GridDev& g, long long p, const in
 }
 
 // ------------------------------------------------------------------ WENO5
-// The candidate stencils use exact reciprocals of 3 and 6 rounded once, and
-// the nonlinear weights share one division: with d_k = (eps + s_k)^2,
-//   sum_k (g_k/d_k) p_k / sum_k (g_k/d_k)
-//     = (g1 d2 d3 p1 + g2 d1 d3 p2 + g3 d1 d2 p3) / (g1 d2 d3 + g2 d1 d3 + g3 d1 d2).
+// Both one-sided HJ-WENO5 derivatives at a node from the six divided
+// differences q_0..q_5 (q_k = (f_{i+k-2} - f_{i+k-3}) / h), in the
+// equivalent form of Jiang & Peng (2000): with e_k = q_{k+1} - q_k,
+//   d- = c - Phi(e0, e1, e2, e3),   d+ = c + Phi(e4, e3, e2, e1),
+//   c  = (7 (q2 + q3) - (q1 + q4)) / 12,
+//   Phi(a,b,c,d) = w0 (a - 2b + c) / 3 + (w2 - 1/2)(b - 2c + d) / 6,
+// w_k = alpha_k / sum alpha, alpha = (1, 6, 3) / (eps' + I_k)^2 with
+// I_0 = (13/3)(a-b)^2 + (a-3b)^2, I_1 = (13/3)(b-c)^2 + (b+c)^2,
+// I_2 = (13/3)(c-d)^2 + (3c-d)^2.  I_k is 4 times the smoothness indicator
+// of the usual weighted form with eps = 1e-6, so eps' = 4 eps gives the same
+// weights; the usual weighted sum of the three candidate stencils is the
+// same number up to rounding.  The second differences and c are shared by
+// the two sides; in FP64 the two sides also share one division.
 template <typename C>
-__device__ __forceinline__ C weno5(C v1, C v2, C v3, C v4, C v5) {
-  constexpr C sixth = C(1.0 / 6.0);
-  const C p1 = (C(2) * v1 - C(7) * v2 + C(11) * v3) * sixth;
-  const C p2 = (-v2 + C(5) * v3 + C(2) * v4) * sixth;
-  const C p3 = (C(2) * v3 + C(5) * v4 - v5) * sixth;
-  const C a = v1 - C(2) * v2 + v3, b = v1 - C(4) * v2 + C(3) * v3;
-  const C c = v2 - C(2) * v3 + v4, d = v2 - v4;
-  const C e = v3 - C(2) * v4 + v5, f = C(3) * v3 - C(4) * v4 + v5;
-  const C s1 = C(13.0 / 12.0) * (a * a) + C(0.25) * (b * b);
-  const C s2 = C(13.0 / 12.0) * (c * c) + C(0.25) * (d * d);
-  const C s3 = C(13.0 / 12.0) * (e * e) + C(0.25) * (f * f);
-  const C e1 = C(WENO_EPS) + s1, e2 = C(WENO_EPS) + s2, e3 = C(WENO_EPS) + s3;
-  const C d1 = e1 * e1, d2 = e2 * e2, d3 = e3 * e3;
-  const C w1 = C(0.1) * (d2 * d3), w2 = C(0.6) * (d1 * d3), w3 = C(0.3) * (d1 * d2);
-  return (w1 * p1 + w2 * p2 + w3 * p3) / (w1 + w2 + w3);
+__device__ __forceinline__ void weno5_side(C a, C b, C c, C d, C& num, C& den) {
+  constexpr C k13 = C(13.0 / 3.0), eps4 = C(4.0 * WENO_EPS);
+  const C t0 = a - b, t1 = b - c, t2 = c - d;
+  const C u0 = a - C(3) * b, u1 = b + c, u2 = C(3) * c - d;
+  const C i0 = k13 * (t0 * t0) + u0 * u0, i1 = k13 * (t1 * t1) + u1 * u1, i2 = k13 * (t2 * t2) + u2 * u2;
+  const C s0 = eps4 + i0, s1 = eps4 + i1, s2 = eps4 + i2;
+  const C d0 = s0 * s0, d1 = s1 * s1, d2 = s2 * s2;
+  const C w0 = d1 * d2, w1 = C(6) * (d0 * d2), w2 = C(3) * (d0 * d1);
+  den = w0 + w1 + w2;
+  num = w0 * ((t0 - t1) * C(1.0 / 3.0)) + (w2 - C(0.5) * den) * ((t1 - t2) * C(1.0 / 6.0));
+}
+
+template <typename C>
+__device__ __forceinline__ void weno5_pair(const C* q, C& dm, C& dp) {
+  const C e0 = q[1] - q[0], e1 = q[2] - q[1], e2 = q[3] - q[2], e3 = q[4] - q[3], e4 = q[5] - q[4];
+  const C cen = (C(7) * (q[2] + q[3]) - (q[1] + q[4])) * C(1.0 / 12.0);
+  C nm, sm, np, sp;
+  weno5_side<C>(e0, e1, e2, e3, nm, sm);
+  weno5_side<C>(e4, e3, e2, e1, np, sp);
+  if constexpr (sizeof(C) == 8) {
+    // sm, sp >= 10 (4 eps)^4 > 2.5e-21, and for |q| < 1e18 the product stays
+    // finite: it neither underflows nor overflows in FP64
+    const C r = C(1) / (sm * sp);
+    dm = cen - nm * (sp * r);
+    dp = cen + np * (sm * r);
+  } else {
+    dm = cen - nm / sm;
+    dp = cen + np / sp;
+  }
 }
 
 // Godunov |grad phi| at node p from array src; positive: outward motion.
@@ -165,17 +188,13 @@ __device__ double godunov(const GridDev& g, const double* __restrict__ src, long
     C q[6];  // q[k+2] = (f(i+k) - f(i+k-1)) / h, k = -2..3
 #pragma unroll
     for (int k = -2; k <= 3; ++k) q[k + 2] = C((f[k + 3] - f[k + 2]) * inv_h);
-    const C dm = weno5<C>(q[0], q[1], q[2], q[3], q[4]);
-    const C dp = weno5<C>(q[5], q[4], q[3], q[2], q[1]);
-    C t;
-    if (positive) {
-      const C x = dm > C(0) ? dm : C(0), y = dp < C(0) ? dp : C(0);
-      t = fmax(x * x, y * y);
-    } else {
-      const C x = dm < C(0) ? dm : C(0), y = dp > C(0) ? dp : C(0);
-      t = fmax(x * x, y * y);
-    }
-    acc += t;
+    C dm, dp;
+    weno5_pair<C>(q, dm, dp);
+    // outward: max(d-, 0)^2 against min(d+, 0)^2; inward: the mirror image.
+    // Written with exact sign flips and no branch, so that no FP64 work of
+    // the other case is issued predicated off.
+    const C x = fmax(positive ? dm : -dm, C(0)), y = fmax(positive ? -dp : dp, C(0));
+    acc += fmax(x * x, y * y);
   }
   return (double)sqrt(acc);
 }
@@ -501,6 +520,7 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gth = (long long)gridDim.x * blockDim.x;
   const double h = g.h;
   const double inv_h = 1.0 / h;
+  const double inv_2h = 0.5 * inv_h;
   const double G = BAND * h;
 
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -530,18 +550,20 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
     const long long p = __ldcg(a.b.list + i);
     int ix[N];
     unpack<N>(a.b.lcoord[i], ix);
+    // central differences times 1/(2h), one reciprocal of |grad phi|: FP64
+    // divisions cost about ten FP64 instructions each
     double gr[N];
     double s2 = 0.0;
 #pragma unroll
     for (int d = 0; d < N; ++d) {
-      gr[d] = (a.phi[nbr(g, p, ix, d, 1)] - a.phi[nbr(g, p, ix, d, -1)]) / (2.0 * h);
+      gr[d] = (a.phi[nbr(g, p, ix, d, 1)] - a.phi[nbr(g, p, ix, d, -1)]) * inv_2h;
       s2 += gr[d] * gr[d];
     }
-    const double nr = fmax(sqrt(s2), GRAD_FLOOR);
+    const double rn = 1.0 / fmax(sqrt(s2), GRAD_FLOOR);
     double nv[N];
 #pragma unroll
     for (int d = 0; d < N; ++d) {
-      nv[d] = gr[d] / nr;
+      nv[d] = gr[d] * rn;
       a.b.nrm[d * cap + i] = nv[d];
     }
     const uint8_t f = a.b.lflag[i];
@@ -549,8 +571,8 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
     double un = 0.0;
     if ((f & F_V1) && (f & F_T2)) {
 #pragma unroll
-      for (int d = 0; d < N; ++d)
-        un += nv[d] * (a.u[nbr(g, p, ix, d, 1)] - a.u[nbr(g, p, ix, d, -1)]) / (2.0 * h);
+      for (int d = 0; d < N; ++d) un += nv[d] * (a.u[nbr(g, p, ix, d, 1)] - a.u[nbr(g, p, ix, d, -1)]);
+      un *= inv_2h;
     }
     UN[0][p] = un;
     a.b.p1[p] = a.phi[p];
@@ -567,7 +589,8 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
 #pragma unroll
       for (int d = 0; d < N; ++d)
         unn += __ldcg(a.b.nrm + d * cap + i) *
-               (__ldcg(UN[0] + nbr(g, p, ix, d, 1)) - __ldcg(UN[0] + nbr(g, p, ix, d, -1))) / (2.0 * h);
+               (__ldcg(UN[0] + nbr(g, p, ix, d, 1)) - __ldcg(UN[0] + nbr(g, p, ix, d, -1)));
+      unn *= inv_2h;
     }
     UNN[0][p] = unn;
   }
@@ -699,30 +722,36 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
         const double dist = sidx == 0 ? h : 2.0 * h;
         int i0[N];
         double fr[N];
+        long long q0 = 0;
 #pragma unroll
         for (int d = 0; d < N; ++d) {
-          double s = ((xg[d] - dist * nv[d]) - g.lo[d]) / h;
+          double s = ((xg[d] - dist * nv[d]) - g.lo[d]) * inv_h;
           s = fmin(fmax(s, 0.0), (double)(g.n[d] - 1));
           int ii = (int)floor(s);
           ii = min(ii, g.n[d] - 2);
           i0[d] = ii;
           fr[d] = s - ii;
+          q0 += (long long)ii * g.stride[d];
         }
-        double out = 0.0;
-        for (int corner = 0; corner < (1 << N); ++corner) {
-          double w = 1.0;
-          long long q = 0;
+        // N-linear interpolation one axis at a time (2^N - 1 lerps; the
+        // same value as the sum of corner weights times corner values)
+        double cv[1 << N];
 #pragma unroll
-          for (int d = 0; d < N; ++d) {
-            const int bit = (corner >> d) & 1;
-            w = w * (bit ? fr[d] : (1.0 - fr[d]));
-            q += (long long)(i0[d] + bit) * g.stride[d];
-          }
-          out += w * a.u[q];
+        for (int corner = 0; corner < (1 << N); ++corner) {
+          long long q = q0;
+#pragma unroll
+          for (int d = 0; d < N; ++d)
+            if ((corner >> d) & 1) q += g.stride[d];
+          cv[corner] = a.u[q];
         }
-        us[sidx] = out;
+#pragma unroll
+        for (int d = 0; d < N; ++d) {
+#pragma unroll
+          for (int corner = 0; corner < (1 << N); corner += 2 << d) cv[corner] = fma(fr[d], cv[corner + (1 << d)] - cv[corner], cv[corner]);
+        }
+        us[sidx] = cv[0];
       }
-      const double V = a.mu * fmax(0.0, (4.0 * us[0] - us[1]) / (2.0 * h));
+      const double V = a.mu * fmax(0.0, (4.0 * us[0] - us[1]) * inv_2h);
       a.b.V[i] = V;
       stage_push(a, (int)i, true);
       vm = fmax(vm, V);
