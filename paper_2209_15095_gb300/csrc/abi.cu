@@ -150,7 +150,7 @@ size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
   DevStatus* st = cv.take<DevStatus>(1);
   StatsDev* stats = cv.take<StatsDev>(1);
   double* part = cv.take<double>(8 * MAX_BLOCKS);
-  int* tiles = cv.take<int>(scan_tiles(g.size) + 1);
+  int* tiles = cv.take<int>(init_scratch_ints(g.size) + 1);
   if (c) {
     c->st = st;
     c->stats = stats;

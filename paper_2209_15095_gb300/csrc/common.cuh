@@ -99,6 +99,15 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned& k, int sit
   return s_ok != 0;
 }
 
+// Index of this thread in the node loops: 32-index chunks dealt round-robin
+// over the CTAs (chunk j to warp j / gridDim of CTA j % gridDim), a
+// bijection onto [0, gridDim * blockDim).  A problem smaller than the grid
+// then spreads over every SM instead of filling the first CTAs, whose FP64
+// pipes are shared by all of their warps.
+__device__ __forceinline__ long long dealt_tid() {
+  return (long long)(threadIdx.x & 31) + 32ll * ((long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5));
+}
+
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

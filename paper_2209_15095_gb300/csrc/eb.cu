@@ -21,8 +21,7 @@
 
 namespace etd {
 
-constexpr int SCAN_TILE = 2048;   // nodes per block in the compaction
-constexpr int SCAN_NT = 256;
+constexpr int INIT_NT = 512;  // threads per CTA of the set-up kernel
 
 // x < 0 decided on the bit pattern (integer pipe; FP64 compares are costly
 // over the whole grid): sign bit set, and x is neither -0 nor NaN.
@@ -31,147 +30,40 @@ __device__ __forceinline__ bool negative(double x) {
   return (long long)b < 0 && (b << 1) - 1ull < 0xFFE0000000000000ull;
 }
 
-// Class of node p from phi; nodes on the box boundary cannot be computational.
-// Grids hold fewer than 2^31 nodes: 32-bit index arithmetic.
-__device__ __forceinline__ uint8_t classify_node(const GridDev& g, const double* __restrict__ phi, long long p,
-                                                 bool& near_edge) {
-  unsigned rem = (unsigned)p;
-  bool edge = false;
-  near_edge = false;
-  for (int d = 0; d < g.ndim; ++d) {
-    const unsigned st = (unsigned)g.stride[d];
-    const int i = (int)(rem / st);
-    rem -= (unsigned)i * st;
-    if (i == 0 || i == g.n[d] - 1) edge = true;
-    if (i < 3 || i > g.n[d] - 4) near_edge = true;
-  }
-  if (!negative(phi[p])) return K_OUT;
-  if (edge) return K_GHOST;
-  for (int d = 0; d < g.ndim; ++d) {
-    if (!negative(phi[p - g.stride[d]]) || !negative(phi[p + g.stride[d]])) return K_GHOST;
-  }
-  return K_COMP;
-}
-
-// Pass 1: classify, zero stale vector entries where a computational node
-// stopped being one, count computational nodes per tile.
-__global__ void __launch_bounds__(SCAN_NT) classify_count_kernel(ClassifyArgs a) {
-  const GridDev g = a.g;
-  const long long base = (long long)blockIdx.x * SCAN_TILE;
-  int cnt = 0;
-  for (int i = 0; i < SCAN_TILE / SCAN_NT; ++i) {
-    long long p = base + threadIdx.x + (long long)i * SCAN_NT;
-    if (p >= g.size) break;
-    bool near_edge;
-    uint8_t k = classify_node(g, a.phi, p, near_edge);
-    if (k != K_OUT && near_edge) atomicOr(&a.st->err, ERRF_DOMAIN);
-    uint8_t old = a.kind[p] & 3;
-    if (old == K_COMP && k != K_COMP) {
-      for (int s = 0; s < a.nzero; ++s) {
-        if (a.zero_f64[s]) a.zero_f64[s][p] = 0.0;
-        if (a.zero_f32[s]) a.zero_f32[s][p] = 0.0f;
-      }
-      for (int j = 0; j < a.nbasis; ++j) {
-        if (a.basis_f64) a.basis_f64[(long long)j * g.size + p] = 0.0;
-        if (a.basis_f32) a.basis_f32[(long long)j * g.size + p] = 0.0f;
-      }
-    }
-    a.kind[p] = k;
-    cnt += (k == K_COMP);
-  }
-  __shared__ int s_cnt[SCAN_NT / 32];
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = cnt;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int w = 0; w < SCAN_NT / 32; ++w) t += s_cnt[w];
-    a.tile_count[blockIdx.x] = t;
-  }
-}
-
-// Pass 2: exclusive scan of tile counts by one block.
-__global__ void __launch_bounds__(1024) scan_tiles_kernel(int* tile_count, int ntiles, int* total) {
-  __shared__ int s_part[1024];
-  const int per = (ntiles + 1023) / 1024;
-  const int b0 = threadIdx.x * per;
-  int sum = 0;
-  for (int i = 0; i < per; ++i) {
-    int b = b0 + i;
-    if (b < ntiles) sum += tile_count[b];
-  }
-  s_part[threadIdx.x] = sum;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    int v = threadIdx.x >= o ? s_part[threadIdx.x - o] : 0;
-    __syncthreads();
-    s_part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  int run = s_part[threadIdx.x] - sum;  // exclusive prefix of this thread's chunk
-  for (int i = 0; i < per; ++i) {
-    int b = b0 + i;
-    if (b < ntiles) {
-      int c = tile_count[b];
-      tile_count[b] = run;
-      run += c;
-    }
-  }
-  if (threadIdx.x == 1023) *total = s_part[1023];
-}
-
-// Pass 3: write the grid indices of computational nodes in grid order.
-__global__ void __launch_bounds__(SCAN_NT) scatter_kernel(const GridDev g, const uint8_t* __restrict__ kind,
-                                                          const int* __restrict__ tile_offset, int* __restrict__ idx) {
-  __shared__ int s_w[SCAN_NT / 32];
-  const long long base = (long long)blockIdx.x * SCAN_TILE;
-  int run = tile_offset[blockIdx.x];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int i = 0; i < SCAN_TILE / SCAN_NT; ++i) {
-    long long p = base + threadIdx.x + (long long)i * SCAN_NT;
-    bool f = p < g.size && (kind[p] & 3) == K_COMP;
-    unsigned bal = __ballot_sync(0xffffffffu, f);
-    int before = __popc(bal & ((1u << lane) - 1u));
-    if (lane == 0) s_w[wid] = __popc(bal);
-    __syncthreads();
-    int woff = 0, tot = 0;
-    for (int w = 0; w < SCAN_NT / 32; ++w) {
-      int c = s_w[w];
-      if (w < wid) woff += c;
-      tot += c;
-    }
-    if (f) idx[run + woff + before] = (int)p;
-    run += tot;
-    __syncthreads();
-  }
-}
-
 // Case-3 ghost weight (reading for Eq. rbf_ubp, see the header comment).
-// p has axis indices ip; q = p + s * e_dq, s = +-1.
+// p has axis indices ip; q = p + s * e_dq, s = +-1.  FP64 divisions and
+// square roots cost about ten FP64 instructions each, so the gradients use
+// 1/(2h), unit vectors use rsqrt, and the length test on Gamma2 - Gamma1 is
+// made on its square; the decisions are those of the plain formulas up to
+// rounding at the thresholds.
 template <int N>
 __device__ double case3_weight(const GridDev& g, const double* __restrict__ phi, long long p, const int* ip,
                                long long q, int dq, int s) {
   const double h = g.h;
+  const double inv_2h = 0.5 / h;
   double xp[N], xq[N], gp[N], gq[N];
 #pragma unroll
   for (int d = 0; d < N; ++d) {
     xp[d] = g.lo[d] + h * ip[d];
     xq[d] = g.lo[d] + h * (ip[d] + (d == dq ? s : 0));
-    gp[d] = (phi[p + g.stride[d]] - phi[p - g.stride[d]]) / (2.0 * h);
-    gq[d] = (phi[q + g.stride[d]] - phi[q - g.stride[d]]) / (2.0 * h);
+    gp[d] = (phi[p + g.stride[d]] - phi[p - g.stride[d]]) * inv_2h;
+    gq[d] = (phi[q + g.stride[d]] - phi[q - g.stride[d]]) * inv_2h;
   }
   const double php = phi[p], phq = phi[q];
   double np2 = 0.0, nq2 = 0.0;
+#pragma unroll
   for (int d = 0; d < N; ++d) {
     np2 += gp[d] * gp[d];
     nq2 += gq[d] * gq[d];
   }
   const double fallback = phq / php;
   if (!(np2 > 0.0) || !(nq2 > 0.0)) return fallback;
+  const double cq = phq / nq2, cp = php / np2;
   double G1[N], G2[N];
+#pragma unroll
   for (int d = 0; d < N; ++d) {
-    G1[d] = xq[d] - (phq / nq2) * gq[d];
-    G2[d] = xp[d] - (php / np2) * gp[d];
+    G1[d] = xq[d] - cq * gq[d];
+    G2[d] = xp[d] - cp * gp[d];
   }
   if (N == 2) {
     double e1x = G1[0] - xp[0], e1y = G1[1] - xp[1], e2x = G2[0] - xp[0], e2y = G2[1] - xp[1];
@@ -181,35 +73,42 @@ __device__ double case3_weight(const GridDev& g, const double* __restrict__ phi,
     return (f1x * f2y - f1y * f2x) / det;
   } else {
     double nb[N], t[N], n[N];
-    double nbl = 0.0, tl = 0.0;
+    double nb2 = 0.0, t2 = 0.0;
+#pragma unroll
     for (int d = 0; d < N; ++d) {
       nb[d] = gq[d] + gp[d];
-      nbl += nb[d] * nb[d];
+      nb2 += nb[d] * nb[d];
       t[d] = G2[d] - G1[d];
-      tl += t[d] * t[d];
+      t2 += t[d] * t[d];
     }
-    nbl = sqrt(nbl);
-    tl = sqrt(tl);
-    if (!(nbl > 0.0)) return fallback;
-    for (int d = 0; d < N; ++d) nb[d] /= nbl;
-    if (tl >= 1e-12 * h) {
+    if (!(nb2 > 0.0)) return fallback;
+    const double rnb = rsqrt(nb2);
+#pragma unroll
+    for (int d = 0; d < N; ++d) nb[d] *= rnb;
+    if (t2 >= 1e-24 * h * h) {
+      const double rt = rsqrt(t2);
       double dot = 0.0;
+#pragma unroll
       for (int d = 0; d < N; ++d) {
-        t[d] /= tl;
+        t[d] *= rt;
         dot += nb[d] * t[d];
       }
-      double nl = 0.0;
+      double nl2 = 0.0;
+#pragma unroll
       for (int d = 0; d < N; ++d) {
         n[d] = nb[d] - dot * t[d];
-        nl += n[d] * n[d];
+        nl2 += n[d] * n[d];
       }
-      nl = sqrt(nl);
-      if (!(nl > 0.0)) return fallback;
-      for (int d = 0; d < N; ++d) n[d] /= nl;
+      if (!(nl2 > 0.0)) return fallback;
+      const double rnl = rsqrt(nl2);
+#pragma unroll
+      for (int d = 0; d < N; ++d) n[d] *= rnl;
     } else {
+#pragma unroll
       for (int d = 0; d < N; ++d) n[d] = nb[d];
     }
     double num = 0.0, den = 0.0;
+#pragma unroll
     for (int d = 0; d < N; ++d) {
       num += (xq[d] - G1[d]) * n[d];
       den += (xp[d] - G1[d]) * n[d];
@@ -224,14 +123,58 @@ __device__ __forceinline__ void atomic_max_pos(double* a, double v) {
   atomicMax((unsigned long long*)a, (unsigned long long)__double_as_longlong(v));
 }
 
-// Pass 4: per computational row, D_p and the Gershgorin row sum.  One thread
-// per face: a warp holds 32 / (2N) rows with their 2N faces on consecutive
-// lanes; the row's first lane sums the face terms in face order.
+// Class of a node from phi: inside (phi < 0) with all 2N axis neighbours
+// inside and not on the box boundary is computational, inside otherwise a
+// ghost; near flags inside-or-not nodes within 3 of the boundary.  Loading
+// (node_load) is split from deciding (node_class) so that a warp issues the
+// loads of several words before it waits on any of them; neighbour indices
+// are clamped into the box (an edge node is a ghost or outside whatever they
+// hold).  Grids hold fewer than 2^31 nodes: 32-bit index arithmetic.
 template <int N>
-__global__ void __launch_bounds__(256) metadata_kernel(MetaArgs a) {
+struct NodeLoad {
+  double v, w[2 * N];
+  bool edge, near;
+};
+
+template <int N>
+__device__ __forceinline__ void node_load(const GridDev& g, const double* __restrict__ phi, long long p,
+                                          NodeLoad<N>& L) {
+  unsigned rem = (unsigned)p;
+  L.edge = false;
+  L.near = false;
+  long long nb[2 * N];
+#pragma unroll
+  for (int d = 0; d < N; ++d) {
+    const unsigned st = (unsigned)g.stride[d];
+    const int i = (int)(rem / st);
+    rem -= (unsigned)i * st;
+    if (i == 0 || i == g.n[d] - 1) L.edge = true;
+    if (i < 3 || i > g.n[d] - 4) L.near = true;
+    nb[2 * d] = i > 0 ? p - g.stride[d] : p;
+    nb[2 * d + 1] = i < g.n[d] - 1 ? p + g.stride[d] : p;
+  }
+  L.v = phi[p];
+#pragma unroll
+  for (int j = 0; j < 2 * N; ++j) L.w[j] = phi[nb[j]];
+}
+
+template <int N>
+__device__ __forceinline__ uint8_t node_class(const NodeLoad<N>& L) {
+  if (!negative(L.v)) return K_OUT;
+  bool all = !L.edge;
+#pragma unroll
+  for (int j = 0; j < 2 * N; ++j) all = all && negative(L.w[j]);
+  return all ? K_COMP : K_GHOST;
+}
+
+// Phase 3: per computational row, D_p and the Gershgorin row sum.  One
+// thread per face: a warp holds 32 / (2N) rows with their 2N faces on
+// consecutive lanes (warps dealt round-robin over the CTAs); the row's first
+// lane sums the face terms in face order.
+template <int N>
+__device__ void metadata_phase(const MetaArgs& a, int ncomp) {
   constexpr int FPR = 2 * N, RPW = 32 / FPR;
-  const GridDev g = a.g;
-  const int ncomp = *a.ncomp;
+  const GridDev& g = a.g;
   const double h2 = g.h * g.h;
   const int lane = threadIdx.x & 31;
   const int slot = lane / FPR, f = lane % FPR, d = f / 2, si = f % 2;
@@ -239,12 +182,13 @@ __global__ void __launch_bounds__(256) metadata_kernel(MetaArgs a) {
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   double gmax = 0.0;
   int nclamp = 0;
-  for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * RPW < ncomp; w += nwarps) {
+  for (long long w = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5); w * RPW < ncomp;
+       w += nwarps) {
     const long long k = w * RPW + slot;
     const bool act = slot < RPW && k < ncomp;
     double cD = 0.0, cOff = 0.0;
     if (act) {
-      const long long p = a.idx[k];
+      const long long p = __ldcg(a.idx + k);
       int ip[N];
       {
         unsigned rem = (unsigned)p;
@@ -260,7 +204,7 @@ __global__ void __launch_bounds__(256) metadata_kernel(MetaArgs a) {
       const int iq = ip[d] + (si == 0 ? -1 : 1);
       const double bf = a.beta_field ? 0.5 * (a.beta_field[p] + a.beta_field[q]) : a.beta_c;
       double gw = 0.0;  // 1 - w on a ghost face, 0 on a face to a computational point
-      if ((a.kind[q] & 3) == K_COMP) {
+      if ((__ldcg(a.kind + q) & 3) == K_COMP) {
         cD = bf;
         cOff = bf;
       } else if (iq <= 0 || iq >= g.n[d] - 1) {
@@ -286,10 +230,8 @@ __global__ void __launch_bounds__(256) metadata_kernel(MetaArgs a) {
     double D = 0.0, off = 0.0;
 #pragma unroll
     for (int j = 0; j < FPR; ++j) {
-      const double vD = __shfl_sync(0xffffffffu, cD, lead + j);
-      const double vO = __shfl_sync(0xffffffffu, cOff, lead + j);
-      D += vD;
-      off += vO;
+      D += __shfl_sync(0xffffffffu, cD, lead + j);
+      off += __shfl_sync(0xffffffffu, cOff, lead + j);
     }
     if (act && f == 0) {
       a.diag[k] = D;
@@ -302,28 +244,171 @@ __global__ void __launch_bounds__(256) metadata_kernel(MetaArgs a) {
     nclamp += __shfl_xor_sync(0xffffffffu, nclamp, o);
   }
   if (lane == 0) {
-    atomic_max_pos(a.gersh, gmax);
+    if (gmax > 0.0) atomic_max_pos(a.gersh, gmax);
     if (nclamp) atomicAdd(&a.st->nclamp, nclamp);
   }
 }
 
-int scan_tiles(long long size) { return (int)((size + SCAN_TILE - 1) / SCAN_TILE); }
+// The whole set-up as one persistent cooperative kernel (one CTA per SM):
+//   phase 1  classify this CTA's chunk of nodes (whole 32-node words), zero
+//            stale vector entries where a computational node stopped being
+//            one, count computational nodes;
+//   phase 2  (after a grid barrier) this CTA's offset from the counts of the
+//            CTAs before it, then the grid indices of its computational nodes
+//            in grid order;
+//   phase 3  (after a second barrier) the row metadata.
+template <int N>
+__global__ void __launch_bounds__(INIT_NT, 1) init_domain_kernel(const ClassifyArgs ca, const MetaArgs ma) {
+  const GridDev& g = ca.g;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  unsigned bar = 0;
+  // this CTA's 32-node words; the computational-node bit plane follows the
+  // per-CTA counts in the scratch
+  const long long nw = (g.size + 31) / 32;
+  const long long cw = (nw + gridDim.x - 1) / gridDim.x;
+  const long long wlo = min((long long)blockIdx.x * cw, nw), whi = min(wlo + cw, nw);
+  uint32_t* cbits = (uint32_t*)(ca.tile_count + MAX_BLOCKS);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ma.gersh = 0.0;
+  __shared__ int s_w[INIT_NT / 32];
+  __shared__ int s_off, s_tot;
+  int cnt = 0;
+  constexpr int UW = 4;  // words per warp and iteration: their loads overlap
+  for (long long w0 = wlo + (long long)wid * UW; w0 < whi; w0 += (long long)nwarp * UW) {
+    NodeLoad<N> L[UW];
+    uint8_t old[UW];
+    bool val[UW];
+#pragma unroll
+    for (int u = 0; u < UW; ++u) {
+      const long long p = 32 * (w0 + u) + lane;
+      val[u] = w0 + u < whi && p < g.size;
+      old[u] = K_OUT;
+      if (val[u]) {
+        node_load<N>(g, ca.phi, p, L[u]);
+        old[u] = ca.kind[p] & 3;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UW; ++u) {
+      const long long p = 32 * (w0 + u) + lane;
+      const uint8_t k = val[u] ? node_class<N>(L[u]) : K_OUT;
+      if (val[u]) {
+        if (k != K_OUT && L[u].near) atomicOr(&ca.st->err, ERRF_DOMAIN);
+        if (old[u] == K_COMP && k != K_COMP) {
+          for (int s = 0; s < ca.nzero; ++s) {
+            if (ca.zero_f64[s]) ca.zero_f64[s][p] = 0.0;
+            if (ca.zero_f32[s]) ca.zero_f32[s][p] = 0.0f;
+          }
+          for (int j = 0; j < ca.nbasis; ++j) {
+            if (ca.basis_f64) ca.basis_f64[(long long)j * g.size + p] = 0.0;
+            if (ca.basis_f32) ca.basis_f32[(long long)j * g.size + p] = 0.0f;
+          }
+        }
+        ca.kind[p] = k;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, val[u] && k == K_COMP);
+      if (lane == 0 && w0 + u < whi) {
+        cbits[w0 + u] = bal;
+        cnt += __popc(bal);
+      }
+    }
+  }
+  if (lane == 0) s_w[wid] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int j = 0; j < nwarp; ++j) t += s_w[j];
+    ca.tile_count[blockIdx.x] = t;
+  }
+  if (!grid_barrier(ca.st, bar, 60)) return;
+  if (wid == 0) {
+    int off = 0, tot = 0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+      const int v = __ldcg(ca.tile_count + b);
+      if (b < (int)blockIdx.x) off += v;
+      tot += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (lane == 0) {
+      s_off = off;
+      s_tot = tot;
+      if (blockIdx.x == 0) *ma.ncomp = tot;
+    }
+  }
+  __syncthreads();
+  // ordered compaction: a thread per word, block scan of the popcounts,
+  // then each thread writes its word's nodes
+  int run = s_off;
+  for (long long base = wlo; base < whi; base += blockDim.x) {
+    const long long w = base + threadIdx.x;
+    const unsigned v = w < whi ? cbits[w] : 0u;
+    const int c = __popc(v);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    __syncthreads();
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    int woff = 0, tot = 0;
+    for (int j = 0; j < nwarp; ++j) {
+      const int cc = s_w[j];
+      if (j < wid) woff += cc;
+      tot += cc;
+    }
+    int pos = run + woff + incl - c;
+    unsigned rest = v;
+    while (rest) {
+      const int b = __ffs(rest) - 1;
+      rest &= rest - 1u;
+      ma.idx[pos++] = (int)(32 * w + b);
+    }
+    run += tot;
+  }
+  const int ncomp = s_tot;
+  if (!grid_barrier(ca.st, bar, 61)) return;
+  metadata_phase<N>(ma, ncomp);
+}
+
+// ints of scratch the set-up kernel needs: one count per CTA, then one bit
+// per node
+int init_scratch_ints(long long size) { return MAX_BLOCKS + (int)((size + 31) / 32); }
+
+template <int N>
+static void* init_fn() {
+  return (void*)init_domain_kernel<N>;
+}
 
 cudaError_t launch_init_domain(const ClassifyArgs& ca, const MetaArgs& ma, int* tile_count, int* ncomp_dev,
                                cudaStream_t stream) {
-  const int ntiles = scan_tiles(ca.g.size);
-  classify_count_kernel<<<ntiles, SCAN_NT, 0, stream>>>(ca);
-  scan_tiles_kernel<<<1, 1024, 0, stream>>>(tile_count, ntiles, ncomp_dev);
-  scatter_kernel<<<ntiles, SCAN_NT, 0, stream>>>(ca.g, ca.kind, tile_count, ma.idx);
-  cudaMemsetAsync(ma.gersh, 0, sizeof(double), stream);
-  const int nb = 152 * 8;
+  (void)tile_count;
+  (void)ncomp_dev;
+  void* fn;
   switch (ma.g.ndim) {
-    case 2: metadata_kernel<2><<<nb, 256, 0, stream>>>(ma); break;
-    case 3: metadata_kernel<3><<<nb, 256, 0, stream>>>(ma); break;
-    case 4: metadata_kernel<4><<<nb, 256, 0, stream>>>(ma); break;
+    case 2: fn = init_fn<2>(); break;
+    case 3: fn = init_fn<3>(); break;
+    case 4: fn = init_fn<4>(); break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  int dev = 0, sms = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, INIT_NT, 0);
+  if (e != cudaSuccess) return e;
+  if (per < 1) return cudaErrorLaunchOutOfResources;
+  const int nb = min(sms, MAX_BLOCKS);
+  e = cudaMemsetAsync(&ca.st->barrier, 0, sizeof(unsigned), stream);
+  if (e != cudaSuccess) return e;
+  ClassifyArgs c1 = ca;
+  MetaArgs m1 = ma;
+  void* args[] = {(void*)&c1, (void*)&m1};
+  return cudaLaunchCooperativeKernel(fn, nb, INIT_NT, args, 0, stream);
 }
 
 }  // namespace etd

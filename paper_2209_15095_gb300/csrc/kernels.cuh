@@ -25,7 +25,7 @@ struct MetaArgs {
   const double* phi;
   const uint8_t* kind;
   int* idx;  // written by the compaction, read by the metadata pass
-  const int* ncomp;
+  int* ncomp;  // written by the compaction, read by the metadata pass
   const double* beta_field;  // node field or nullptr
   double beta_c;
   double* diag;
@@ -35,7 +35,7 @@ struct MetaArgs {
   DevStatus* st;
 };
 
-int scan_tiles(long long size);
+int init_scratch_ints(long long size);  // per-CTA counts of the set-up kernel
 cudaError_t launch_init_domain(const ClassifyArgs& ca, const MetaArgs& ma, int* tile_count, int* ncomp_dev,
                                cudaStream_t stream);
 

@@ -230,15 +230,6 @@ __device__ __forceinline__ double* part_buf(double* part, int& red) {
   return b;
 }
 
-// Index of this thread in the node loops: 32-index chunks dealt round-robin
-// over the CTAs (chunk j to warp j / gridDim of CTA j % gridDim), a
-// bijection onto [0, gridDim * blockDim).  A problem smaller than the grid
-// then spreads over every SM instead of filling the first CTAs, whose FP64
-// pipes are shared by all of their warps.
-__device__ __forceinline__ long long dealt_tid() {
-  return (long long)(threadIdx.x & 31) + 32ll * ((long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5));
-}
-
 template <typename T, int N>
 __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int sidx, Ctl& c, unsigned& bar,
                               int& red, double ynorm2, double vscale) {

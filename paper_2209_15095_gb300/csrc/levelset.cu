@@ -87,6 +87,7 @@ LevelsetBufs levelset_carve(const GridDev& g, const std::function<char*(size_t)>
   b.lcoord = (ushort4*)take(G * sizeof(ushort4));
   b.count = (int*)take(4 * sizeof(int));
   b.cta_count = (int*)take(MAX_BLOCKS * sizeof(int));
+  b.sw = (int*)take(8 * sizeof(int));
   b.vmax = (double*)take(sizeof(double));
   b.nsub = (int*)take(sizeof(int));
   b.info = (int*)take(8 * sizeof(int));
@@ -127,76 +128,92 @@ __device__ __forceinline__ long long nbr(const GridDev& g, long long p, const in
 }
 
 // ------------------------------------------------------------------ WENO5
-// Both one-sided HJ-WENO5 derivatives at a node from the six divided
-// differences q_0..q_5 (q_k = (f_{i+k-2} - f_{i+k-3}) / h), in the
-// equivalent form of Jiang & Peng (2000): with e_k = q_{k+1} - q_k,
+// Both one-sided HJ-WENO5 derivatives at a node from six consecutive
+// differences q_0..q_5 (q_k = f_{i+k-2} - f_{i+k-3}, optionally divided by
+// h), in the equivalent form of Jiang & Peng (2000): with e_k = q_{k+1} - q_k,
 //   d- = c - Phi(e0, e1, e2, e3),   d+ = c + Phi(e4, e3, e2, e1),
 //   c  = (7 (q2 + q3) - (q1 + q4)) / 12,
 //   Phi(a,b,c,d) = w0 (a - 2b + c) / 3 + (w2 - 1/2)(b - 2c + d) / 6,
 // w_k = alpha_k / sum alpha, alpha = (1, 6, 3) / (eps' + I_k)^2 with
 // I_0 = (13/3)(a-b)^2 + (a-3b)^2, I_1 = (13/3)(b-c)^2 + (b+c)^2,
 // I_2 = (13/3)(c-d)^2 + (3c-d)^2.  I_k is 4 times the smoothness indicator
-// of the usual weighted form with eps = 1e-6, so eps' = 4 eps gives the same
-// weights; the usual weighted sum of the three candidate stencils is the
-// same number up to rounding.  The second differences and c are shared by
-// the two sides; in FP64 the two sides also share one division.
+// of the usual weighted form with eps = 1e-6 (on divided differences), so
+// eps' = 4 eps (times h^2 on undivided ones) gives the same weights; the
+// usual weighted sum of the three candidate stencils is the same number up
+// to rounding.  Shared by the two sides: the second differences, c, the
+// squares (a-b)^2 of common pairs and b - 2c + d (equal on both sides).
+// With W = w0 + w1 + w2 (unnormalised): Phi = (2 w0 (a-b-(b-c)) +
+// (w2 - W/2)(b - 2c + d)) / (6 W).  In FP64 the two sides share one
+// division.
 template <typename C>
-__device__ __forceinline__ void weno5_side(C a, C b, C c, C d, C& num, C& den) {
-  constexpr C k13 = C(13.0 / 3.0), eps4 = C(4.0 * WENO_EPS);
-  const C t0 = a - b, t1 = b - c, t2 = c - d;
-  const C u0 = a - C(3) * b, u1 = b + c, u2 = C(3) * c - d;
-  const C i0 = k13 * (t0 * t0) + u0 * u0, i1 = k13 * (t1 * t1) + u1 * u1, i2 = k13 * (t2 * t2) + u2 * u2;
-  const C s0 = eps4 + i0, s1 = eps4 + i1, s2 = eps4 + i2;
-  const C d0 = s0 * s0, d1 = s1 * s1, d2 = s2 * s2;
-  const C w0 = d1 * d2, w1 = C(6) * (d0 * d2), w2 = C(3) * (d0 * d1);
-  den = w0 + w1 + w2;
-  num = w0 * ((t0 - t1) * C(1.0 / 3.0)) + (w2 - C(0.5) * den) * ((t1 - t2) * C(1.0 / 6.0));
-}
-
-template <typename C>
-__device__ __forceinline__ void weno5_pair(const C* q, C& dm, C& dp) {
+__device__ __forceinline__ void weno5_pair(const C* q, C epsw, C& dm, C& dp) {
+  constexpr C k13 = C(13.0 / 3.0);
   const C e0 = q[1] - q[0], e1 = q[2] - q[1], e2 = q[3] - q[2], e3 = q[4] - q[3], e4 = q[5] - q[4];
   const C cen = (C(7) * (q[2] + q[3]) - (q[1] + q[4])) * C(1.0 / 12.0);
-  C nm, sm, np, sp;
-  weno5_side<C>(e0, e1, e2, e3, nm, sm);
-  weno5_side<C>(e4, e3, e2, e1, np, sp);
+  // minus side (a,b,c,d) = (e0,e1,e2,e3): t = (ta, tb, tc);
+  // plus side (e4,e3,e2,e1): t = (td, -tc, -tb)
+  const C ta = e0 - e1, tb = e1 - e2, tc = e2 - e3, td = e4 - e3;
+  const C sa = ta * ta, sb = tb * tb, sc = tc * tc, sd = td * td;
+  const C e2x3 = C(3) * e2;
+  const C um0 = e0 - C(3) * e1, um1 = e1 + e2, um2 = e2x3 - e3;
+  const C up0 = e4 - C(3) * e3, up1 = e3 + e2, up2 = e2x3 - e1;
+  const C Y = tb - tc;
+  C num[2], den[2];
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const C i0 = side == 0 ? k13 * sa + um0 * um0 : k13 * sd + up0 * up0;
+    const C i1 = side == 0 ? k13 * sb + um1 * um1 : k13 * sc + up1 * up1;
+    const C i2 = side == 0 ? k13 * sc + um2 * um2 : k13 * sb + up2 * up2;
+    const C X = side == 0 ? ta - tb : td + tc;
+    const C s0 = epsw + i0, s1 = epsw + i1, s2 = epsw + i2;
+    const C d0 = s0 * s0, d1 = s1 * s1, d2 = s2 * s2;
+    const C w0 = d1 * d2, w1 = C(6) * (d0 * d2), w2 = C(3) * (d0 * d1);
+    const C W = w0 + w1 + w2;
+    den[side] = C(6) * W;
+    num[side] = w0 * (X + X) + (w2 - C(0.5) * W) * Y;
+  }
   if constexpr (sizeof(C) == 8) {
-    // sm, sp >= 10 (4 eps)^4 > 2.5e-21, and for |q| < 1e18 the product stays
-    // finite: it neither underflows nor overflows in FP64
-    const C r = C(1) / (sm * sp);
-    dm = cen - nm * (sp * r);
-    dp = cen + np * (sm * r);
+    // den >= 60 eps'^4 (> 1e-60 for h > 1e-6) and for |q| < 1e18 the
+    // product stays finite: it neither underflows nor overflows in FP64
+    const C r = C(1) / (den[0] * den[1]);
+    dm = cen - num[0] * (den[1] * r);
+    dp = cen + num[1] * (den[0] * r);
   } else {
-    dm = cen - nm / sm;
-    dp = cen + np / sp;
+    dm = cen - num[0] / den[0];
+    dp = cen + num[1] / den[1];
   }
 }
 
 // Godunov |grad phi| at node p from array src; positive: outward motion.
-// The divided differences are formed in FP64; C is the type of the WENO5
-// and Godunov arithmetic (double, or float on the FP32-mixed path).
+// FP64 (C = double): undivided differences, eps scaled by h^2, one factor
+// 1/h at the end.  FP32-mixed (C = float): differences formed in FP64 and
+// divided by h, then WENO5 and Godunov in FP32 (an eps scaled by h^2 would
+// leave the FP32 normal range).
 template <typename C, int N>
 __device__ double godunov(const GridDev& g, const double* __restrict__ src, long long p, const int* ix,
                           bool positive) {
+  constexpr bool RAW = sizeof(C) == 8;
   const double inv_h = 1.0 / g.h;
+  const C epsw = RAW ? C(4.0 * WENO_EPS * g.h * g.h) : C(4.0 * WENO_EPS);
   C acc = C(0);
 #pragma unroll
   for (int d = 0; d < N; ++d) {
     double f[7];
 #pragma unroll
     for (int k = -3; k <= 3; ++k) f[k + 3] = __ldcg(src + nbr(g, p, ix, d, k));
-    C q[6];  // q[k+2] = (f(i+k) - f(i+k-1)) / h, k = -2..3
+    C q[6];
 #pragma unroll
-    for (int k = -2; k <= 3; ++k) q[k + 2] = C((f[k + 3] - f[k + 2]) * inv_h);
+    for (int k = -2; k <= 3; ++k) q[k + 2] = RAW ? C(f[k + 3] - f[k + 2]) : C((f[k + 3] - f[k + 2]) * inv_h);
     C dm, dp;
-    weno5_pair<C>(q, dm, dp);
-    // outward: max(d-, 0)^2 against min(d+, 0)^2; inward: the mirror image.
-    // Written with exact sign flips and no branch, so that no FP64 work of
-    // the other case is issued predicated off.
-    const C x = fmax(positive ? dm : -dm, C(0)), y = fmax(positive ? -dp : dp, C(0));
-    acc += fmax(x * x, y * y);
+    weno5_pair<C>(q, epsw, dm, dp);
+    // outward: max(max(d-, 0)^2, min(d+, 0)^2) = max(d-, -d+, 0)^2 (a square
+    // is monotone on the non-negatives); inward: the mirror image.  Exact
+    // sign flips and no branch, so that no FP64 work of the other case is
+    // issued predicated off.
+    const C mx = fmax(fmax(positive ? dm : -dm, positive ? -dp : dp), C(0));
+    acc = fma(mx, mx, acc);
   }
-  return (double)sqrt(acc);
+  return RAW ? (double)sqrt(acc) * inv_h : (double)sqrt(acc);
 }
 
 // ------------------------------------------------------------ work lists
@@ -408,6 +425,16 @@ __device__ bool build_work_set(const LsArgs& a, LsCtx& c, bool with_valid, int s
   return grid_barrier(a.st, c.bar, 25);
 }
 
+// Number of extension solves whose region holds a work-list entry with
+// flags f: the regions T minus V2 (u_nn), T minus V1 (u_n) and T minus V0 (u)
+// are nested because V2 lies in V1 and V1 in V0.
+__device__ __forceinline__ int sweep_level(uint8_t f) {
+  if (!(f & F_T)) return 0;
+  if (!(f & F_V0)) return 3;
+  if (!(f & F_V1)) return 2;
+  return (f & F_V2) ? 0 : 1;
+}
+
 // TVD-RK3 on the nodes of T (list order); L(src, p) supplied by the caller.
 // Stage values p1/p2 hold phi off T (copied when the work set is built).
 // The stage list holds the work-list positions of the update set T: entries
@@ -538,6 +565,7 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
     *a.b.vmax = 0.0;
     a.b.count[1] = 0;
     a.b.count[2] = 0;
+    for (int k = 0; k < 8; ++k) a.b.sw[k] = 0;
   }
   if (!build_work_set<N>(a, c, true, 0)) return;
   const int n = __ldcg(a.b.count);
@@ -545,7 +573,8 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
   double* const UNN[2] = {a.b.q[0], a.b.q[1]};
   double* const UN[2] = {a.b.q[2], a.b.q[3]};
   double* const U[2] = {a.b.q[4], a.b.q[5]};
-  // normals, u_0, u_n, stage buffers
+  // normals, u_0, u_n, stage buffers; counts of the sweep levels
+  int lc1 = 0, lc2 = 0, lc3 = 0;
   for (long long i = gtid; i < n; i += gth) {
     const long long p = __ldcg(a.b.list + i);
     int ix[N];
@@ -567,6 +596,10 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
       a.b.nrm[d * cap + i] = nv[d];
     }
     const uint8_t f = a.b.lflag[i];
+    const int lev = sweep_level(f);
+    lc1 += lev == 1;
+    lc2 += lev == 2;
+    lc3 += lev == 3;
     U[0][p] = (f & F_V0) ? a.u[p] : 0.0;
     double un = 0.0;
     if ((f & F_V1) && (f & F_T2)) {
@@ -578,26 +611,64 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
     a.b.p1[p] = a.phi[p];
     a.b.p2[p] = a.phi[p];
   }
-  if (!grid_barrier(a.st, c.bar, 51)) return;
-  for (long long i = gtid; i < n; i += gth) {
-    const long long p = __ldcg(a.b.list + i);
-    const uint8_t f = a.b.lflag[i];
-    double unn = 0.0;
-    if ((f & F_V2) && (f & F_T1)) {
-      int ix[N];
-      unpack<N>(a.b.lcoord[i], ix);
-#pragma unroll
-      for (int d = 0; d < N; ++d)
-        unn += __ldcg(a.b.nrm + d * cap + i) *
-               (__ldcg(UN[0] + nbr(g, p, ix, d, 1)) - __ldcg(UN[0] + nbr(g, p, ix, d, -1)));
-      unn *= inv_2h;
+  {
+    const int lane = threadIdx.x & 31;
+    for (int o = 16; o > 0; o >>= 1) {
+      lc1 += __shfl_xor_sync(0xffffffffu, lc1, o);
+      lc2 += __shfl_xor_sync(0xffffffffu, lc2, o);
+      lc3 += __shfl_xor_sync(0xffffffffu, lc3, o);
     }
-    UNN[0][p] = unn;
+    if (lane == 0) {
+      if (lc1) atomicAdd(&a.b.sw[1], lc1);
+      if (lc2) atomicAdd(&a.b.sw[2], lc2);
+      if (lc3) atomicAdd(&a.b.sw[3], lc3);
+    }
+  }
+  if (!grid_barrier(a.st, c.bar, 51)) return;
+  // u_nn; the sweep list: entries of level 3, then 2, then 1 (warp-aggregated
+  // placement; the order within a level does not matter to a Jacobi sweep)
+  {
+    const int lane = threadIdx.x & 31;
+    const int c3 = __ldcg(a.b.sw + 3), c2 = __ldcg(a.b.sw + 2);
+    for (long long base = gtid - lane; base < n; base += gth) {
+      const long long i = base + lane;
+      int lev = 0;
+      if (i < n) {
+        const long long p = __ldcg(a.b.list + i);
+        const uint8_t f = a.b.lflag[i];
+        lev = sweep_level(f);
+        double unn = 0.0;
+        if ((f & F_V2) && (f & F_T1)) {
+          int ix[N];
+          unpack<N>(a.b.lcoord[i], ix);
+#pragma unroll
+          for (int d = 0; d < N; ++d)
+            unn += __ldcg(a.b.nrm + d * cap + i) *
+                   (__ldcg(UN[0] + nbr(g, p, ix, d, 1)) - __ldcg(UN[0] + nbr(g, p, ix, d, -1)));
+          unn *= inv_2h;
+        }
+        UNN[0][p] = unn;
+      }
+#pragma unroll
+      for (int L = 1; L <= 3; ++L) {
+        const unsigned m = __ballot_sync(0xffffffffu, lev == L);
+        if (m) {
+          const int leader = __ffs(m) - 1;
+          int b0 = 0;
+          if (lane == leader) b0 = atomicAdd(&a.b.sw[4 + L], __popc(m));
+          b0 = __shfl_sync(0xffffffffu, b0, leader);
+          const int seg = L == 3 ? 0 : (L == 2 ? c3 : c3 + c2);
+          if (lev == L) a.b.slist[seg + b0 + __popc(m & ((1u << lane) - 1u))] = (int)i;
+        }
+      }
+    }
   }
   if (!grid_barrier(a.st, c.bar, 52)) return;
   // three extrapolation sweeps.  Values off the sweep region never change,
   // so both ping-pong buffers get them once; each pass then touches only the
-  // region.  The first-order upwind step
+  // region: the first len_s entries of the sweep list, read in 32-entry
+  // chunks dealt round-robin over the CTAs (full warps on every SM).  The
+  // first-order upwind step
   //   q' = q - dtau (sum_d n_d D_d q - s),  D_d backward where n_d > 0,
   // is used in the rearranged form q' = c0 q + sum_d a_d q(up_d) + dtau s,
   // a_d = dtau |n_d| / h, c0 = 1 - sum_d a_d (equal up to rounding).  Each
@@ -607,12 +678,15 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
   const int K = (int)ceil(12.0 * sqrt((double)N));
   const double dtau = h / (2.0 * sqrt((double)N));
   const double dth = dtau * inv_h;
-  const uint8_t vbits[3] = {F_V2, F_V1, F_V0};
   double* const* bufs[3] = {UNN, UN, U};
   const double* src = nullptr;
   constexpr int SW_CACHE = 2;
+  const int* const swl = a.b.slist;
+  const int sc1 = __ldcg(a.b.sw + 1), sc2 = __ldcg(a.b.sw + 2), sc3 = __ldcg(a.b.sw + 3);
+  const long long jt = dealt_tid();
   for (int sw = 0; sw < 3; ++sw) {
     double* const* B = bufs[sw];
+    const long long len = sw == 0 ? sc1 + sc2 + sc3 : (sw == 1 ? sc2 + sc3 : sc3);
     for (long long i = gtid; i < n; i += gth) {
       const long long p = __ldcg(a.b.list + i);
       B[1][p] = __ldcg(B[0] + p);
@@ -622,8 +696,8 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
     double cq[SW_CACHE], cds[SW_CACHE], cc0[SW_CACHE], ca[SW_CACHE][N];
 #pragma unroll
     for (int r = 0; r < SW_CACHE; ++r) {
-      const long long i = gtid + r * gth;
-      creg[r] = false;
+      const long long j = jt + r * gth;
+      creg[r] = j < len;
       cp[r] = 0;
       cq[r] = cds[r] = cc0[r] = 0.0;
 #pragma unroll
@@ -631,26 +705,23 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
         cup[r][d] = 0;
         ca[r][d] = 0.0;
       }
-      if (i < n) {
+      if (creg[r]) {
+        const long long i = __ldcg(swl + j);
         const long long p = __ldcg(a.b.list + i);
-        const uint8_t f = a.b.lflag[i];
-        creg[r] = (f & F_T) && !(f & vbits[sw]);
-        if (creg[r]) {
-          cp[r] = (int)p;
-          cq[r] = __ldcg(B[0] + p);
-          cds[r] = src ? dtau * __ldcg(src + p) : 0.0;
-          int ix[N];
-          unpack<N>(a.b.lcoord[i], ix);
-          double asum = 0.0;
+        cp[r] = (int)p;
+        cq[r] = __ldcg(B[0] + p);
+        cds[r] = src ? dtau * __ldcg(src + p) : 0.0;
+        int ix[N];
+        unpack<N>(a.b.lcoord[i], ix);
+        double asum = 0.0;
 #pragma unroll
-          for (int d = 0; d < N; ++d) {
-            const double nd = __ldcg(a.b.nrm + d * cap + i);
-            cup[r][d] = (int)nbr(g, p, ix, d, nd > 0.0 ? -1 : 1);
-            ca[r][d] = dth * fabs(nd);
-            asum += ca[r][d];
-          }
-          cc0[r] = 1.0 - asum;
+        for (int d = 0; d < N; ++d) {
+          const double nd = __ldcg(a.b.nrm + d * cap + i);
+          cup[r][d] = (int)nbr(g, p, ix, d, nd > 0.0 ? -1 : 1);
+          ca[r][d] = dth * fabs(nd);
+          asum += ca[r][d];
         }
+        cc0[r] = 1.0 - asum;
       }
     }
     if (!grid_barrier(a.st, c.bar, 53)) return;
@@ -670,10 +741,9 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
         cq[r] = t;
         qn[cp[r]] = t;
       }
-      for (long long i = gtid + SW_CACHE * gth; i < n; i += gth) {
+      for (long long j = jt + SW_CACHE * gth; j < len; j += gth) {
+        const long long i = __ldcg(swl + j);
         const long long p = __ldcg(a.b.list + i);
-        const uint8_t f = a.b.lflag[i];
-        if (!((f & F_T) && !(f & vbits[sw]))) continue;
         int ix[N];
         unpack<N>(a.b.lcoord[i], ix);
         double asum = 0.0, qu[N], ad[N];

@@ -14,6 +14,7 @@ struct LevelsetBufs {
   int* slist;       // RK stage list: work-list positions of the update set
   int* count;       // [0] list length, [1] [2] stage-list front / back counts
   int* cta_count;   // per-CTA counts for the in-kernel compaction
+  int* sw;          // extension sweep list: [1..3] entries per level, [5..7] placement cursors
   double* vmax;     // [0] max Stefan speed on the tube
   int* nsub;        // [0] advection substeps of the last call
   int* info;        // last call: list and tube sizes, substeps (see levelset_last_stats)

@@ -96,7 +96,7 @@ extern "C" etd_status etd_phi_combination_noalloc(const etd_grid* grid, const do
   DevStatus* dst = cv.take<DevStatus>(1);
   StatsDev* stats = cv.take<StatsDev>(1);
   double* part = cv.take<double>(8 * MAX_BLOCKS);
-  int* tiles = cv.take<int>(scan_tiles(g.size) + 1);
+  int* tiles = cv.take<int>(init_scratch_ints(g.size) + 1);
   uint8_t* kind = cv.take<uint8_t>(G);
   int* idx = cv.take<int>(G);
   int* ncomp = cv.take<int>(1);
