@@ -35,6 +35,16 @@ constexpr double TAU_MIN = 1e-6;
 constexpr double BREAKDOWN_REL = 1e-12;
 constexpr float TAYLOR_THETA = 8.0f;
 constexpr int MAX_SUBSTEPS = 20000;  // bounded work per call
+// From SPLIT_MIN computational points on, a Krylov vector costs two passes
+// (V_j = w_j at the own points; after a barrier Z_j = A V_j and the sums)
+// instead of one pass that rebuilds w_j at all 2N + 1 stencil points: about
+// 15 instead of 30 FP64 instructions per point, which is what bounds FP64 at
+// those sizes, for one more barrier and 2 more vector accesses per point.
+// Each thread then keeps SPLIT_U points in flight.
+template <typename T>
+constexpr int SPLIT_MIN = sizeof(T) == 8 ? (1 << 17) : (1 << 18);
+template <typename T>
+constexpr int SPLIT_U = sizeof(T) == 8 ? 2 : 4;
 
 __constant__ double c_inv_fact[64];  // 1/k!
 
@@ -213,6 +223,22 @@ __device__ __forceinline__ double diag_of<double>(const SpeciesDev<double>& S, i
 template <>
 __device__ __forceinline__ float diag_of<float>(const SpeciesDev<float>& S, int k) { return __ldg(S.diagf + k); }
 
+// Exact widening to FP64.  For a float, normal values are widened on the
+// integer pipe (rebias the exponent, shift the mantissa): the hardware
+// conversion is an FP64-pipe instruction, which costs as much as an FMA.
+// Zero, subnormal, infinite and NaN values take the hardware conversion.
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) {
+  const unsigned f = __float_as_uint(x);
+  const unsigned e = (f >> 23) & 0xffu;
+  if (e - 1u < 254u) {
+    const unsigned hi = (f & 0x80000000u) | ((e + 896u) << 20) | ((f & 0x7fffffu) >> 3);
+    const unsigned lo = (f & 7u) << 29;
+    return __hiloint2double((int)hi, (int)lo);
+  }
+  return (double)x;
+}
+
 // w = ca Z + cb V1 + cc V2 at grid node q (zero off the computational set,
 // since all three arrays are).
 template <typename T>
@@ -242,6 +268,8 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   const double anorm = a.dt * (*S.gersh);
   const int m_max = a.m_max;
   const long long vs = g.size;
+  // large problems: split Lanczos pass (see SPLIT_MIN)
+  const bool split = ncomp >= SPLIT_MIN<T>;
   double* pb = nullptr;
   if (threadIdx.x == 0) {
     c.t = 0.0;
@@ -333,7 +361,60 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         const T* V1 = S.V + (long long)(j - 1) * vs;
         const T* V2 = S.V + (long long)(j >= 2 ? j - 2 : 0) * vs;
         T* Vj = S.V + (long long)j * vs;
-        {
+        if (split) {
+          // pass A_j: V_j = w_j at the own points only
+          constexpr int U = SPLIT_U<T>;
+          for (long long k0 = gtid; k0 < ncomp; k0 += U * gthreads) {
+            long long pk[U];
+            T zv[U], v1v[U], v2v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const long long k = k0 + u * gthreads;
+              pk[u] = k < ncomp ? (long long)__ldg(S.idx + k) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              if (pk[u] < 0) continue;
+              zv[u] = __ldcg(Zp + pk[u]);
+              v1v[u] = __ldcg(V1 + pk[u]);
+              v2v[u] = __ldcg(V2 + pk[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              if (pk[u] >= 0) Vj[pk[u]] = ca * zv[u] + cb * v1v[u] + cc * v2v[u];
+          }
+          if (!grid_barrier(a.st, bar, 15)) return false;
+          // pass B_j: Z_j = A V_j from the stored V_j, and the three sums
+          Acc<T> d1, d2, d3;
+          for (long long k0 = gtid; k0 < ncomp; k0 += U * gthreads) {
+            long long pk[U];
+            T dk[U], zv[U], wv[U], v1v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const long long k = k0 + u * gthreads;
+              pk[u] = k < ncomp ? (long long)__ldg(S.idx + k) : -1;
+              dk[u] = k < ncomp ? diag_of<T>(S, (int)k) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              if (pk[u] < 0) continue;
+              zv[u] = stencil<T, N>(Vj, pk[u], g, dk[u], S.beta_field, bc, cfac);
+              wv[u] = __ldcg(Vj + pk[u]);
+              v1v[u] = __ldcg(V1 + pk[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              if (pk[u] < 0) continue;
+              Zn[pk[u]] = zv[u];
+              d1.add(wv[u], wv[u]);
+              d2.add(zv[u], wv[u]);
+              d3.add(zv[u], v1v[u]);
+            }
+          }
+          double v[3] = {d1.value(), d2.value(), d3.value()};
+          pb = part_buf(a.part, red);
+          block_partials<3>(v, pb);
+        } else {
           Acc<T> d1, d2, d3;
           for (long long k = gtid; k < ncomp; k += gthreads) {
             const long long p = __ldg(S.idx + k);
@@ -443,7 +524,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
       for (long long k = gtid; k < ncomp; k += gthreads) {
         const long long p = __ldg(S.idx + k);
         double sum = 0.0;
-        for (int i = 0; i < m; ++i) sum = fma(c.coef[i], (double)__ldcg(S.V + (long long)i * vs + p), sum);
+        for (int i = 0; i < m; ++i) sum = fma(c.coef[i], to_f64(__ldcg(S.V + (long long)i * vs + p)), sum);
         double y = fma(tau, (double)__ldcg(S.W1g + p), __ldcg(S.Yc + k)) + sum;
         S.Yc[k] = y;
         S.Yg[p] = (T)y;

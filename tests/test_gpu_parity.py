@@ -161,6 +161,37 @@ def test_phi_combination_mixed(lib, ndim, n, box, kind):
     assert np.max(np.abs(yg - yo)) <= 1e-5 * np.max(np.abs(yo))
 
 
+@pytest.mark.parametrize("precision,n,split_min", [("fp64", 112, 1 << 17), ("mixed", 140, 1 << 18)])
+def test_phi_combination_large_split_pass(lib, precision, n, split_min):
+    """Problems of at least 2^17 (FP64) or 2^18 (FP32) computational points
+    take the split Lanczos pass (V_j stored, then Z_j = A V_j) with several
+    points in flight per thread."""
+    g, ph = _shape_phi(3, n, 2.0, "ball")
+    op = EBOperator(g, ph, 1.0)
+    assert op.ncomp >= split_min
+    tol = 1e-10 if precision == "fp64" else 1e-7
+    ctx = _ctx(lib, g, precision=precision, tol=tol, m_max=40)
+    ctx.init_domain(0, _dev(ph))
+    rng = np.random.default_rng(17)
+    if precision == "fp64":
+        vs = [rng.standard_normal(op.ncomp) for _ in range(3)]
+        dt = 4.0 * g.h * g.h
+    else:
+        u = rng.uniform(0, 1, op.ncomp)
+        dt = g.h * g.h
+        vs = [u, dt * u * (1 - u), 0.1 * dt * u * (1 - u)]
+    y = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    st = ctx.phi_combination(0, dt, *[_dev(op.to_grid(v)) for v in vs], y, stats=True)
+    yg = op.from_grid(y.cpu().numpy())
+    if precision == "fp64":
+        yo, tr = _compare_phipm(ctx, op, dt, vs, tol, 40, st, yg)
+        assert np.max(np.abs(yg - yo)) <= 1e-10 * np.max(np.abs(yo)), (st, tr)
+    else:
+        yo, _ = krylov.phipm(lambda x: dt * (op.C @ x), vs, 1e-12, 40, dt * op.gershgorin())
+        assert np.max(np.abs(yg - yo)) <= 1e-5 * np.max(np.abs(yo))
+    assert np.all(y.cpu().numpy()[~op.comp] == 0.0)
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
 def test_etd2_step_from_state(lib, precision, tol):
     g, ph = _shape_phi(3, 26, 2.0, "ellipsoid")
