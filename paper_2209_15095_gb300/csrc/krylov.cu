@@ -45,6 +45,8 @@ template <typename T>
 constexpr int SPLIT_MIN = sizeof(T) == 8 ? (1 << 17) : (1 << 18);
 template <typename T>
 constexpr int SPLIT_U = sizeof(T) == 8 ? 2 : 4;
+template <typename T>
+constexpr int SPLIT_UB = sizeof(T) == 8 ? 2 : 3;  // the stencil pass (register bound)
 
 __constant__ double c_inv_fact[64];  // 1/k!
 
@@ -54,6 +56,8 @@ struct Ctl {
   double low[MAX_M + 2];
   double scale[MAX_M + 2];  // 1 / |V_j|
   double coef[MAX_M + 2];   // tau^2 beta phi_2(tau H) e_1, times scale
+  float chi[MAX_M + 2];     // coef as a sum of two floats (FP32 basis sum)
+  float clo[MAX_M + 2];
   double yexp[64];
   // controller scalars
   double t, tau, ynorm, beta, err, hn;
@@ -247,6 +251,48 @@ __device__ __forceinline__ T wval(const T* __restrict__ Z, const T* __restrict__
   return ca * __ldcg(Z + q) + cb * __ldcg(V1 + q) + cc * __ldcg(V2 + q);
 }
 
+// Node loop over the computational points with U points per thread and
+// iteration: the indices of the U points are loaded first, then body(kk, pp)
+// issues all of its loads before its stores, so that a thread waits on memory
+// about twice per U points instead of twice per point.  U = 1 is the plain
+// loop.  pp[u] < 0 marks a slot past the end.
+template <int U, typename Body>
+__device__ __forceinline__ void node_loop(long long gtid, long long gth, int ncomp, const int* __restrict__ idx,
+                                          Body&& body) {
+  // the indices of the next iteration are loaded before this one's body, so
+  // that their latency overlaps its data loads
+  int nx[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const long long k = gtid + u * gth;
+    nx[u] = k < ncomp ? __ldg(idx + k) : -1;
+  }
+  for (long long k0 = gtid; k0 < ncomp; k0 += U * gth) {
+    long long kk[U], pp[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      kk[u] = k0 + u * gth;
+      pp[u] = nx[u];
+      const long long kn = kk[u] + U * gth;
+      nx[u] = kn < ncomp ? __ldg(idx + kn) : -1;
+    }
+    body(kk, pp);
+  }
+}
+
+// FP32 vectors: two points in flight per thread for problems of at least
+// SPLIT_MIN points, one below (where the loop is latency-bound on barriers
+// anyway).  FP64: one point (FP64 issue bounds these loops at those sizes,
+// and two points would spill registers).
+template <typename T, typename Body>
+__device__ __forceinline__ void node_loop_sized(long long gtid, long long gth, int ncomp, const int* __restrict__ idx,
+                                                Body&& body) {
+  if (sizeof(T) == 4 && ncomp >= SPLIT_MIN<T>) node_loop<2>(gtid, gth, ncomp, idx, body);
+  else node_loop<1>(gtid, gth, ncomp, idx, body);
+}
+
+#define NL_U(kk) ((int)(sizeof(kk) / sizeof((kk)[0])))
+
 // Runs phipm for one species; returns false if the kernel must stop.
 // Two partial-sum buffers used alternately: between two reductions that use
 // the same buffer every CTA has passed a barrier after reading it.
@@ -254,6 +300,29 @@ __device__ __forceinline__ double* part_buf(double* part, int& red) {
   double* b = part + (red & 1) * (4 * MAX_BLOCKS);
   ++red;
   return b;
+}
+
+// sum_i coef_i V_i[p] for an FP32 basis with error-free FP32 transformations
+// (Ogita, Rump & Oishi 2005, Dot2): coef_i = chi_i + clo_i as two floats,
+// chi_i V_i exactly as a product and its FMA-computed error, the running sum
+// by TwoSum, all error terms (and clo_i V_i) in a second float.  About 2^-46
+// relative to sum |coef_i V_i|, at FP32 rate instead of one FP64 FMA per
+// basis vector.
+__device__ __forceinline__ double basis_sum_f32(const Ctl& c, const float* __restrict__ V, long long vs, long long p,
+                                                int m) {
+  float s = 0.f, e = 0.f;
+#pragma unroll 4
+  for (int i = 0; i < m; ++i) {
+    const float a = __ldcg(V + (long long)i * vs + p);
+    const float pr = __fmul_rn(c.chi[i], a);
+    const float pe = __fmaf_rn(c.chi[i], a, -pr);
+    const float t = __fadd_rn(s, pr);
+    const float z = __fsub_rn(t, s);
+    const float te = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(pr, z));
+    s = t;
+    e = __fadd_rn(e, __fadd_rn(te, __fmaf_rn(c.clo[i], a, pe)));
+  }
+  return to_f64(s) + to_f64(e);
 }
 
 template <typename T, int N>
@@ -292,31 +361,56 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
     __syncthreads();
     const double t = c.t;
     // w_1 = A y + v_1 + t v_2
-    for (long long k = gtid; k < ncomp; k += gthreads) {
-      const long long p = __ldg(S.idx + k);
-      T ay = stencil<T, N>(S.Yg, p, g, diag_of<T>(S, (int)k), S.beta_field, bc, cfac);
-      T w1 = ay + __ldcg(S.V1c + k) + (T)t * __ldcg(S.V2c + k);
-      S.W1g[p] = w1;
-    }
+    node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
+      constexpr int U = NL_U(kk);
+      T ay[U], a1[U], a2[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (pp[u] < 0) continue;
+        ay[u] = stencil<T, N>(S.Yg, pp[u], g, diag_of<T>(S, (int)kk[u]), S.beta_field, bc, cfac);
+        a1[u] = __ldcg(S.V1c + kk[u]);
+        a2[u] = __ldcg(S.V2c + kk[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (pp[u] >= 0) S.W1g[pp[u]] = ay[u] + a1[u] + (T)t * a2[u];
+    });
     if (!grid_barrier(a.st, bar, 10)) return false;
     // w_2 = A w_1 + v_2 -> V_0 (unnormalised)
-    for (long long k = gtid; k < ncomp; k += gthreads) {
-      const long long p = __ldg(S.idx + k);
-      T aw = stencil<T, N>(S.W1g, p, g, diag_of<T>(S, (int)k), S.beta_field, bc, cfac);
-      S.V[p] = aw + __ldcg(S.V2c + k);
-    }
+    node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
+      constexpr int U = NL_U(kk);
+      T aw[U], a2[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (pp[u] < 0) continue;
+        aw[u] = stencil<T, N>(S.W1g, pp[u], g, diag_of<T>(S, (int)kk[u]), S.beta_field, bc, cfac);
+        a2[u] = __ldcg(S.V2c + kk[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (pp[u] >= 0) S.V[pp[u]] = aw[u] + a2[u];
+    });
     if (!grid_barrier(a.st, bar, 11)) return false;
     // P_0: Z_0 = A V_0, |V_0|^2, <Z_0, V_0>
     {
       Acc<T> d1, d2;
-      for (long long k = gtid; k < ncomp; k += gthreads) {
-        const long long p = __ldg(S.idx + k);
-        const T v = __ldcg(S.V + p);
-        const T z = stencil<T, N>(S.V, p, g, diag_of<T>(S, (int)k), S.beta_field, bc, cfac);
-        S.Z[0][p] = z;
-        d1.add(v, v);
-        d2.add(z, v);
-      }
+      node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
+        constexpr int U = NL_U(kk);
+        T vv[U], zz[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (pp[u] < 0) continue;
+          vv[u] = __ldcg(S.V + pp[u]);
+          zz[u] = stencil<T, N>(S.V, pp[u], g, diag_of<T>(S, (int)kk[u]), S.beta_field, bc, cfac);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (pp[u] < 0) continue;
+          S.Z[0][pp[u]] = zz[u];
+          d1.add(vv[u], vv[u]);
+          d2.add(zz[u], vv[u]);
+        }
+      });
       double v[2] = {d1.value(), d2.value()};
       pb = part_buf(a.part, red);
       block_partials<2>(v, pb);
@@ -364,53 +458,41 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         if (split) {
           // pass A_j: V_j = w_j at the own points only
           constexpr int U = SPLIT_U<T>;
-          for (long long k0 = gtid; k0 < ncomp; k0 += U * gthreads) {
-            long long pk[U];
+          node_loop<U>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
             T zv[U], v1v[U], v2v[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-              const long long k = k0 + u * gthreads;
-              pk[u] = k < ncomp ? (long long)__ldg(S.idx + k) : -1;
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-              if (pk[u] < 0) continue;
-              zv[u] = __ldcg(Zp + pk[u]);
-              v1v[u] = __ldcg(V1 + pk[u]);
-              v2v[u] = __ldcg(V2 + pk[u]);
+              if (pp[u] < 0) continue;
+              zv[u] = __ldcg(Zp + pp[u]);
+              v1v[u] = __ldcg(V1 + pp[u]);
+              v2v[u] = __ldcg(V2 + pp[u]);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u)
-              if (pk[u] >= 0) Vj[pk[u]] = ca * zv[u] + cb * v1v[u] + cc * v2v[u];
-          }
+              if (pp[u] >= 0) Vj[pp[u]] = ca * zv[u] + cb * v1v[u] + cc * v2v[u];
+          });
           if (!grid_barrier(a.st, bar, 15)) return false;
           // pass B_j: Z_j = A V_j from the stored V_j, and the three sums
           Acc<T> d1, d2, d3;
-          for (long long k0 = gtid; k0 < ncomp; k0 += U * gthreads) {
-            long long pk[U];
-            T dk[U], zv[U], wv[U], v1v[U];
+          node_loop<SPLIT_UB<T>>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
+            constexpr int UB = NL_U(kk);
+            T zv[UB], wv[UB], v1v[UB];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-              const long long k = k0 + u * gthreads;
-              pk[u] = k < ncomp ? (long long)__ldg(S.idx + k) : -1;
-              dk[u] = k < ncomp ? diag_of<T>(S, (int)k) : T(0);
+            for (int u = 0; u < UB; ++u) {
+              if (pp[u] < 0) continue;
+              zv[u] = stencil<T, N>(Vj, pp[u], g, diag_of<T>(S, (int)kk[u]), S.beta_field, bc, cfac);
+              wv[u] = __ldcg(Vj + pp[u]);
+              v1v[u] = __ldcg(V1 + pp[u]);
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-              if (pk[u] < 0) continue;
-              zv[u] = stencil<T, N>(Vj, pk[u], g, dk[u], S.beta_field, bc, cfac);
-              wv[u] = __ldcg(Vj + pk[u]);
-              v1v[u] = __ldcg(V1 + pk[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-              if (pk[u] < 0) continue;
-              Zn[pk[u]] = zv[u];
+            for (int u = 0; u < UB; ++u) {
+              if (pp[u] < 0) continue;
+              Zn[pp[u]] = zv[u];
               d1.add(wv[u], wv[u]);
               d2.add(zv[u], wv[u]);
               d3.add(zv[u], v1v[u]);
             }
-          }
+          });
           double v[3] = {d1.value(), d2.value(), d3.value()};
           pb = part_buf(a.part, red);
           block_partials<3>(v, pb);
@@ -521,10 +603,24 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
       const int m = c.m;
       const double tau = c.tau;
       Acc<double> yn;
+      if constexpr (sizeof(T) == 4) {
+        // coefficients split into two floats for the FP32 basis sum
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+          const float hi = (float)c.coef[i];
+          c.chi[i] = hi;
+          c.clo[i] = (float)(c.coef[i] - (double)hi);
+        }
+        __syncthreads();
+      }
       for (long long k = gtid; k < ncomp; k += gthreads) {
         const long long p = __ldg(S.idx + k);
-        double sum = 0.0;
-        for (int i = 0; i < m; ++i) sum = fma(c.coef[i], to_f64(__ldcg(S.V + (long long)i * vs + p)), sum);
+        double sum;
+        if constexpr (sizeof(T) == 4) {
+          sum = basis_sum_f32(c, S.V, vs, p, m);
+        } else {
+          sum = 0.0;
+          for (int i = 0; i < m; ++i) sum = fma(c.coef[i], to_f64(__ldcg(S.V + (long long)i * vs + p)), sum);
+        }
         double y = fma(tau, (double)__ldcg(S.W1g + p), __ldcg(S.Yc + k)) + sum;
         S.Yc[k] = y;
         S.Yg[p] = (T)y;
@@ -588,41 +684,51 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
     const SpeciesDev<T>& S = a.sp[s];
     const int ncomp = *S.ncomp;
     Acc<double> acc, acc1, acc2;
-    for (long long k = gtid; k < ncomp; k += gthreads) {
-      const long long p = __ldg(S.idx + k);
-      double y, v1, v2;
-      if (a.mode == MODE_GIVEN) {
-        y = a.given[0][p];
-        v1 = a.given[1][p];
-        v2 = a.given[2][p];
-      } else if (a.mode == MODE_EXPLICIT) {
-        const double u = a.given[0][p], um = a.given[1][p];
-        const double F = reaction(a.reaction, a.rp, 0, u, 0.0);
-        const double Fm = reaction(a.reaction, a.rp, 0, um, 0.0);
-        y = u;
-        v1 = a.dt * F;
-        v2 = a.dt * (F - Fm);
-      } else {
-        const double u = S.u[p];
-        double other = 0.0;
-        if (a.nspecies == 2) {
-          const SpeciesDev<T>& O = a.sp[1 - s];
-          other = (O.kind[p] & 3) == K_COMP ? O.u[p] : 0.0;
+    node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
+      constexpr int U = NL_U(kk);
+      double y[U], v1[U], v2[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        if (pp[q] < 0) continue;
+        const long long p = pp[q];
+        if (a.mode == MODE_GIVEN) {
+          y[q] = a.given[0][p];
+          v1[q] = a.given[1][p];
+          v2[q] = a.given[2][p];
+        } else if (a.mode == MODE_EXPLICIT) {
+          const double u = a.given[0][p], um = a.given[1][p];
+          const double F = reaction(a.reaction, a.rp, 0, u, 0.0);
+          const double Fm = reaction(a.reaction, a.rp, 0, um, 0.0);
+          y[q] = u;
+          v1[q] = a.dt * F;
+          v2[q] = a.dt * (F - Fm);
+        } else {
+          const double u = S.u[p];
+          double other = 0.0;
+          if (a.nspecies == 2) {
+            const SpeciesDev<T>& O = a.sp[1 - s];
+            other = (O.kind[p] & 3) == K_COMP ? O.u[p] : 0.0;
+          }
+          const double F = s == 0 ? reaction(a.reaction, a.rp, 0, u, other) : reaction(a.reaction, a.rp, 1, other, u);
+          const double Fp = S.fvalid[p] ? S.Fprev[p] : F;
+          y[q] = u;
+          v1[q] = a.dt * F;
+          v2[q] = a.dt * (F - Fp);
         }
-        const double F = s == 0 ? reaction(a.reaction, a.rp, 0, u, other) : reaction(a.reaction, a.rp, 1, other, u);
-        const double Fp = S.fvalid[p] ? S.Fprev[p] : F;
-        y = u;
-        v1 = a.dt * F;
-        v2 = a.dt * (F - Fp);
       }
-      S.Yc[k] = y;
-      S.Yg[p] = (T)y;
-      S.V1c[k] = (T)v1;
-      S.V2c[k] = (T)v2;
-      acc.add(y, y);
-      acc1.add(v1, v1);
-      acc2.add(v2, v2);
-    }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        if (pp[q] < 0) continue;
+        const long long k = kk[q], p = pp[q];
+        S.Yc[k] = y[q];
+        S.Yg[p] = (T)y[q];
+        S.V1c[k] = (T)v1[q];
+        S.V2c[k] = (T)v2[q];
+        acc.add(y[q], y[q]);
+        acc1.add(v1[q], v1[q]);
+        acc2.add(v2[q], v2[q]);
+      }
+    });
     sums[s][0] = acc.value();
     sums[s][1] = acc1.value();
     sums[s][2] = acc2.value();
@@ -665,10 +771,16 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
   for (int s = 0; s < a.nspecies; ++s) {
     const SpeciesDev<T>& S = a.sp[s];
     const int ncomp = *S.ncomp;
-    for (long long k = gtid; k < ncomp; k += gthreads) {
-      const long long p = __ldg(S.idx + k);
-      S.u[p] = __ldcg(S.Yc + k);
-    }
+    node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
+      constexpr int U = NL_U(kk);
+      double y[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q)
+        if (pp[q] >= 0) y[q] = __ldcg(S.Yc + kk[q]);
+#pragma unroll
+      for (int q = 0; q < U; ++q)
+        if (pp[q] >= 0) S.u[pp[q]] = y[q];
+    });
     // 16 nodes per thread and iteration: one 16-byte load of kinds, the
     // validity flags rewritten from them, unconditional zero stores for u.
     const long long n16 = g.size >> 4;
