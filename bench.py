@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--clocks", default="on", choices=["on", "off"])
     ap.add_argument("--no-stress", action="store_true")
     ap.add_argument("--stress-steps", type=int, default=3)
+    ap.add_argument("--stress-n", type=int, default=512, help="grid nodes per axis of the stress ball")
+    ap.add_argument("--stress-precision", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--stress-only", action="store_true",
+                    help="run only the stress shape and print its results (a profiling aid, not the bench line)")
     return ap.parse_args()
 
 
@@ -258,9 +262,11 @@ def main():
                 k += 1
             ctx.sync()
             times, parts, cells, iters, subs, ls_flops = [], [], 0, 0, 0, 0.0
+            nre = 0
             for _ in range(args.steps):
                 flush.zero_()
                 ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                nre += int(w.reinit_every > 0 and (k + 1) % w.reinit_every == 0)
                 one_step(ctx, phis, us, k, ev)
                 k += 1
                 st = ctx.last_stats()  # synchronises; outside the events
@@ -272,8 +278,15 @@ def main():
                 subs += sum(s_["substeps"] for s_ in st)
         ctx.sync()
         return {"ctx": ctx, "phis": phis, "us": us, "times": times, "parts": parts, "cells": cells,
-                "iters": iters, "substeps": subs, "k": k, "ls_flops": ls_flops}
+                "iters": iters, "substeps": subs, "k": k, "ls_flops": ls_flops, "reinit_steps": nre}
 
+    if args.stress_only:
+        if rank == 0:
+            del flush
+            torch.cuda.empty_cache()
+            print(json.dumps({"stress": run_stress(etd, stream, dev, args.stress_steps, args.stress_n,
+                                                   args.stress_precision)}))
+        return
     clocks = ClockSampler(local, enabled=args.clocks == "on" and rank == 0)
     r64 = run("fp64")
     rmx = None if args.no_mixed else run("mixed")
@@ -282,7 +295,7 @@ def main():
     if not args.no_stress and rank == 0:
         del flush
         torch.cuda.empty_cache()
-        stress = run_stress(etd, stream, dev, args.stress_steps)
+        stress = run_stress(etd, stream, dev, args.stress_steps, args.stress_n, args.stress_precision)
     clk = clocks.stop()
 
     t64 = sum(r64["times"]) / 1e3
@@ -355,6 +368,25 @@ def mixed_error(r64, rmx, nsp):
 # flops x 2.07 GHz (the measured FMA loop reaches 1.17 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# levelset_kernel<3> on star3d from one ncu capture (command and figures in
+# profiles/levelset_kernel_star3d.md), valid only for the kernel sources whose
+# SHA-256 prefix is recorded here; any change to them reports null.
+LS_TRAFFIC = {"sources": ("levelset.cu", "levelset.cuh", "common.cuh"), "sha256": "0a1a9dcc2431f9c6",
+              "no_reinit": 22.23e6, "reinit": 22.73e6}
+
+
+def levelset_traffic(reinit_fraction):
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in LS_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_2209_15095_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != LS_TRAFFIC["sha256"]:
+        return None
+    return (1.0 - reinit_fraction) * LS_TRAFFIC["no_reinit"] + reinit_fraction * LS_TRAFFIC["reinit"]
+
 
 def levelset_flops(info, ndim):
     """Algorithmic FP64 flops of one level-set launch, counted from the
@@ -399,7 +431,8 @@ def roofline(r, w, avg_parts, names):
     t_ls = avg_parts[0] / 1e3
     flops = r["ls_flops"] / steps
     ls = {"bound": "alu", "kernel": names[0], "achieved": flops / t_ls / 1e12, "peak": FP64_PEAK_TFLOPS,
-          "unit": "TFLOP/s", "frac": flops / t_ls / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+          "unit": "TFLOP/s", "frac": flops / t_ls / 1e12 / FP64_PEAK_TFLOPS,
+          "traffic": levelset_traffic(r["reinit_steps"] / steps) if w.name == "star3d" else None,
           "peak_source": "FP64 nominal: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (unit counts and clock); the measured FP64 FMA rate on this GB300 is 1.005 TFLOP/s",
           "algorithmic_flops_per_launch": flops}
     out = ls if dom == 0 else krylov
@@ -420,23 +453,25 @@ def krylov_bytes(ncomp, iters, subs, s):
     return ncomp * (iters * (3 * s + b) + subs * 2 * (3 * s + b) + (iters + 2 * subs) * s + subs * 16 + 48)
 
 
-def run_stress(etd, stream, dev, steps):
+def run_stress(etd, stream, dev, steps, n=512, precisions="both"):
     """Bandwidth stress shape: ETD2 steps on a fixed ball of radius 7 in a
-    512^3 grid (vectors far above L2), FP64 and FP32-mixed."""
+    512^3 grid over [-8, 8]^3 (vectors far above L2), FP64 and FP32-mixed.
+    Each precision: domain set-up, one warm-up step, then the timed steps."""
     import numpy as np
     import torch
 
     from paper_2209_15095_gb300 import inputs
 
-    w = inputs.ball512()
+    w = inputs.ball512(n=n)
     phi = torch.tensor(w.phi0[0], dtype=torch.float64, device=dev)
     u0 = torch.tensor(w.u0[0], dtype=torch.float64, device=dev)
     del w.phi0, w.u0
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    out = {"workload": "ball512", "grid": list(w.n), "dt": w.dt, "m_max": w.m_max, "steps": steps}
-    for precision in ("fp64", "mixed"):
+    out = {"workload": "ball512" if n == 512 else "ball%d" % n, "grid": list(w.n), "dt": w.dt, "m_max": w.m_max,
+           "steps": steps}
+    for precision in (("fp64", "mixed") if precisions == "both" else (precisions,)):
         torch.cuda.synchronize(dev)
         with torch.cuda.stream(stream):
             ctx = etd.Context(w.n, w.lo, w.hi, nspecies=1, precision=precision, tol=w.tol, m_max=w.m_max,
