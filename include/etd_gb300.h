@@ -58,14 +58,19 @@ typedef struct {
 
 enum { ETD_REACTION_NONE = 0, ETD_REACTION_LOGISTIC = 1, ETD_REACTION_LOGISTIC_AK = 2, ETD_REACTION_COMPETITION = 3 };
 enum { ETD_PRECISION_FP64 = 0, ETD_PRECISION_MIXED = 1 };
+enum { ETD_SCHEME_ETD1 = 1, ETD_SCHEME_ETD2 = 2, ETD_SCHEME_ETD2RK = 3 };
 
 /* Method parameters.
  *   nspecies    1 or 2
  *   precision   ETD_PRECISION_FP64: every vector and reduction in FP64.
  *               ETD_PRECISION_MIXED: Krylov vectors and the stencil in FP32,
- *               dot products / norms accumulated error-free in FP32 pairs and
- *               summed across the grid in FP64; H, the small exponential, the
- *               controller, u, F and the level set stay FP64.
+ *               dot products / norms and the basis combination accumulated
+ *               error-free in FP32 pairs and summed across the grid in FP64;
+ *               H, the small exponential, the controller, u and F stay FP64.
+ *               In the level set, phi, u, the extension, the Stefan speed and
+ *               the RK updates stay FP64; the HJ-WENO5/Godunov arithmetic is
+ *               FP32 for the advection and, beyond 3h from the interface, for
+ *               the reinitialisation.
  *   krylov_tol  relative tolerance of the adaptive Krylov evaluation
  *   m_max       largest Krylov basis, 5 <= m_max <= 61
  *   reaction    f(u):  NONE 0;  LOGISTIC u(1-u);  LOGISTIC_AK rp[0] u (1 - u/rp[1]);
@@ -73,7 +78,9 @@ enum { ETD_PRECISION_FP64 = 0, ETD_PRECISION_MIXED = 1 };
  *   mu[s]       Stefan coefficient of species s (boundary speed mu |grad u|)
  *   beta[s]     constant diffusion coefficient of species s, used when no
  *               beta field is given to etd_init_domain
- *   adjoint     1 to reserve the workspace of etd_adjoint_step (species 0) */
+ *   adjoint     1 to reserve the workspace of etd_adjoint_step (species 0)
+ *   scheme      time integrator of etd_step (Sec. 3.1-3.2): ETD_SCHEME_ETD1,
+ *               ETD_SCHEME_ETD2 (also selected by 0) or ETD_SCHEME_ETD2RK */
 typedef struct {
   int nspecies;
   int precision;
@@ -84,6 +91,7 @@ typedef struct {
   double mu[2];
   double beta[2];
   int adjoint;
+  int scheme;
 } etd_params;
 
 #define ETD_TRACE_MAX 64
@@ -124,14 +132,22 @@ void etd_destroy(etd_ctx* ctx);
  * else a full-grid node field (face value = mean of the two nodes). */
 etd_status etd_init_domain(etd_ctx* ctx, int species, const double* phi, const double* beta_field);
 
-/* One ETD2 step (Sec. 3.1) of every species on the current domains:
- *   U_{n+1} = phi_0(dt C) U_n + dt phi_1(dt C) F_n + dt phi_2(dt C)(F_n - F_{n-1}),
- * the phi-combination (Eq. 3.9) evaluated by adaptive Krylov time-stepping of
- * the ODE of Eq. 3.10.  u[s] (device, full grid, in/out): read at the
- * computational points of species s; on return it holds U_{n+1} there and 0 at
- * every other node.  F_{n-1} is kept by the context; where a point was not
- * computational at the previous step (and at the first step) F_{n-1} = F_n.
- * stats: NULL for an asynchronous call, else filled after synchronising. */
+/* One time step of every species on the current domains, by the scheme of
+ * params->scheme:
+ *   ETD2   (Sec. 3.1)  U_{n+1} = phi_0(dt C) U_n + dt phi_1(dt C) F_n
+ *                                + dt phi_2(dt C)(F_n - F_{n-1});
+ *   ETD1   (Sec. 3.1)  the same without the phi_2 term;
+ *   ETD2RK (Sec. 3.2)  a_n = phi_0(dt C) U_n + dt phi_1(dt C) F_n (the ETD1 step),
+ *                      U_{n+1} = a_n + dt phi_2(dt C)(F(a_n) - F_n): two Krylov
+ *                      evaluations, the second with v_0 = v_1 = 0.
+ * Each phi-combination (Eq. 3.9) is evaluated by adaptive Krylov
+ * time-stepping of the ODE of Eq. 3.10.  u[s] (device, full grid, in/out):
+ * read at the computational points of species s; on return it holds U_{n+1}
+ * there and 0 at every other node.  F_{n-1} (ETD2) is kept by the context;
+ * where a point was not computational at the previous step (and at the first
+ * step) F_{n-1} = F_n.  stats: NULL for an asynchronous call, else filled
+ * after synchronising; for ETD2RK the counts add both evaluations and the
+ * trace lists the first evaluation's substeps, then the second's. */
 etd_status etd_step(etd_ctx* ctx, double dt, double* const* u, etd_step_stats* stats);
 
 /* The phi-combination alone (Sec. 3.3, Eq. 3.9 with p = 2):

@@ -1,5 +1,6 @@
-"""Reaction terms and the ETD1 / ETD2 steps (Sec. 3, Eq. 3.1-3.3 and the ETD1 /
-ETD2 formulas of Sec. 3.1), on a fixed embedded-boundary domain.
+"""Reaction terms and the ETD1 / ETD2 / ETD2RK steps (Sec. 3, Eq. 3.1-3.3, the
+ETD1 / ETD2 formulas of Sec. 3.1 and ETD2RK of Sec. 3.2), on a fixed
+embedded-boundary domain.
 
 Semi-discrete system (Eq. 3.2): U_t = C U + F(U, t) with C from oracle.eb.
 ETD2 (Cox-Matthews multistep, Sec. 3.1):
@@ -7,6 +8,11 @@ ETD2 (Cox-Matthews multistep, Sec. 3.1):
 i.e. the combination of Eq. 3.9 with A = dt C, v_0 = U_n, v_1 = dt F_n,
 v_2 = dt (F_n - F_{n-1}).  The first step takes F_{-1} = F_0 (a reading), which
 makes it exactly ETD1:  U_1 = U_0 + dt phi_1(dt C)(F_0 + C U_0).
+ETD2RK (Sec. 3.2):
+    a_n     = U_n + dt phi_1(dt C)(F_n + C U_n)      (= the ETD1 step)
+    U_{n+1} = U_n + dt phi_1(dt C)(F_n + C U_n) + dt phi_2(dt C)(F(a_n, t_n + dt) - F_n)
+            = a_n + dt phi_2(dt C)(F(a_n, t_n + dt) - F_n),
+so two combinations: (v_0, v_1, v_2) = (U_n, dt F_n, 0), then (0, 0, dt (F(a_n) - F_n)).
 """
 import numpy as np
 
@@ -58,17 +64,45 @@ def etd2_step(op, u_n, F_n, F_nm1, dt, tol=1e-10, m_max=40, exact=False, forced_
     return krylov.phipm(apply_A, vs, tol, m_max, anorm, forced_trace=forced_trace)
 
 
-def run_fixed_domain(op, u0, dt, nsteps, F_of, tol=1e-10, m_max=40, exact=False):
-    """nsteps ETD2 steps on a fixed domain.  F_of(U, t) -> F vector.
-    Returns U at t = nsteps dt."""
+def combination(op, vs, dt, tol=1e-10, m_max=40, exact=False, forced_trace=None):
+    """phi_0(dt C) v_0 + phi_1(dt C) v_1 + phi_2(dt C) v_2 (Eq. 3.9): the dense
+    augmented expm (exact=True, small grids) or the adaptive Krylov phipm.
+    Returns (y, trace)."""
+    if exact:
+        return phi.combination_expm(dt * op.C.toarray(), vs), []
+    C = op.C
+    return krylov.phipm(lambda x: dt * (C @ x), vs, tol, m_max, dt * op.gershgorin(), forced_trace=forced_trace)
+
+
+def etd1_step(op, u_n, F_n, dt, tol=1e-10, m_max=40, exact=False):
+    """One ETD1 step: U_{n+1} = phi_0(dt C) U_n + dt phi_1(dt C) F_n."""
+    return combination(op, [u_n, dt * F_n, np.zeros_like(u_n)], dt, tol, m_max, exact)
+
+
+def etd2rk_step(op, u_n, F_of, t_n, dt, tol=1e-10, m_max=40, exact=False):
+    """One ETD2RK step (Sec. 3.2).  F_of(U, t) -> F vector.  Returns
+    (U_{n+1}, a_n, (trace of the first combination, trace of the second))."""
+    F_n = F_of(u_n, t_n)
+    a, tr1 = etd1_step(op, u_n, F_n, dt, tol, m_max, exact)
+    z = np.zeros_like(u_n)
+    d, tr2 = combination(op, [z, z, dt * (F_of(a, t_n + dt) - F_n)], dt, tol, m_max, exact)
+    return a + d, a, (tr1, tr2)
+
+
+def run_fixed_domain(op, u0, dt, nsteps, F_of, tol=1e-10, m_max=40, exact=False, scheme="etd2"):
+    """nsteps steps of `scheme` (etd1, etd2 or etd2rk) on a fixed domain.
+    F_of(U, t) -> F vector.  Returns U at t = nsteps dt."""
     u = np.array(u0, dtype=np.float64, copy=True)
     F_prev = None
     t = 0.0
     for _ in range(nsteps):
-        F_n = F_of(u, t)
-        if F_prev is None:
+        if scheme == "etd2rk":
+            u, _, _ = etd2rk_step(op, u, F_of, t, dt, tol=tol, m_max=m_max, exact=exact)
+        else:
+            F_n = F_of(u, t)
+            if F_prev is None or scheme == "etd1":
+                F_prev = F_n
+            u, _ = etd2_step(op, u, F_n, F_prev, dt, tol=tol, m_max=m_max, exact=exact)
             F_prev = F_n
-        u, _ = etd2_step(op, u, F_n, F_prev, dt, tol=tol, m_max=m_max, exact=exact)
-        F_prev = F_n
         t += dt
     return u

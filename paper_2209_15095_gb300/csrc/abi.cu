@@ -129,6 +129,10 @@ bool check_params(const etd_params* p, std::string& why) {
     why = "krylov_tol must be positive";
     return false;
   }
+  if (p->scheme < 0 || p->scheme > ETD_SCHEME_ETD2RK) {
+    why = "unknown scheme";
+    return false;
+  }
   if (p->reaction < 0 || p->reaction > 3 || (p->reaction == ETD_REACTION_COMPETITION && p->nspecies != 2)) {
     why = "unknown reaction, or competition without two species";
     return false;
@@ -266,7 +270,7 @@ SpeciesDev<T> species_dev(etd_ctx* c, int s, double* u) {
 
 template <typename T>
 etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int species, const double* given[3],
-                     etd_step_stats* stats) {
+                     etd_step_stats* stats, bool etd1 = false, bool keep_stats = false) {
   PhipmArgs<T> a;
   memset(&a, 0, sizeof(a));
   a.g = c->g;
@@ -277,7 +281,8 @@ etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int spec
   a.tol = c->par.krylov_tol;
   a.reaction = c->par.reaction;
   for (int i = 0; i < 4; ++i) a.rp[i] = c->par.rp[i];
-  if (mode == MODE_ETD2) {
+  a.etd1 = etd1 ? 1 : 0;
+  if (mode == MODE_ETD2 || mode == MODE_RK2) {
     a.nspecies = c->par.nspecies;
     for (int s = 0; s < a.nspecies; ++s) a.sp[s] = species_dev<T>(c, s, u[s]);
   } else {
@@ -292,12 +297,15 @@ etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int spec
   a.part = c->part;
   a.st = c->st;
   a.stats = c->stats;
-  cudaError_t e = cudaMemsetAsync(c->stats, 0, sizeof(StatsDev), c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "stats reset");
+  cudaError_t e = cudaSuccess;
+  if (!keep_stats) {
+    e = cudaMemsetAsync(c->stats, 0, sizeof(StatsDev), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stats reset");
+  }
   e = launch_phipm<T>(a, c->nblocks, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "phipm launch");
   c->last_nspecies = a.nspecies;
-  c->last_species0 = mode == MODE_ETD2 ? 0 : species;
+  c->last_species0 = (mode == MODE_ETD2 || mode == MODE_RK2) ? 0 : species;
   if (!stats) return ETD_OK;
   return copy_stats(c, stats);
 }
@@ -407,8 +415,19 @@ etd_status etd_step(etd_ctx* c, double dt, double* const* u, etd_step_stats* sta
     if (!u[s]) return fail(c, ETD_ERR_ARG, "u[s] is NULL");
     if (!c->sp[s].ready) return fail(c, ETD_ERR_ARG, "etd_init_domain not called for every species");
   }
-  return c->fp32 ? run_phipm<float>(c, MODE_ETD2, dt, u, 0, nullptr, stats)
-                 : run_phipm<double>(c, MODE_ETD2, dt, u, 0, nullptr, stats);
+  const int scheme = c->par.scheme == 0 ? ETD_SCHEME_ETD2 : c->par.scheme;
+  if (scheme != ETD_SCHEME_ETD2RK) {
+    const bool etd1 = scheme == ETD_SCHEME_ETD1;
+    return c->fp32 ? run_phipm<float>(c, MODE_ETD2, dt, u, 0, nullptr, stats, etd1)
+                   : run_phipm<double>(c, MODE_ETD2, dt, u, 0, nullptr, stats, etd1);
+  }
+  // ETD2RK: the ETD1 step gives a_n in u (and leaves F_n in F_{n-1}'s
+  // store), then u += dt phi_2(dt C)(F(a_n) - F_n)
+  etd_status r = c->fp32 ? run_phipm<float>(c, MODE_ETD2, dt, u, 0, nullptr, nullptr, true)
+                         : run_phipm<double>(c, MODE_ETD2, dt, u, 0, nullptr, nullptr, true);
+  if (r != ETD_OK) return r;
+  return c->fp32 ? run_phipm<float>(c, MODE_RK2, dt, u, 0, nullptr, stats, false, true)
+                 : run_phipm<double>(c, MODE_RK2, dt, u, 0, nullptr, stats, false, true);
 }
 
 etd_status etd_phi_combination(etd_ctx* c, int species, double dt, const double* v0, const double* v1,

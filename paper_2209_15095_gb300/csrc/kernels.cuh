@@ -79,10 +79,13 @@ struct SpeciesDev {
 
 // mode of the phi-combination kernel
 enum : int {
-  MODE_ETD2 = 0,      // v0 = u, v1 = dt F(u), v2 = dt (F(u) - F_prev); writes u
+  MODE_ETD2 = 0,      // v0 = u, v1 = dt F(u), v2 = dt (F(u) - F_prev) (0 with etd1);
+                      // F_prev <- F(u); writes u
   MODE_GIVEN = 1,     // v0, v1, v2 given on the grid; writes the output field
   MODE_EXPLICIT = 2,  // given[0] = u_n, given[1] = u_{n-1}: v0 = u_n, v1 = dt F(u_n),
                       // v2 = dt (F(u_n) - F(u_{n-1})); writes the output field
+  MODE_RK2 = 3,       // second ETD2RK stage: v0 = v1 = 0, v2 = dt (F(u) - F_prev);
+                      // u <- u + result
 };
 
 template <typename T>
@@ -98,6 +101,7 @@ struct PhipmArgs {
   double rp[4];
   SpeciesDev<T> sp[2];
   const double* given[3];  // MODE_GIVEN: v0, v1, v2 on the grid (species 0)
+  int etd1;                // MODE_ETD2: v2 = 0 (the ETD1 step)
   double* part;
   DevStatus* st;
   StatsDev* stats;

@@ -62,6 +62,7 @@ struct Ctl {
   // controller scalars
   double t, tau, ynorm, beta, err, hn;
   int m, accepted, breakdown, last, abort, nrej;
+  int trace0;  // trace entries of earlier launches of the step (block 0)
 };
 
 // ---------------------------------------------------------------------------
@@ -339,6 +340,8 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   const long long vs = g.size;
   // large problems: split Lanczos pass (see SPLIT_MIN)
   const bool split = ncomp >= SPLIT_MIN<T>;
+  // the statistics accumulate over the launches of one step (zeroed by the host)
+  if (blockIdx.x == 0 && threadIdx.x == 0) c.trace0 = a.stats ? a.stats->trace_len[sidx] : 0;
   double* pb = nullptr;
   if (threadIdx.x == 0) {
     c.t = 0.0;
@@ -638,9 +641,10 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         const int m = c.m;
         if (blockIdx.x == 0 && a.stats) {
           StatsDev* st = a.stats;
-          if (nsub < TRACE_MAX) {  // the trace keeps the first TRACE_MAX substeps
-            st->trace_m[sidx][nsub] = m;
-            st->trace_tau[sidx][nsub] = c.tau;
+          const int ti = c.trace0 + nsub;  // after the entries of earlier launches of the step
+          if (ti < TRACE_MAX) {          // the trace keeps the first TRACE_MAX substeps
+            st->trace_m[sidx][ti] = m;
+            st->trace_tau[sidx][ti] = c.tau;
           }
           st->rejections[sidx] += c.nrej;
           st->iters[sidx] += m;
@@ -662,8 +666,8 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
     ++nsub;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats) {
-    a.stats->substeps[sidx] = nsub;
-    a.stats->trace_len[sidx] = min(nsub, TRACE_MAX);
+    a.stats->substeps[sidx] += nsub;
+    a.stats->trace_len[sidx] = min(c.trace0 + nsub, TRACE_MAX);
   }
   return true;
 }
@@ -703,6 +707,8 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
           v1[q] = a.dt * F;
           v2[q] = a.dt * (F - Fm);
         } else {
+          // MODE_ETD2 (v2 = 0 for ETD1), or the second ETD2RK stage MODE_RK2
+          // (u holds a_n, F_prev holds F_n: v0 = v1 = 0, v2 = dt (F(a_n) - F_n))
           const double u = S.u[p];
           double other = 0.0;
           if (a.nspecies == 2) {
@@ -711,9 +717,10 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
           }
           const double F = s == 0 ? reaction(a.reaction, a.rp, 0, u, other) : reaction(a.reaction, a.rp, 1, other, u);
           const double Fp = S.fvalid[p] ? S.Fprev[p] : F;
-          y[q] = u;
-          v1[q] = a.dt * F;
-          v2[q] = a.dt * (F - Fp);
+          const bool rk2 = a.mode == MODE_RK2;
+          y[q] = rk2 ? 0.0 : u;
+          v1[q] = rk2 ? 0.0 : a.dt * F;
+          v2[q] = a.etd1 ? 0.0 : a.dt * (F - Fp);
         }
       }
 #pragma unroll
@@ -771,15 +778,19 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
   for (int s = 0; s < a.nspecies; ++s) {
     const SpeciesDev<T>& S = a.sp[s];
     const int ncomp = *S.ncomp;
+    const bool add = a.mode == MODE_RK2;  // u <- a_n + the second stage's result
     node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
       constexpr int U = NL_U(kk);
-      double y[U];
+      double y[U], b[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        if (pp[q] < 0) continue;
+        y[q] = __ldcg(S.Yc + kk[q]);
+        b[q] = add ? S.u[pp[q]] : 0.0;
+      }
 #pragma unroll
       for (int q = 0; q < U; ++q)
-        if (pp[q] >= 0) y[q] = __ldcg(S.Yc + kk[q]);
-#pragma unroll
-      for (int q = 0; q < U; ++q)
-        if (pp[q] >= 0) S.u[pp[q]] = y[q];
+        if (pp[q] >= 0) S.u[pp[q]] = add ? b[q] + y[q] : y[q];
     });
     // 16 nodes per thread and iteration: one 16-byte load of kinds, the
     // validity flags rewritten from them, unconditional zero stores for u.

@@ -43,7 +43,10 @@ class Grid(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("nspecies", ctypes.c_int), ("precision", ctypes.c_int), ("krylov_tol", ctypes.c_double),
                 ("m_max", ctypes.c_int), ("reaction", ctypes.c_int), ("rp", ctypes.c_double * 4),
-                ("mu", ctypes.c_double * 2), ("beta", ctypes.c_double * 2), ("adjoint", ctypes.c_int)]
+                ("mu", ctypes.c_double * 2), ("beta", ctypes.c_double * 2), ("adjoint", ctypes.c_int),
+                ("scheme", ctypes.c_int)]
+
+SCHEMES = {"etd1": 1, "etd2": 2, "etd2rk": 3}
 
 
 class StepStats(ctypes.Structure):
@@ -121,7 +124,7 @@ class Context:
     """One library context: grid, parameters, workspace and stream."""
 
     def __init__(self, n, lo, hi, nspecies=1, precision="fp64", tol=1e-8, m_max=30, reaction="logistic",
-                 rparams=(), mu=(1.0, 1.0), beta=(1.0, 1.0), device=None, adjoint=False):
+                 rparams=(), mu=(1.0, 1.0), beta=(1.0, 1.0), device=None, adjoint=False, scheme="etd2"):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
         self.lib = library()
@@ -138,6 +141,7 @@ class Context:
         p = Params()
         p.nspecies = nspecies
         p.precision = {"fp64": 0, "mixed": 1}[precision]
+        p.scheme = SCHEMES[scheme]
         p.krylov_tol = float(tol)
         p.m_max = int(m_max)
         p.reaction = REACTIONS[reaction]

@@ -217,6 +217,34 @@ def test_etd2_step_from_state(lib, precision, tol):
         assert np.all(ug[~op.comp] == 0.0)
 
 
+@pytest.mark.parametrize("scheme", ["etd1", "etd2rk"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_etd1_etd2rk_steps_from_state(lib, scheme, precision, tol):
+    """Two steps of ETD1 or ETD2RK (Sec. 3.1-3.2) through etd_step against the
+    oracle; ETD2RK runs two Krylov evaluations per step and the statistics
+    add both."""
+    g, ph = _shape_phi(3, 26, 2.0, "ellipsoid")
+    op = EBOperator(g, ph, 1.0)
+    ctx = _ctx(lib, g, precision=precision, tol=1e-10 if precision == "fp64" else 1e-6, m_max=40, scheme=scheme)
+    ctx.init_domain(0, _dev(ph))
+    rng = np.random.default_rng(9)
+    u0 = op.to_grid(rng.uniform(0, 1, op.ncomp))
+    du = torch.tensor(u0, device="cuda")
+    dt = 0.02
+    F = lambda v: v * (1 - v)
+    uo = op.from_grid(u0)
+    for _ in range(2):
+        st = ctx.step(dt, [du], stats=True)[0]
+        ug = du.cpu().numpy()
+        if scheme == "etd1":
+            uo, _ = oetd.etd1_step(op, uo, F(uo), dt, tol=1e-12, m_max=40)
+        else:
+            uo, _, _ = oetd.etd2rk_step(op, uo, lambda v, t: F(v), 0.0, dt, tol=1e-12, m_max=40)
+            assert st["substeps"] >= 2 and len(st["trace"]) == st["substeps"]
+        assert np.max(np.abs(op.from_grid(ug) - uo)) <= tol * np.max(np.abs(uo)) * 10
+        assert np.all(ug[~op.comp] == 0.0)
+
+
 def test_levelset_step_matches(lib):
     from paper_2209_15095_gb300 import inputs
 
