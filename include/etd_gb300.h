@@ -80,7 +80,9 @@ enum { ETD_SCHEME_ETD1 = 1, ETD_SCHEME_ETD2 = 2, ETD_SCHEME_ETD2RK = 3 };
  *               beta field is given to etd_init_domain
  *   adjoint     1 to reserve the workspace of etd_adjoint_step (species 0)
  *   scheme      time integrator of etd_step (Sec. 3.1-3.2): ETD_SCHEME_ETD1,
- *               ETD_SCHEME_ETD2 (also selected by 0) or ETD_SCHEME_ETD2RK */
+ *               ETD_SCHEME_ETD2 (also selected by 0) or ETD_SCHEME_ETD2RK
+ *   boundary_data  1 to reserve the workspace of nonzero Dirichlet data
+ *               (etd_boundary_points / etd_set_boundary_values) */
 typedef struct {
   int nspecies;
   int precision;
@@ -92,6 +94,7 @@ typedef struct {
   double beta[2];
   int adjoint;
   int scheme;
+  int boundary_data;
 } etd_params;
 
 #define ETD_TRACE_MAX 64
@@ -156,6 +159,35 @@ etd_status etd_step(etd_ctx* ctx, double dt, double* const* u, etd_step_stats* s
  * FP64 arrays; y is 0 off the computational set. */
 etd_status etd_phi_combination(etd_ctx* ctx, int species, double dt, const double* v0, const double* v1,
                                const double* v2, double* y, etd_step_stats* stats);
+
+/* Additive source term of F for `species` (Sec. 3, Eq. 3.2: F(U, t) = f(U) +
+ * sources): src_n (device, full grid FP64, caller-owned, read at the
+ * computational points) enters F_n in every following etd_step; src_np1 is
+ * the source at t_n + dt, read by the second ETD2RK stage (NULL: src_n).
+ * Both pointers must stay valid while steps that use them run; NULL clears.
+ * The stored F_{n-1} of ETD2 includes the source of its step. */
+etd_status etd_set_source(etd_ctx* ctx, int species, const double* src_n, const double* src_np1);
+
+/* Nonzero Dirichlet data u = u_Gamma on the boundary (Sec. 2: the ghost
+ * value of case 2 (Eq. DirichletLineByLine) is w u_p + g_Gamma u_Gamma at the
+ * crossing point, of case 3 in 2D (Eq. rbf_ubp) w u_p + c_1 u(Gamma1) +
+ * c_2 u(Gamma2); the boundary part goes to the right-hand side).  Needs
+ * params->boundary_data.  After etd_init_domain, returns the number of
+ * computational points (*ncomp) and of boundary slots per point (*slots =
+ * 2N faces x J, J = 2 for N = 2, else 1) and, if `points` (device, at least
+ * ncomp * slots * N doubles, caller-owned) is not NULL, copies the slot
+ * points there: slot (k, f, j) of computational point k (index-list order),
+ * face f (axis f / 2, side f % 2: -1, +1) at points[((k * 2N + f) * J + j) * N
+ * + 0..N-1]; slots without a boundary point hold NaN.  Synchronises.  A
+ * case-3 face in N >= 3 has no boundary reading: ETD_ERR_ARG. */
+etd_status etd_boundary_points(etd_ctx* ctx, int species, double* points, int* ncomp, int* slots);
+
+/* Boundary values u_Gamma at the slot points, in the slot order above
+ * (device, ncomp * slots doubles, caller-owned; NaN slots are ignored):
+ * values_n enter F_n of every following etd_step, values_np1 (t_n + dt,
+ * NULL: values_n) the second ETD2RK stage.  They must stay valid while steps
+ * that use them run; NULL clears. */
+etd_status etd_set_boundary_values(etd_ctx* ctx, int species, const double* values_n, const double* values_np1);
 
 /* Replace the reaction kind and parameters of the context (as in
  * etd_params; rp: host, 4 doubles). */

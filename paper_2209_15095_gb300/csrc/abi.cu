@@ -25,6 +25,13 @@ struct SpeciesBufs {
   void* V2c = nullptr;
   void* Z[2] = {nullptr, nullptr};
   const double* beta_field = nullptr;
+  // boundary data (params.boundary_data): per point, face and slot
+  double* bco = nullptr;
+  double* bpts = nullptr;
+  // caller's source fields and boundary values at t_n and t_{n+1} (device,
+  // caller-owned; the t_{n+1} ones are read by the second ETD2RK stage)
+  const double* src[2] = {nullptr, nullptr};
+  const double* bval[2] = {nullptr, nullptr};
   bool ready = false;
 };
 
@@ -91,6 +98,7 @@ bool check_grid(const etd_grid* grid, GridDev& g, std::string& why) {
     g.stride[d] = s;
     s *= grid->n[d];
   }
+  grid_divisors(g);
   double h0 = (grid->hi[0] - grid->lo[0]) / (grid->n[0] - 1);
   if (!(h0 > 0.0)) {
     why = "hi must exceed lo";
@@ -182,6 +190,17 @@ size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
   }
   LevelsetBufs lb = levelset_carve(g, [&](size_t bytes) { return cv.take<char>(bytes); });
   if (c) c->ls = lb;
+  if (p.boundary_data) {
+    const size_t slots = G * 2 * (size_t)g.ndim * (g.ndim == 2 ? 2 : 1);
+    for (int sp = 0; sp < p.nspecies; ++sp) {
+      double* bco = cv.take<double>(slots);
+      double* bpts = cv.take<double>(slots * (size_t)g.ndim);
+      if (c) {
+        c->sp[sp].bco = bco;
+        c->sp[sp].bpts = bpts;
+      }
+    }
+  }
   if (p.adjoint) {
     for (int i = 0; i < 8; ++i) {
       double* b = cv.take<double>(G);
@@ -216,6 +235,8 @@ etd_status read_status(etd_ctx* c) {
   if (err & ERRF_NONFINITE) return fail(c, ETD_ERR_NONFINITE, "non-finite value in a reduction");
   if (err & ERRF_DOMAIN) return fail(c, ETD_ERR_DOMAIN, "an inside node lies within 3 nodes of the box edge");
   if (err & ERRF_KRYLOV) return fail(c, ETD_ERR_KRYLOV, "Krylov tolerance not met at the smallest substep");
+  if (err & ERRF_UNSUPPORTED)
+    return fail(c, ETD_ERR_ARG, "nonzero boundary data at a case-3 ghost face is defined for N = 2 only");
   return fail(c, ETD_ERR_ARG, "a device list or trace outgrew its buffer");
 }
 
@@ -243,9 +264,12 @@ etd_status copy_stats(etd_ctx* c, etd_step_stats* stats) {
 }
 
 template <typename T>
-SpeciesDev<T> species_dev(etd_ctx* c, int s, double* u) {
+SpeciesDev<T> species_dev(etd_ctx* c, int s, double* u, int stage = 0) {
   SpeciesBufs& b = c->sp[s];
   SpeciesDev<T> d;
+  d.src = b.src[stage] ? b.src[stage] : b.src[0];
+  d.bco = b.bco;
+  d.bval = b.bval[stage] ? b.bval[stage] : b.bval[0];
   d.idx = b.idx;
   d.ncomp = b.ncomp;
   d.diag = b.diag;
@@ -284,7 +308,7 @@ etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int spec
   a.etd1 = etd1 ? 1 : 0;
   if (mode == MODE_ETD2 || mode == MODE_RK2) {
     a.nspecies = c->par.nspecies;
-    for (int s = 0; s < a.nspecies; ++s) a.sp[s] = species_dev<T>(c, s, u[s]);
+    for (int s = 0; s < a.nspecies; ++s) a.sp[s] = species_dev<T>(c, s, u[s], mode == MODE_RK2 ? 1 : 0);
   } else {
     a.nspecies = 1;
     a.sp[0] = species_dev<T>(c, species, u[0]);
@@ -400,6 +424,8 @@ etd_status etd_init_domain(etd_ctx* c, int species, const double* phi, const dou
   ma.diag = b.diag;
   ma.diagf = b.diagf;
   ma.facew = species == 0 ? c->facew : nullptr;
+  ma.bco = b.bco;
+  ma.bpts = b.bpts;
   ma.gersh = &c->st->gersh[species];
   ma.st = c->st;
   cudaError_t e = launch_init_domain(ca, ma, c->tile_count, b.ncomp, c->stream);
@@ -440,6 +466,46 @@ etd_status etd_phi_combination(etd_ctx* c, int species, double dt, const double*
   double* out[1] = {y};
   return c->fp32 ? run_phipm<float>(c, MODE_GIVEN, dt, out, species, given, stats)
                  : run_phipm<double>(c, MODE_GIVEN, dt, out, species, given, stats);
+}
+
+etd_status etd_set_source(etd_ctx* c, int species, const double* src_n, const double* src_np1) {
+  if (!c) return ETD_ERR_ARG;
+  if (species < 0 || species >= c->par.nspecies) return fail(c, ETD_ERR_ARG, "bad species");
+  c->sp[species].src[0] = src_n;
+  c->sp[species].src[1] = src_np1;
+  return ETD_OK;
+}
+
+etd_status etd_boundary_points(etd_ctx* c, int species, double* points, int* ncomp, int* slots) {
+  if (!c || !ncomp || !slots) return ETD_ERR_ARG;
+  if (species < 0 || species >= c->par.nspecies) return fail(c, ETD_ERR_ARG, "bad species");
+  if (!c->par.boundary_data) return fail(c, ETD_ERR_ARG, "created without boundary_data");
+  if (!c->sp[species].ready) return fail(c, ETD_ERR_ARG, "etd_init_domain not called");
+  etd_status rs = read_status(c);
+  if (rs != ETD_OK) return rs;
+  int n = 0;
+  cudaError_t e = cudaMemcpy(&n, c->sp[species].ncomp, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ncomp read");
+  const int N = c->g.ndim;
+  *ncomp = n;
+  *slots = 2 * N * (N == 2 ? 2 : 1);
+  if (points && n > 0) {
+    e = cudaMemcpyAsync(points, c->sp[species].bpts, (size_t)n * (size_t)(*slots) * N * sizeof(double),
+                        cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "boundary points copy");
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
+  }
+  return ETD_OK;
+}
+
+etd_status etd_set_boundary_values(etd_ctx* c, int species, const double* values_n, const double* values_np1) {
+  if (!c) return ETD_ERR_ARG;
+  if (species < 0 || species >= c->par.nspecies) return fail(c, ETD_ERR_ARG, "bad species");
+  if (!c->par.boundary_data && (values_n || values_np1)) return fail(c, ETD_ERR_ARG, "created without boundary_data");
+  c->sp[species].bval[0] = values_n;
+  c->sp[species].bval[1] = values_np1;
+  return ETD_OK;
 }
 
 etd_status etd_set_reaction(etd_ctx* c, int reaction, const double* rp) {

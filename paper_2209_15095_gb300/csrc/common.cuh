@@ -11,6 +11,23 @@ constexpr int MAXD = 4;
 constexpr int MAX_M = 61;           // largest Krylov basis (m + p + 1 <= 64)
 constexpr int MAX_BLOCKS = 1024;    // partial-sum slots per reduction quantity
 
+// Unsigned division of n < 2^31 by a divisor d >= 1 fixed at set-up, on the
+// integer pipe: with s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1,
+// n / d = (umulhi(m, n) + n) >> s (the round-up method of Granlund &
+// Montgomery 1994; the sum cannot overflow for n < 2^31).  A division by a
+// runtime divisor otherwise goes through float conversions, which GB300
+// issues at its FP64 rate.
+struct FastDiv {
+  unsigned m;
+  int s;
+  __host__ __device__ FastDiv() : m(1u), s(0) {}
+  __host__ explicit FastDiv(unsigned d) : s(0) {
+    while ((1ull << s) < (unsigned long long)d) ++s;
+    m = (unsigned)(((1ull << 32) * ((1ull << s) - d)) / d + 1ull);
+  }
+  __device__ __forceinline__ unsigned div(unsigned n) const { return (__umulhi(m, n) + n) >> s; }
+};
+
 struct GridDev {
   int ndim;
   int n[MAXD];
@@ -18,7 +35,22 @@ struct GridDev {
   long long size;
   double lo[MAXD];
   double h;
+  FastDiv sdiv[MAXD];  // by stride[d]
+  // bit-plane geometry of the level-set work sets (rows along the last axis
+  // padded to 32-bit words): by the words per row and by the row strides
+  // stride[d] / n[ndim - 1] of the other axes
+  FastDiv wdiv, rdiv[MAXD];
 };
+
+// Fills the FastDiv members of g from ndim, n and stride (host side).
+inline void grid_divisors(GridDev& g) {
+  const long long nx = g.n[g.ndim - 1];
+  for (int d = 0; d < g.ndim; ++d) {
+    g.sdiv[d] = FastDiv((unsigned)g.stride[d]);
+    g.rdiv[d] = FastDiv((unsigned)(g.stride[d] / nx > 0 ? g.stride[d] / nx : 1));
+  }
+  g.wdiv = FastDiv((unsigned)((nx + 31) / 32));
+}
 
 // node class in the low two bits of a kind byte
 enum : uint8_t { K_OUT = 0, K_GHOST = 1, K_COMP = 2 };
@@ -30,6 +62,7 @@ enum : int {
   ERRF_KRYLOV = 4,     // tolerance not met at tau_min
   ERRF_NONFINITE = 8,  // NaN / Inf in a reduction
   ERRF_CAPACITY = 16,  // a list or trace outgrew its buffer
+  ERRF_UNSUPPORTED = 32,  // boundary data at a case-3 face with N >= 3
 };
 
 struct DevStatus {

@@ -36,9 +36,16 @@ __device__ __forceinline__ bool negative(double x) {
 // 1/(2h), unit vectors use rsqrt, and the length test on Gamma2 - Gamma1 is
 // made on its square; the decisions are those of the plain formulas up to
 // rounding at the thresholds.
+// Boundary part of a case-3 ghost value in 2D, u_q = w u_p + c1 u(G1) + c2 u(G2)
+// (barycentric coordinates of x_q in the triangle x_p, G1, G2).
+struct Case3Bnd {
+  double c1, c2, G1[2], G2[2];
+  bool ok;  // false: no boundary part defined (N >= 3, or no gradient)
+};
+
 template <int N>
 __device__ double case3_weight(const GridDev& g, const double* __restrict__ phi, long long p, const int* ip,
-                               long long q, int dq, int s) {
+                               long long q, int dq, int s, Case3Bnd* bo = nullptr) {
   const double h = g.h;
   const double inv_2h = 0.5 / h;
   double xp[N], xq[N], gp[N], gq[N];
@@ -57,6 +64,7 @@ __device__ double case3_weight(const GridDev& g, const double* __restrict__ phi,
     nq2 += gq[d] * gq[d];
   }
   const double fallback = phq / php;
+  if (bo) bo->ok = false;
   if (!(np2 > 0.0) || !(nq2 > 0.0)) return fallback;
   const double cq = phq / nq2, cp = php / np2;
   double G1[N], G2[N];
@@ -68,8 +76,27 @@ __device__ double case3_weight(const GridDev& g, const double* __restrict__ phi,
   if (N == 2) {
     double e1x = G1[0] - xp[0], e1y = G1[1] - xp[1], e2x = G2[0] - xp[0], e2y = G2[1] - xp[1];
     double det = e1x * e2y - e1y * e2x;
-    if (fabs(det) < 1e-12 * h * h) return fallback;
+    if (bo) {
+      bo->ok = true;
+      bo->G1[0] = G1[0];
+      bo->G1[1] = G1[N - 1];
+      bo->G2[0] = G2[0];
+      bo->G2[1] = G2[N - 1];
+    }
+    if (fabs(det) < 1e-12 * h * h) {
+      // degenerate triangle: w = phi_q / phi_p, the rest carried by G1
+      if (bo) {
+        bo->c1 = 1.0 - fallback;
+        bo->c2 = 0.0;
+      }
+      return fallback;
+    }
     double f1x = G1[0] - xq[0], f1y = G1[1] - xq[1], f2x = G2[0] - xq[0], f2y = G2[1] - xq[1];
+    if (bo) {
+      const double dx = xq[0] - xp[0], dy = xq[1] - xp[1];
+      bo->c1 = (dx * e2y - dy * e2x) / det;
+      bo->c2 = (e1x * dy - e1y * dx) / det;
+    }
     return (f1x * f2y - f1y * f2x) / det;
   } else {
     double nb[N], t[N], n[N];
@@ -146,7 +173,7 @@ __device__ __forceinline__ void node_load(const GridDev& g, const double* __rest
 #pragma unroll
   for (int d = 0; d < N; ++d) {
     const unsigned st = (unsigned)g.stride[d];
-    const int i = (int)(rem / st);
+    const int i = (int)g.sdiv[d].div(rem);
     rem -= (unsigned)i * st;
     if (i == 0 || i == g.n[d] - 1) L.edge = true;
     if (i < 3 || i > g.n[d] - 4) L.near = true;
@@ -195,7 +222,7 @@ __device__ void metadata_phase(const MetaArgs& a, int ncomp) {
 #pragma unroll
         for (int e = 0; e < N; ++e) {
           const unsigned st = (unsigned)g.stride[e];
-          ip[e] = (int)(rem / st);
+          ip[e] = (int)g.sdiv[e].div(rem);
           rem -= (unsigned)ip[e] * st;
         }
       }
@@ -204,6 +231,14 @@ __device__ void metadata_phase(const MetaArgs& a, int ncomp) {
       const int iq = ip[d] + (si == 0 ? -1 : 1);
       const double bf = a.beta_field ? 0.5 * (a.beta_field[p] + a.beta_field[q]) : a.beta_c;
       double gw = 0.0;  // 1 - w on a ghost face, 0 on a face to a computational point
+      // boundary-data slots of this face: coefficient of u_Gamma in the row
+      // (beta_f c / h^2, the ghost value's weight on the boundary point) and
+      // the point; coefficient 0 and a NaN point where there is none
+      double bc[2] = {0.0, 0.0}, bx[2][N];
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int e = 0; e < N; ++e) bx[j][e] = __longlong_as_double(0x7ff8000000000000ll);
       if ((__ldcg(a.kind + q) & 3) == K_COMP) {
         cD = bf;
         cOff = bf;
@@ -217,8 +252,29 @@ __device__ void metadata_phase(const MetaArgs& a, int ncomp) {
         if (!negative(a.phi[r])) {
           const double theta = a.phi[q] / (a.phi[q] - a.phi[r]);
           wv = theta / (1.0 + theta);
+          if (a.bco) {
+            // case 2: the crossing at x_q + s theta h e_d, weight 1 / (1 + theta)
+            bc[0] = bf * (1.0 / (1.0 + theta)) / h2;
+#pragma unroll
+            for (int e = 0; e < N; ++e)
+              bx[0][e] = g.lo[e] + g.h * ip[e] + (e == d ? (si == 0 ? -1.0 : 1.0) * g.h * (1.0 + theta) : 0.0);
+          }
         } else {
-          wv = case3_weight<N>(g, a.phi, p, ip, q, d, si == 0 ? -1 : 1);
+          Case3Bnd cb;
+          wv = case3_weight<N>(g, a.phi, p, ip, q, d, si == 0 ? -1 : 1, a.bco ? &cb : nullptr);
+          if (a.bco) {
+            if (N == 2 && cb.ok) {
+              bc[0] = bf * cb.c1 / h2;
+              bc[1] = bf * cb.c2 / h2;
+              bx[0][0] = cb.G1[0];
+              bx[0][N - 1] = cb.G1[1];
+              bx[1][0] = cb.G2[0];
+              bx[1][N - 1] = cb.G2[1];
+            } else {
+              // nonzero boundary data at a case-3 face is defined for N = 2 only
+              atomicOr(&a.st->err, ERRF_UNSUPPORTED);
+            }
+          }
         }
         const double wc = fmin(fmax(wv, 0.0), 1.0);
         if (!(wc == wv)) ++nclamp;
@@ -226,6 +282,16 @@ __device__ void metadata_phase(const MetaArgs& a, int ncomp) {
         gw = 1.0 - wc;
       }
       if (a.facew) a.facew[k * FPR + f] = gw;
+      if (a.bco) {
+        const int J = N == 2 ? 2 : 1;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const long long slot = (k * FPR + f) * J + j;
+          a.bco[slot] = bc[j];
+#pragma unroll
+          for (int e = 0; e < N; ++e) a.bpts[slot * N + e] = bx[j][e];
+        }
+      }
     }
     double D = 0.0, off = 0.0;
 #pragma unroll

@@ -31,6 +31,8 @@ struct MetaArgs {
   double* diag;
   float* diagf;  // nullptr unless FP32 vectors are in use
   double* facew; // nullptr, or per point and face: 1 - w on ghost faces, 0 otherwise
+  double* bco;   // nullptr, or per point, face and slot (2 slots for N = 2, else 1):
+  double* bpts;  //   boundary-data coefficient and point (N doubles)
   double* gersh;
   DevStatus* st;
 };
@@ -75,6 +77,11 @@ struct SpeciesDev {
   T* V1c;
   T* V2c;
   T* Z[2];  // full grid: A V_j of the last two basis vectors (unnormalised)
+  // caller's source (full grid) and boundary data for this launch: F gains
+  // src[p] + sum over the point's face slots of bco * bval (nullptr: none)
+  const double* src;
+  const double* bco;
+  const double* bval;
 };
 
 // mode of the phi-combination kernel

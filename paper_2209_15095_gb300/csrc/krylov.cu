@@ -221,6 +221,26 @@ __device__ __forceinline__ double reaction(int kind, const double* rp, int speci
   }
 }
 
+// The caller's source and boundary-data terms of F at computational point k
+// (grid node p): src[p] plus, over the point's contiguous face slots, the
+// boundary coefficient times the boundary value (empty slots have
+// coefficient 0 and are skipped, their values being NaN).
+template <typename T, int N>
+__device__ __forceinline__ double extra_F(const SpeciesDev<T>& S, long long k, long long p) {
+  double e = 0.0;
+  if (S.src) e += S.src[p];
+  if (S.bco && S.bval) {
+    constexpr int SL = 2 * N * (N == 2 ? 2 : 1);
+    const long long b = k * SL;
+#pragma unroll
+    for (int i = 0; i < SL; ++i) {
+      const double cf = S.bco[b + i];
+      if (cf != 0.0) e = fma(cf, S.bval[b + i], e);
+    }
+  }
+  return e;
+}
+
 template <typename T>
 __device__ __forceinline__ T diag_of(const SpeciesDev<T>& S, int k);
 template <>
@@ -715,7 +735,8 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
             const SpeciesDev<T>& O = a.sp[1 - s];
             other = (O.kind[p] & 3) == K_COMP ? O.u[p] : 0.0;
           }
-          const double F = s == 0 ? reaction(a.reaction, a.rp, 0, u, other) : reaction(a.reaction, a.rp, 1, other, u);
+          const double F = (s == 0 ? reaction(a.reaction, a.rp, 0, u, other) : reaction(a.reaction, a.rp, 1, other, u)) +
+                           extra_F<T, N>(S, kk[q], p);
           const double Fp = S.fvalid[p] ? S.Fprev[p] : F;
           const bool rk2 = a.mode == MODE_RK2;
           y[q] = rk2 ? 0.0 : u;
@@ -763,7 +784,8 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
           const SpeciesDev<T>& O = a.sp[1 - s];
           other = (O.kind[p] & 3) == K_COMP ? O.u[p] : 0.0;
         }
-        const double F = s == 0 ? reaction(a.reaction, a.rp, 0, u, other) : reaction(a.reaction, a.rp, 1, other, u);
+        const double F = (s == 0 ? reaction(a.reaction, a.rp, 0, u, other) : reaction(a.reaction, a.rp, 1, other, u)) +
+                         extra_F<T, N>(S, k, p);
         S.Fprev[p] = F;
         S.fvalid[p] = 1;
       }

@@ -107,7 +107,7 @@ __device__ __forceinline__ void coords(const GridDev& g, long long p, int* ix) {
 #pragma unroll
   for (int d = 0; d < N; ++d) {
     const unsigned st = (unsigned)g.stride[d];
-    const unsigned q = rem / st;
+    const unsigned q = g.sdiv[d].div(rem);
     ix[d] = (int)q;
     rem -= q * st;
   }
@@ -257,7 +257,7 @@ __device__ bool build_work_set(const LsArgs& a, LsCtx& c, bool with_valid, int s
   }
   // pass A: one warp per word, a lane per node
   for (long long w = c.wlo + wid; w < c.whi; w += nwarp) {
-    const unsigned r = (unsigned)w / (unsigned)bg.W;
+    const unsigned r = g.wdiv.div((unsigned)w);
     const int x = (int)((unsigned)w - r * (unsigned)bg.W) * 32 + lane;
     bool sb = false, vb = false;
     if (x < bg.nx) {
@@ -281,12 +281,12 @@ __device__ bool build_work_set(const LsArgs& a, LsCtx& c, bool with_valid, int s
     const uint32_t* vsrc = pl + (P_V0 + pass) * bg.nw;
     uint32_t* vdst = pl + (P_V1 + pass) * bg.nw;
     for (long long w = c.wlo + threadIdx.x; w < c.whi; w += blockDim.x) {
-      unsigned r = (unsigned)w / (unsigned)bg.W;
+      unsigned r = g.wdiv.div((unsigned)w);
       const int wi = (int)((unsigned)w - r * (unsigned)bg.W);
       int ir[N > 1 ? N - 1 : 1];
 #pragma unroll
       for (int d = 0; d < N - 1; ++d) {
-        ir[d] = (int)(r / rstr[d]);
+        ir[d] = (int)g.rdiv[d].div(r);
         r -= (unsigned)ir[d] * rstr[d];
       }
       const unsigned tm = tail_mask(bg, wi);
@@ -377,15 +377,15 @@ __device__ bool build_work_set(const LsArgs& a, LsCtx& c, bool with_valid, int s
     }
     for (int k = 0; k < wid; ++k) woff += s_w[k];
     if (v) {
-      unsigned r = (unsigned)w / (unsigned)bg.W;
+      unsigned r = g.wdiv.div((unsigned)w);
       const int wi = (int)((unsigned)w - r * (unsigned)bg.W);
       int ix[N];
 #pragma unroll
       for (int d = 0; d < N - 1; ++d) {
-        ix[d] = (int)(r / rstr[d]);
+        ix[d] = (int)g.rdiv[d].div(r);
         r -= (unsigned)ix[d] * rstr[d];
       }
-      const long long row0 = (long long)((unsigned)w / (unsigned)bg.W) * bg.nx;
+      const long long row0 = (long long)(g.wdiv.div((unsigned)w)) * bg.nx;
       const unsigned wT = __ldcg(pl + P_T * bg.nw + w), wT1 = __ldcg(pl + P_T1 * bg.nw + w),
                      wT2 = __ldcg(pl + P_T2 * bg.nw + w);
       unsigned wV0 = 0, wV1 = 0, wV2 = 0;

@@ -56,6 +56,7 @@ bool grid_of(const etd_grid* grid, GridDev& g) {
     g.stride[d] = s;
     s *= grid->n[d];
   }
+  grid_divisors(g);
   const double h0 = (grid->hi[0] - grid->lo[0]) / (grid->n[0] - 1);
   if (!(h0 > 0.0)) return false;
   for (int d = 0; d < grid->ndim; ++d) {

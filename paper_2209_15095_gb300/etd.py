@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
     _fields_ = [("nspecies", ctypes.c_int), ("precision", ctypes.c_int), ("krylov_tol", ctypes.c_double),
                 ("m_max", ctypes.c_int), ("reaction", ctypes.c_int), ("rp", ctypes.c_double * 4),
                 ("mu", ctypes.c_double * 2), ("beta", ctypes.c_double * 2), ("adjoint", ctypes.c_int),
-                ("scheme", ctypes.c_int)]
+                ("scheme", ctypes.c_int), ("boundary_data", ctypes.c_int)]
 
 SCHEMES = {"etd1": 1, "etd2": 2, "etd2rk": 3}
 
@@ -97,6 +97,9 @@ def library():
         "levelset_last_stats": (I, [P, ctypes.POINTER(I)]),
         "etd_read_domain": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), P, P, P, I]),
         "etd_last_error": (ctypes.c_char_p, [P]),
+        "etd_set_source": (I, [P, I, P, P]),
+        "etd_boundary_points": (I, [P, I, P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "etd_set_boundary_values": (I, [P, I, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -124,7 +127,8 @@ class Context:
     """One library context: grid, parameters, workspace and stream."""
 
     def __init__(self, n, lo, hi, nspecies=1, precision="fp64", tol=1e-8, m_max=30, reaction="logistic",
-                 rparams=(), mu=(1.0, 1.0), beta=(1.0, 1.0), device=None, adjoint=False, scheme="etd2"):
+                 rparams=(), mu=(1.0, 1.0), beta=(1.0, 1.0), device=None, adjoint=False, scheme="etd2",
+                 boundary_data=False):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
         self.lib = library()
@@ -148,6 +152,7 @@ class Context:
         for i, v in enumerate(rparams):
             p.rp[i] = float(v)
         p.adjoint = 1 if adjoint else 0
+        p.boundary_data = 1 if boundary_data else 0
         for s in range(2):
             p.mu[s] = float(mu[s] if s < len(mu) else mu[-1])
             p.beta[s] = float(beta[s] if s < len(beta) else beta[-1])
@@ -166,6 +171,8 @@ class Context:
             raise EtdError(rc, "etd_create failed")
         self.ctx = ctx
         self._beta_fields = [None, None]
+        self._sources = [(None, None), (None, None)]  # the library reads them during steps
+        self._bvalues = [(None, None), (None, None)]
         self.adjoint_enabled = bool(adjoint)
 
     def __del__(self):
@@ -198,6 +205,34 @@ class Context:
                                                  _ptr(y, self.n, "y"),
                                                  ctypes.byref(st) if st is not None else None))
         return st.as_dict(1)[0] if st is not None else None
+
+    def set_source(self, species, src_n, src_np1=None):
+        """Additive source of F (full grid FP64) at t_n and, for ETD2RK's
+        second stage, at t_n + dt (None: src_n).  None clears."""
+        self._sources[species] = (src_n, src_np1)
+        self._check(self.lib.etd_set_source(self.ctx, species, _ptr(src_n, self.n, "src_n"),
+                                            _ptr(src_np1, self.n, "src_np1")))
+
+    def boundary_points(self, species):
+        """Boundary-data slot points of the current domain as a (ncomp, slots,
+        N) float64 CUDA tensor (NaN where a slot is empty)."""
+        n, sl = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self.lib.etd_boundary_points(self.ctx, species, None, ctypes.byref(n), ctypes.byref(sl)))
+        out = torch.empty((max(n.value, 1), sl.value, self.ndim), dtype=torch.float64, device=self.device)
+        self._check(self.lib.etd_boundary_points(self.ctx, species, ctypes.c_void_p(out.data_ptr()),
+                                                 ctypes.byref(n), ctypes.byref(sl)))
+        return out[:n.value]
+
+    def set_boundary_values(self, species, values_n, values_np1=None):
+        """Boundary values at the slot points ((ncomp, slots) float64 CUDA
+        tensors, t_n and t_n + dt).  None clears."""
+        for v, name in ((values_n, "values_n"), (values_np1, "values_np1")):
+            if v is not None and (not v.is_cuda or v.dtype != torch.float64 or not v.is_contiguous()):
+                raise TypeError("%s must be a contiguous float64 CUDA tensor" % name)
+        self._bvalues[species] = (values_n, values_np1)
+        self._check(self.lib.etd_set_boundary_values(
+            self.ctx, species, ctypes.c_void_p(values_n.data_ptr()) if values_n is not None else None,
+            ctypes.c_void_p(values_np1.data_ptr()) if values_np1 is not None else None))
 
     def set_reaction(self, reaction, rparams):
         rp = (ctypes.c_double * 4)(*([float(v) for v in rparams] + [0.0] * (4 - len(rparams))))
