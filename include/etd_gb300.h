@@ -160,6 +160,20 @@ etd_status etd_step(etd_ctx* ctx, double dt, double* const* u, etd_step_stats* s
 etd_status etd_phi_combination(etd_ctx* ctx, int species, double dt, const double* v0, const double* v1,
                                const double* v2, double* y, etd_step_stats* stats);
 
+/* Embedded-boundary Poisson solve (Sec. 2: div(beta grad u) = f with
+ * Dirichlet data; Sec. 4.1): at the computational points of `species`,
+ * C u + b = f, with C the operator of etd_init_domain (dt = 1) and b the
+ * boundary-data term of etd_set_boundary_values (values_n; none set: zero
+ * data).  Conjugate gradients on -C (symmetric positive definite, Sec. 2) in
+ * FP64.  f (device, full grid) is read at the computational points; u
+ * (device, full grid, in/out) holds the initial guess there and receives the
+ * solution (other nodes unchanged).  Stops when |r| <= tol |b - f|; after
+ * max_iter iterations without that, returns ETD_ERR_KRYLOV.  iters,
+ * rel_resid (host, optional): iterations and |r| / |b - f|.  Synchronises.
+ * FP64 contexts only (ETD_ERR_ARG otherwise). */
+etd_status etd_poisson_solve(etd_ctx* ctx, int species, const double* f, double* u, double tol, int max_iter,
+                             int* iters, double* rel_resid);
+
 /* Additive source term of F for `species` (Sec. 3, Eq. 3.2: F(U, t) = f(U) +
  * sources): src_n (device, full grid FP64, caller-owned, read at the
  * computational points) enters F_n in every following etd_step; src_np1 is

@@ -46,6 +46,7 @@ struct etd_ctx {
   StatsDev* stats = nullptr;
   double* part = nullptr;
   int* tile_count = nullptr;
+  double* pout = nullptr;  // 2 doubles: Poisson solve iterations and residual
   SpeciesBufs sp[2];
   LevelsetBufs ls;
   // adjoint (species 0): phi actions, quadrature vectors, face weights
@@ -162,11 +163,13 @@ size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
   DevStatus* st = cv.take<DevStatus>(1);
   StatsDev* stats = cv.take<StatsDev>(1);
   double* part = cv.take<double>(8 * MAX_BLOCKS);
+  double* pout = cv.take<double>(2);
   int* tiles = cv.take<int>(init_scratch_ints(g.size) + 1);
   if (c) {
     c->st = st;
     c->stats = stats;
     c->part = part;
+    c->pout = pout;
     c->tile_count = tiles;
   }
   for (int sp = 0; sp < p.nspecies; ++sp) {
@@ -506,6 +509,36 @@ etd_status etd_set_boundary_values(etd_ctx* c, int species, const double* values
   c->sp[species].bval[0] = values_n;
   c->sp[species].bval[1] = values_np1;
   return ETD_OK;
+}
+
+etd_status etd_poisson_solve(etd_ctx* c, int species, const double* f, double* u, double tol, int max_iter,
+                             int* iters, double* rel_resid) {
+  if (!c) return ETD_ERR_ARG;
+  if (species < 0 || species >= c->par.nspecies || !f || !u || !(tol > 0.0) || max_iter < 1)
+    return fail(c, ETD_ERR_ARG, "bad arguments");
+  if (c->fp32) return fail(c, ETD_ERR_ARG, "the Poisson solve needs an FP64 context");
+  if (!c->sp[species].ready) return fail(c, ETD_ERR_ARG, "etd_init_domain not called");
+  PoissonArgs a;
+  memset(&a, 0, sizeof(a));
+  a.g = c->g;
+  a.S = species_dev<double>(c, species, u);
+  a.S.src = nullptr;
+  a.f = f;
+  a.u = u;
+  a.tol = tol;
+  a.max_iter = max_iter;
+  a.part = c->part;
+  a.st = c->st;
+  a.out = c->pout;
+  cudaError_t e = launch_poisson(a, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "poisson launch");
+  etd_status rs = read_status(c);
+  double out[2] = {0.0, 0.0};
+  e = cudaMemcpy(out, c->pout, sizeof(out), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "poisson result read");
+  if (iters) *iters = (int)out[0];
+  if (rel_resid) *rel_resid = out[1];
+  return rs;
 }
 
 etd_status etd_set_reaction(etd_ctx* c, int reaction, const double* rp) {

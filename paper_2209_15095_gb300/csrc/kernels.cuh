@@ -118,6 +118,20 @@ template <typename T>
 cudaError_t launch_phipm(const PhipmArgs<T>& a, int nblocks, cudaStream_t stream);
 int phipm_max_blocks(int ndim, bool fp32);
 
+// Embedded-boundary Poisson solve by conjugate gradients (FP64)
+struct PoissonArgs {
+  GridDev g;
+  SpeciesDev<double> S;  // domain, beta, boundary data; Yg, Yc, V1c, V2c as CG vectors
+  const double* f;       // full grid: right-hand side
+  double* u;             // full grid: initial guess in, solution out (computational points)
+  double tol;            // relative residual |r| / |b - f|
+  int max_iter;
+  double* part;
+  DevStatus* st;
+  double* out;           // device, 2 doubles: iterations, final relative residual
+};
+cudaError_t launch_poisson(const PoissonArgs& a, cudaStream_t stream);
+
 // y = A x on the computational set (x, y full grid FP64), for parity tests
 struct ApplyArgs {
   GridDev g;

@@ -100,6 +100,7 @@ def library():
         "etd_set_source": (I, [P, I, P, P]),
         "etd_boundary_points": (I, [P, I, P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "etd_set_boundary_values": (I, [P, I, P, P]),
+        "etd_poisson_solve": (I, [P, I, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -205,6 +206,15 @@ class Context:
                                                  _ptr(y, self.n, "y"),
                                                  ctypes.byref(st) if st is not None else None))
         return st.as_dict(1)[0] if st is not None else None
+
+    def poisson_solve(self, species, f, u, tol=1e-12, max_iter=100000):
+        """Solve div(beta grad u) = f on the computational points (boundary data
+        from set_boundary_values); u holds the initial guess and receives the
+        solution.  Returns (iterations, relative residual)."""
+        it, res = ctypes.c_int(0), ctypes.c_double(0.0)
+        self._check(self.lib.etd_poisson_solve(self.ctx, species, _ptr(f, self.n, "f"), _ptr(u, self.n, "u"),
+                                               float(tol), int(max_iter), ctypes.byref(it), ctypes.byref(res)))
+        return it.value, res.value
 
     def set_source(self, species, src_n, src_np1=None):
         """Additive source of F (full grid FP64) at t_n and, for ETD2RK's

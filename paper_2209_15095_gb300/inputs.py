@@ -249,3 +249,53 @@ def fixed_ball(n, box, radius, ndim=3, beta=1.0):
     u0 = np.where(phi0 < 0, np.cos(math.pi * r / (2.0 * radius)), 0.0)
     return Workload(name="fixed_ball%dd" % ndim, n=(n,) * ndim, lo=lo, hi=hi, phi0=[phi0], u0=[u0],
                     beta=[beta], mu=[0.0], reaction="logistic", rparams=(), dt=1e-2, steps=1, tol=1e-8, m_max=40)
+
+
+def virus_radius_fn(samples=200001):
+    """Boundary of the virus-shaped domain of Sec. 4.1, x = (0.6 + 0.1 sin 12t)
+    cos t, y = (0.6 + 0.05 sin 12t) sin t, as a radius R(psi) of the polar
+    angle (the curve's polar angle increases strictly with t), interpolated
+    periodically from a dense sampling."""
+    t = np.linspace(0.0, 2.0 * math.pi, samples)
+    x = (0.6 + 0.1 * np.sin(12 * t)) * np.cos(t)
+    y = (0.6 + 0.05 * np.sin(12 * t)) * np.sin(t)
+    psi = np.unwrap(np.arctan2(y, x))
+    r = np.hypot(x, y)
+
+    def R(ang):
+        a = np.mod(ang - psi[0], 2.0 * math.pi) + psi[0]
+        return np.interp(a, psi, r)
+
+    return R
+
+
+def virus_exact(x, y):
+    """Exact solution u = e^x (x^2 sin y + y^2) of the Sec. 4.1 example."""
+    return np.exp(x) * (x * x * np.sin(y) + y * y)
+
+
+def virus_beta(x, y):
+    return 2.0 + np.sin(x * y)
+
+
+def virus_source(x, y):
+    """f = div(beta grad u) for the exact u and beta = 2 + sin(xy):
+    beta Lap u + grad beta . grad u, with Lap u = e^x (y^2 + 4x sin y + 2 sin y + 2)."""
+    ex = np.exp(x)
+    ux = ex * (x * x * np.sin(y) + y * y + 2 * x * np.sin(y))
+    uy = ex * (x * x * np.cos(y) + 2 * y)
+    lap = ex * (y * y + 4 * x * np.sin(y) + 2 * np.sin(y) + 2)
+    return virus_beta(x, y) * lap + y * np.cos(x * y) * ux + x * np.cos(x * y) * uy
+
+
+def virus2d(N=100):
+    """(N+1)^2 node grid on [-1, 1]^2 with the virus domain (phi = r - R(psi) < 0
+    inside), the beta node field, the source and the exact solution."""
+    n = (N + 1, N + 1)
+    lo, hi = (-1.0, -1.0), (1.0, 1.0)
+    x, y = grid_coords(n, lo, hi)
+    R = virus_radius_fn()
+    phi = np.hypot(x, y) - R(np.arctan2(y, x))
+    return Workload(name="virus2d", n=n, lo=lo, hi=hi, phi0=[phi], u0=[virus_exact(x, y)], beta=[1.0], mu=[0.0],
+                    reaction="none", rparams=(), dt=0.0, steps=0, tol=1e-12, m_max=40,
+                    beta_field=virus_beta(x, y), source=virus_source(x, y), exact=virus_exact)
