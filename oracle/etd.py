@@ -1,6 +1,6 @@
-"""Reaction terms and the ETD1 / ETD2 / ETD2RK steps (Sec. 3, Eq. 3.1-3.3, the
-ETD1 / ETD2 formulas of Sec. 3.1 and ETD2RK of Sec. 3.2), on a fixed
-embedded-boundary domain.
+"""Reaction terms and the ETD1 / ETD2 / ETD2RK / ETD3RK / ETD4RK steps (Sec. 3,
+Eq. 3.1-3.3, the ETD1 / ETD2 formulas of Sec. 3.1 and the Runge-Kutta forms
+of Sec. 3.2), on a fixed embedded-boundary domain.
 
 Semi-discrete system (Eq. 3.2): U_t = C U + F(U, t) with C from oracle.eb.
 ETD2 (Cox-Matthews multistep, Sec. 3.1):
@@ -13,6 +13,12 @@ ETD2RK (Sec. 3.2):
     U_{n+1} = U_n + dt phi_1(dt C)(F_n + C U_n) + dt phi_2(dt C)(F(a_n, t_n + dt) - F_n)
             = a_n + dt phi_2(dt C)(F(a_n, t_n + dt) - F_n),
 so two combinations: (v_0, v_1, v_2) = (U_n, dt F_n, 0), then (0, 0, dt (F(a_n) - F_n)).
+ETD3RK and ETD4RK (Sec. 3.2): the paper's stages in its order, each written as
+one combination using U + h phi_1(h C) C U = phi_0(h C) U.  The paper's phi_k
+are those of Eq. 3.7, phi_k(z) = int_0^1 e^{(1-l) z} l^{k-1} dl, so its phi_3
+is twice the standard phi_3 (which carries 1 / 2!); the paper's recursion,
+Eq. 3.8, confirms that normalisation.  The combinations here use the standard
+phi_k, so the phi_3 vector of the final stage is the paper's times two.
 """
 import numpy as np
 
@@ -65,9 +71,9 @@ def etd2_step(op, u_n, F_n, F_nm1, dt, tol=1e-10, m_max=40, exact=False, forced_
 
 
 def combination(op, vs, dt, tol=1e-10, m_max=40, exact=False, forced_trace=None):
-    """phi_0(dt C) v_0 + phi_1(dt C) v_1 + phi_2(dt C) v_2 (Eq. 3.9): the dense
-    augmented expm (exact=True, small grids) or the adaptive Krylov phipm.
-    Returns (y, trace)."""
+    """sum_k phi_k(dt C) v_k, k = 0 .. len(vs) - 1, standard phi_k (Eq. 3.9):
+    the dense augmented expm (exact=True, small grids) or the adaptive Krylov
+    phipm.  Returns (y, trace)."""
     if exact:
         return phi.combination_expm(dt * op.C.toarray(), vs), []
     C = op.C
@@ -89,8 +95,49 @@ def etd2rk_step(op, u_n, F_of, t_n, dt, tol=1e-10, m_max=40, exact=False):
     return a + d, a, (tr1, tr2)
 
 
+def etd3rk_step(op, u_n, F_of, t_n, dt, tol=1e-10, m_max=40, exact=False):
+    """One ETD3RK step (Sec. 3.2).  Returns (U_{n+1}, (a_n, b_n), traces)."""
+    z = np.zeros_like(u_n)
+    F_n = F_of(u_n, t_n)
+    # a_n = U_n + dt/2 phi_1(dt C / 2)(F_n + C U_n)
+    a, tr_a = combination(op, [u_n, 0.5 * dt * F_n, z], 0.5 * dt, tol, m_max, exact)
+    F_a = F_of(a, t_n + 0.5 * dt)
+    # b_n = U_n + dt phi_1(dt C)(C U_n + 2 F(a_n) - F_n)
+    b, tr_b = combination(op, [u_n, dt * (2.0 * F_a - F_n), z], dt, tol, m_max, exact)
+    F_b = F_of(b, t_n + dt)
+    # U_{n+1} = U_n + dt phi_1 (C U_n + F_n) + dt phi_2 (-3 F_n + 4 F(a_n) - F(b_n))
+    #         + dt phi_3 (2 F_n - 4 F(a_n) + 2 F(b_n)),  the paper's phi_3 = 2 x standard
+    v2 = dt * (-3.0 * F_n + 4.0 * F_a - F_b)
+    v3 = 2.0 * dt * (2.0 * F_n - 4.0 * F_a + 2.0 * F_b)
+    u, tr_u = combination(op, [u_n, dt * F_n, v2, v3], dt, tol, m_max, exact)
+    return u, (a, b), (tr_a, tr_b, tr_u)
+
+
+def etd4rk_step(op, u_n, F_of, t_n, dt, tol=1e-10, m_max=40, exact=False):
+    """One ETD4RK step (Sec. 3.2).  Returns (U_{n+1}, (a_n, b_n, c_n), traces)."""
+    z = np.zeros_like(u_n)
+    h2 = 0.5 * dt
+    F_n = F_of(u_n, t_n)
+    # a_n = U_n + dt/2 phi_1(dt C / 2)(F_n + C U_n)
+    a, tr_a = combination(op, [u_n, h2 * F_n, z], h2, tol, m_max, exact)
+    F_a = F_of(a, t_n + h2)
+    # b_n = U_n + dt/2 phi_1(dt C / 2)(F(a_n) + C U_n)
+    b, tr_b = combination(op, [u_n, h2 * F_a, z], h2, tol, m_max, exact)
+    F_b = F_of(b, t_n + h2)
+    # c_n = a_n + dt/2 phi_1(dt C / 2)(2 F(b_n) - F_n + C a_n)
+    c, tr_c = combination(op, [a, h2 * (2.0 * F_b - F_n), z], h2, tol, m_max, exact)
+    F_c = F_of(c, t_n + dt)
+    # U_{n+1} = U_n + dt phi_1 (C U_n + F_n)
+    #         + dt phi_2 (-3 F_n + 2 (F(a_n) + F(b_n)) - F(c_n))
+    #         + dt phi_3 (2 F_n - 2 (F(a_n) + F(b_n)) + 2 F(c_n)),  the paper's phi_3 = 2 x standard
+    v2 = dt * (-3.0 * F_n + 2.0 * (F_a + F_b) - F_c)
+    v3 = 2.0 * dt * (2.0 * F_n - 2.0 * (F_a + F_b) + 2.0 * F_c)
+    u, tr_u = combination(op, [u_n, dt * F_n, v2, v3], dt, tol, m_max, exact)
+    return u, (a, b, c), (tr_a, tr_b, tr_c, tr_u)
+
+
 def run_fixed_domain(op, u0, dt, nsteps, F_of, tol=1e-10, m_max=40, exact=False, scheme="etd2"):
-    """nsteps steps of `scheme` (etd1, etd2 or etd2rk) on a fixed domain.
+    """nsteps steps of `scheme` (etd1, etd2, etd2rk, etd3rk or etd4rk) on a fixed domain.
     F_of(U, t) -> F vector.  Returns U at t = nsteps dt."""
     u = np.array(u0, dtype=np.float64, copy=True)
     F_prev = None
@@ -98,6 +145,9 @@ def run_fixed_domain(op, u0, dt, nsteps, F_of, tol=1e-10, m_max=40, exact=False,
     for _ in range(nsteps):
         if scheme == "etd2rk":
             u, _, _ = etd2rk_step(op, u, F_of, t, dt, tol=tol, m_max=m_max, exact=exact)
+        elif scheme in ("etd3rk", "etd4rk"):
+            step = etd3rk_step if scheme == "etd3rk" else etd4rk_step
+            u, _, _ = step(op, u, F_of, t, dt, tol=tol, m_max=m_max, exact=exact)
         else:
             F_n = F_of(u, t)
             if F_prev is None or scheme == "etd1":

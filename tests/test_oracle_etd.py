@@ -1,4 +1,6 @@
-"""Pins for oracle.etd: ETD2 and ETD2RK on a scalar ODE in closed form,
+"""Pins for oracle.etd: ETD2 and ETD2RK on a scalar ODE in closed form;
+ETD3RK and ETD4RK exact for forcing quadratic in t, phi_0 alone for F = 0,
+orders 3 and 4 on a Bernoulli ODE and on a stiff EB system;
 first-order (ETD1) and second-order (ETD2, ETD2RK) convergence for a
 manufactured solution on a fixed circle, and the paper's Table 1 (ETD2 and
 ETD2RK on the peanut domain, Sec. 4.2.1) within a factor of 3."""
@@ -185,3 +187,96 @@ def test_table1_etd2rk_peanut_641():
     n, _, li, l2 = [r for r in _golden(GOLDEN_RK) if r[0] == 641][0]
     gi, g2 = _peanut(n, scheme="etd2rk")
     assert li / 3 <= gi <= 3 * li and l2 / 3 <= g2 <= 3 * l2
+
+
+# ---- ETD3RK / ETD4RK (Sec. 3.2)
+
+def _poly_forced_exact(c, coef, t0, u0, dt):
+    """u(t0 + dt) for u' = c u + q(t), q a polynomial (coefficients low to
+    high), by variation of constants with scipy's adaptive quadrature."""
+    from scipy.integrate import quad
+
+    q = lambda t: sum(a * t ** k for k, a in enumerate(coef))
+    val = quad(lambda s: math.exp(c * (dt - s)) * q(t0 + s), 0.0, dt, epsabs=1e-16, epsrel=1e-15)[0]
+    return math.exp(c * dt) * u0 + val
+
+
+@pytest.mark.parametrize("step", [etd.etd3rk_step, etd.etd4rk_step])
+def test_etdrk34_exact_for_quadratic_forcing(step):
+    # With F independent of U the final stage integrates the quadratic
+    # interpolant of F through t_n, t_n + dt/2, t_n + dt exactly, so a forcing
+    # quadratic in t is reproduced to rounding.  The phi_3 term carries the
+    # t^2 part: a phi_3 normalised the standard way instead of by Eq. 3.7
+    # fails here.
+    c, coef, t0, dt, u0 = -3.0, (0.7, -1.3, 0.9), 0.3, 0.2, 0.4
+    op = _ScalarOp(c)
+    F_of = lambda u, t: np.full_like(u, coef[0] + coef[1] * t + coef[2] * t * t)
+    u1 = step(op, np.array([u0]), F_of, t0, dt, tol=1e-14, m_max=8)[0]
+    assert abs(u1[0] - _poly_forced_exact(c, coef, t0, u0, dt)) < 1e-14
+    # a cubic forcing is not integrated exactly (the interpolant is quadratic)
+    Fc = lambda u, t: np.full_like(u, t ** 3)
+    u3 = step(op, np.array([u0]), Fc, t0, dt, tol=1e-14, m_max=8)[0]
+    assert abs(u3[0] - _poly_forced_exact(c, (0.0, 0.0, 0.0, 1.0), t0, u0, dt)) > 1e-8
+
+
+@pytest.mark.parametrize("step", [etd.etd3rk_step, etd.etd4rk_step])
+def test_etdrk34_linear_is_expm(step):
+    # F = 0: every stage is phi_0 alone and U_{n+1} = exp(dt C) U_n (scipy's expm)
+    import scipy.linalg as sl
+
+    g = Grid((14, 14), (-2, -2), (2, 2))
+    op = EBOperator(g, g.radius() - 1.3, 1.0)
+    u0 = np.random.default_rng(2).uniform(-1, 1, op.ncomp)
+    dt = 0.05
+    u1 = step(op, u0, lambda u, t: np.zeros_like(u), 0.0, dt, tol=1e-13, m_max=40)[0]
+    want = sl.expm(dt * op.C.toarray()) @ u0
+    assert np.max(np.abs(u1 - want)) <= 1e-11 * np.max(np.abs(want))
+
+
+def test_etdrk34_scalar_orders():
+    # u' = c u + u (1 - u) = r u - u^2 (r = 1 + c), a Bernoulli equation with
+    # the closed form u = r u0 e^{rt} / (r + u0 (e^{rt} - 1)).
+    c, u0, T = -2.0, 0.6, 1.0
+    r = 1.0 + c
+    exact = r * u0 * math.exp(r * T) / (r + u0 * (math.exp(r * T) - 1.0))
+    op = _ScalarOp(c)
+    F_of = lambda u, t: u * (1.0 - u)
+    for step, order in ((etd.etd3rk_step, 3), (etd.etd4rk_step, 4)):
+        errs = []
+        for n in (10, 20, 40, 80):
+            u, t = np.array([u0]), 0.0
+            for _ in range(n):
+                u = step(op, u, F_of, t, T / n, tol=1e-14, m_max=8)[0]
+                t += T / n
+            errs.append(abs(u[0] - exact))
+        orders = [math.log2(errs[i] / errs[i + 1]) for i in range(1, 3)]
+        assert min(orders) > order - 0.4, (errs, orders)
+
+
+def test_etdrk34_stiff_system_orders():
+    # The EB system of a small disc with the logistic reaction (spectral
+    # radius of C about 108): temporal convergence against scipy's DOP853 at
+    # tight tolerance, the combinations by the dense augmented expm.  ETD4RK
+    # reaches order 4 and ETD3RK approaches 3, far below ETD2RK's error.
+    from scipy.integrate import solve_ivp
+
+    g = Grid((16, 16), (-2, -2), (2, 2))
+    op = EBOperator(g, g.radius() - 1.3, 1.0)
+    X = np.stack([c.ravel()[op.index] for c in g.coords()], -1)
+    u0 = 0.5 + 0.4 * np.cos(X[:, 0]) * np.sin(X[:, 1] + 0.3)
+    F_of = lambda u, t: u * (1.0 - u)
+    C = op.C.toarray()
+    T = 0.8
+    ref = solve_ivp(lambda t, u: C @ u + F_of(u, t), (0.0, T), u0, method="DOP853", rtol=3e-14,
+                    atol=1e-15).y[:, -1]
+
+    def err(scheme, n):
+        u = etd.run_fixed_domain(op, u0, T / n, n, F_of, exact=True, scheme=scheme)
+        return np.max(np.abs(u - ref))
+
+    e4 = [err("etd4rk", n) for n in (32, 64, 128)]
+    assert min(math.log2(e4[i] / e4[i + 1]) for i in range(2)) > 3.5, e4
+    e3 = [err("etd3rk", n) for n in (128, 256, 512)]
+    assert math.log2(e3[1] / e3[2]) > 2.6, e3
+    e2 = err("etd2rk", 64)
+    assert e4[1] < 5e-3 * e2 and err("etd3rk", 64) < 5e-3 * e2

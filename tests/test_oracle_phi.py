@@ -47,12 +47,23 @@ def test_paper_recursion_k_le_2():
     assert np.allclose(phi.phi_scalar(2, z), (1 * phi.phi_scalar(1, z) - 1.0) / z, rtol=1e-14)
 
 
+def test_paper_phi3_is_twice_standard():
+    # The phi_3 of the ETD3RK / ETD4RK formulas: Eq. 3.7 (the integral of
+    # e^{(1-l) z} l^2 over [0, 1], by quadrature) and Eq. 3.8 with k = 2,
+    # (2 phi_2 - 1) / z, both equal twice the standard phi_3.
+    for z in (-6.0, -1.5, -0.1, 0.7):
+        eq37 = quad(lambda l: math.exp((1.0 - l) * z) * l * l, 0.0, 1.0, epsabs=1e-15, epsrel=1e-14)[0]
+        eq38 = (2.0 * phi.phi_scalar(2, np.array([z]))[0] - 1.0) / z
+        std3 = phi.phi_scalar(3, np.array([z]))[0]
+        assert abs(eq37 - 2.0 * std3) <= 1e-13 * abs(eq37)
+        assert abs(eq38 - 2.0 * std3) <= 1e-12 * abs(eq38)
+
+
 def _spd_neg(n, seed):
     rng = np.random.default_rng(seed)
     Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
     lam = -np.linspace(0.05, 9.0, n)
     return (Q * lam) @ Q.T
-
 
 @pytest.mark.parametrize("p", [1, 2, 3])
 def test_combination_expm_vs_eig(p):
@@ -63,14 +74,12 @@ def test_combination_expm_vs_eig(p):
     b = phi.combination_eig(A, vs)
     assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(a))
 
-
 def test_combination_scalar_matrix():
     # 1 x 1 A = [z]: sum phi_k(z) v_k in closed form
     for z in (-3.0, -0.25, 0.5):
         vs = [np.array([1.3]), np.array([-0.7]), np.array([2.1])]
         want = sum(phi_mp(k, z) * vs[k][0] for k in range(3))
         assert abs(phi.combination_expm(np.array([[z]]), vs)[0] - want) < 1e-13 * abs(want)
-
 
 @pytest.mark.parametrize("p", [2, 3])
 def test_combination_is_ode_solution(p):
@@ -81,10 +90,8 @@ def test_combination_is_ode_solution(p):
 
     def f(t, y):
         return A @ y + sum(t ** (k - 1) / math.factorial(k - 1) * vs[k] for k in range(1, p + 1))
-
     sol = solve_ivp(f, (0.0, 1.0), vs[0], method="DOP853", rtol=1e-13, atol=1e-14)
     assert np.max(np.abs(sol.y[:, -1] - phi.combination_expm(A, vs))) < 1e-10
-
 
 def test_phi_columns_diagonal_and_triangular():
     # diagonal H: phi_k(H) e1 = phi_k(h11) e1
