@@ -49,7 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--no-etd2rk", action="store_true")
+    ap.add_argument("--no-etd2rk", action="store_true", help="skip every Runge-Kutta leg")
+    ap.add_argument("--rk-schemes", default="etd2rk,etd3rk,etd4rk",
+                    help="comma-separated Runge-Kutta integrators timed on the same step (FP64)")
     ap.add_argument("--no-poisson", action="store_true")
     ap.add_argument("--clocks", default="on", choices=["on", "off"])
     ap.add_argument("--no-stress", action="store_true")
@@ -293,7 +295,7 @@ def main():
     clocks = ClockSampler(local, enabled=args.clocks == "on" and rank == 0)
     r64 = run("fp64")
     rmx = None if args.no_mixed else run("mixed")
-    rrk = None if args.no_etd2rk else run("fp64", "etd2rk")
+    rks = {} if args.no_etd2rk else {sc: run("fp64", sc) for sc in args.rk_schemes.split(",") if sc}
     pois = None if args.no_poisson or rank != 0 else run_poisson(etd, stream, dev)
     e2e = None if args.no_e2e else run_e2e(args, w, make_ctx, initial_state, one_step, stream, flush, dev)
     stress = None
@@ -340,12 +342,15 @@ def main():
                         "breakdown_ms": {n: float(v) for n, v in zip(names, np.array(rmx["parts"]).mean(axis=0))}}
     if pois is not None:
         out["poisson"] = pois
-    if rrk is not None:
+    nevals = {"etd2rk": 2, "etd3rk": 3, "etd4rk": 4}
+    for sc, rrk in rks.items():
         trk = sum(rrk["times"]) / 1e3
-        out["etd2rk"] = {"value": rrk["cells"] / trk / 1e6, "ms_per_step": 1e3 * trk / args.steps, "dtype": "f64",
-                         "note": "same step with the ETD2RK integrator (two Krylov evaluations per step)",
-                         "krylov_iters_per_step": rrk["iters"] / args.steps,
-                         "breakdown_ms": {n: float(v) for n, v in zip(names, np.array(rrk["parts"]).mean(axis=0))}}
+        out[sc] = {"value": rrk["cells"] / trk / 1e6, "ms_per_step": 1e3 * trk / args.steps, "dtype": "f64",
+                   "note": "same step with the %s integrator (%d Krylov evaluations per step)"
+                           % (sc.upper(), nevals.get(sc, 0)),
+                   "krylov_iters_per_step": rrk["iters"] / args.steps,
+                   "substeps_per_step": rrk["substeps"] / args.steps,
+                   "breakdown_ms": {n: float(v) for n, v in zip(names, np.array(rrk["parts"]).mean(axis=0))}}
     if e2e is not None:
         out["e2e"] = e2e
     out["roofline"] = roofline(r64, w, avg_parts, names)

@@ -58,7 +58,7 @@ typedef struct {
 
 enum { ETD_REACTION_NONE = 0, ETD_REACTION_LOGISTIC = 1, ETD_REACTION_LOGISTIC_AK = 2, ETD_REACTION_COMPETITION = 3 };
 enum { ETD_PRECISION_FP64 = 0, ETD_PRECISION_MIXED = 1 };
-enum { ETD_SCHEME_ETD1 = 1, ETD_SCHEME_ETD2 = 2, ETD_SCHEME_ETD2RK = 3 };
+enum { ETD_SCHEME_ETD1 = 1, ETD_SCHEME_ETD2 = 2, ETD_SCHEME_ETD2RK = 3, ETD_SCHEME_ETD3RK = 4, ETD_SCHEME_ETD4RK = 5 };
 
 /* Method parameters.
  *   nspecies    1 or 2
@@ -80,7 +80,11 @@ enum { ETD_SCHEME_ETD1 = 1, ETD_SCHEME_ETD2 = 2, ETD_SCHEME_ETD2RK = 3 };
  *               beta field is given to etd_init_domain
  *   adjoint     1 to reserve the workspace of etd_adjoint_step (species 0)
  *   scheme      time integrator of etd_step (Sec. 3.1-3.2): ETD_SCHEME_ETD1,
- *               ETD_SCHEME_ETD2 (also selected by 0) or ETD_SCHEME_ETD2RK
+ *               ETD_SCHEME_ETD2 (also selected by 0), ETD_SCHEME_ETD2RK,
+ *               ETD_SCHEME_ETD3RK or ETD_SCHEME_ETD4RK (the last two need
+ *               m_max <= 60, reserve three more full-grid FP64 fields per
+ *               species, and step the reaction term only: no source, no
+ *               boundary data)
  *   boundary_data  1 to reserve the workspace of nonzero Dirichlet data
  *               (etd_boundary_points / etd_set_boundary_values) */
 typedef struct {
@@ -142,15 +146,19 @@ etd_status etd_init_domain(etd_ctx* ctx, int species, const double* phi, const d
  *   ETD1   (Sec. 3.1)  the same without the phi_2 term;
  *   ETD2RK (Sec. 3.2)  a_n = phi_0(dt C) U_n + dt phi_1(dt C) F_n (the ETD1 step),
  *                      U_{n+1} = a_n + dt phi_2(dt C)(F(a_n) - F_n): two Krylov
- *                      evaluations, the second with v_0 = v_1 = 0.
+ *                      evaluations, the second with v_0 = v_1 = 0;
+ *   ETD3RK, ETD4RK (Sec. 3.2)  the stages a_n, b_n (and c_n) with dt / 2 or
+ *                      dt, then U_{n+1} by one combination up to phi_3: three
+ *                      and four Krylov evaluations.  The paper's phi_3 is that
+ *                      of Eq. 3.7, twice the standard phi_3.
  * Each phi-combination (Eq. 3.9) is evaluated by adaptive Krylov
  * time-stepping of the ODE of Eq. 3.10.  u[s] (device, full grid, in/out):
  * read at the computational points of species s; on return it holds U_{n+1}
  * there and 0 at every other node.  F_{n-1} (ETD2) is kept by the context;
  * where a point was not computational at the previous step (and at the first
  * step) F_{n-1} = F_n.  stats: NULL for an asynchronous call, else filled
- * after synchronising; for ETD2RK the counts add both evaluations and the
- * trace lists the first evaluation's substeps, then the second's. */
+ * after synchronising; for the Runge-Kutta schemes the counts add all
+ * evaluations and the trace lists their substeps in order. */
 etd_status etd_step(etd_ctx* ctx, double dt, double* const* u, etd_step_stats* stats);
 
 /* The phi-combination alone (Sec. 3.3, Eq. 3.9 with p = 2):
@@ -159,6 +167,13 @@ etd_status etd_step(etd_ctx* ctx, double dt, double* const* u, etd_step_stats* s
  * FP64 arrays; y is 0 off the computational set. */
 etd_status etd_phi_combination(etd_ctx* ctx, int species, double dt, const double* v0, const double* v1,
                                const double* v2, double* y, etd_step_stats* stats);
+
+/* The phi-combination with p = 3 (Eq. 3.9, standard phi_k):
+ *   y = phi_0(dt C) v0 + phi_1(dt C) v1 + phi_2(dt C) v2 + phi_3(dt C) v3,
+ * arguments as etd_phi_combination.  Needs m_max <= 60 (ETD_ERR_ARG
+ * otherwise). */
+etd_status etd_phi_combination3(etd_ctx* ctx, int species, double dt, const double* v0, const double* v1,
+                                const double* v2, const double* v3, double* y, etd_step_stats* stats);
 
 /* Embedded-boundary Poisson solve (Sec. 2: div(beta grad u) = f with
  * Dirichlet data; Sec. 4.1): at the computational points of `species`,

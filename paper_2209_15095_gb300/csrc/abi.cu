@@ -23,7 +23,10 @@ struct SpeciesBufs {
   double* Yc = nullptr;
   void* V1c = nullptr;
   void* V2c = nullptr;
+  void* V3c = nullptr;  // phi_3 combinations
+  void* W2g = nullptr;
   void* Z[2] = {nullptr, nullptr};
+  double* stg[3] = {nullptr, nullptr, nullptr};  // ETD3RK / ETD4RK stage fields
   const double* beta_field = nullptr;
   // boundary data (params.boundary_data): per point, face and slot
   double* bco = nullptr;
@@ -138,8 +141,12 @@ bool check_params(const etd_params* p, std::string& why) {
     why = "krylov_tol must be positive";
     return false;
   }
-  if (p->scheme < 0 || p->scheme > ETD_SCHEME_ETD2RK) {
+  if (p->scheme < 0 || p->scheme > ETD_SCHEME_ETD4RK) {
     why = "unknown scheme";
+    return false;
+  }
+  if ((p->scheme == ETD_SCHEME_ETD3RK || p->scheme == ETD_SCHEME_ETD4RK) && p->m_max > MAX_M - 1) {
+    why = "ETD3RK and ETD4RK need m_max <= 60";
     return false;
   }
   if (p->reaction < 0 || p->reaction > 3 || (p->reaction == ETD_REACTION_COMPETITION && p->nspecies != 2)) {
@@ -189,6 +196,10 @@ size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
     b.V2c = cv.take<char>(s * G);
     b.Z[0] = cv.take<char>(s * G);
     b.Z[1] = cv.take<char>(s * G);
+    b.V3c = cv.take<char>(s * G);
+    b.W2g = cv.take<char>(s * G);
+    if (p.scheme == ETD_SCHEME_ETD3RK || p.scheme == ETD_SCHEME_ETD4RK)
+      for (int i = 0; i < 3; ++i) b.stg[i] = cv.take<double>(G);
     if (c) c->sp[sp] = b;
   }
   LevelsetBufs lb = levelset_carve(g, [&](size_t bytes) { return cv.take<char>(bytes); });
@@ -290,14 +301,18 @@ SpeciesDev<T> species_dev(etd_ctx* c, int s, double* u, int stage = 0) {
   d.Yc = b.Yc;
   d.V1c = (T*)b.V1c;
   d.V2c = (T*)b.V2c;
+  d.V3c = (T*)b.V3c;
+  d.W2g = (T*)b.W2g;
   d.Z[0] = (T*)b.Z[0];
   d.Z[1] = (T*)b.Z[1];
+  for (int i = 0; i < 3; ++i) d.stg[i] = b.stg[i];
   return d;
 }
 
 template <typename T>
-etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int species, const double* given[3],
-                     etd_step_stats* stats, bool etd1 = false, bool keep_stats = false) {
+etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int species, const double* const* given,
+                     etd_step_stats* stats, bool etd1 = false, bool keep_stats = false, int p = 2,
+                     const StageDesc* stage = nullptr) {
   PhipmArgs<T> a;
   memset(&a, 0, sizeof(a));
   a.g = c->g;
@@ -309,13 +324,16 @@ etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int spec
   a.reaction = c->par.reaction;
   for (int i = 0; i < 4; ++i) a.rp[i] = c->par.rp[i];
   a.etd1 = etd1 ? 1 : 0;
-  if (mode == MODE_ETD2 || mode == MODE_RK2) {
+  a.p = p;
+  if (stage) a.stage = *stage;
+  const bool all = mode == MODE_ETD2 || mode == MODE_RK2 || mode == MODE_STAGE;
+  if (all) {
     a.nspecies = c->par.nspecies;
     for (int s = 0; s < a.nspecies; ++s) a.sp[s] = species_dev<T>(c, s, u[s], mode == MODE_RK2 ? 1 : 0);
   } else {
     a.nspecies = 1;
     a.sp[0] = species_dev<T>(c, species, u[0]);
-    for (int i = 0; i < 3; ++i) a.given[i] = given[i];
+    for (int i = 0; i <= p; ++i) a.given[i] = given[i];
   }
   if (mode == MODE_EXPLICIT) {
     a.reaction = c->par.reaction;
@@ -332,9 +350,55 @@ etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int spec
   e = launch_phipm<T>(a, c->nblocks, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "phipm launch");
   c->last_nspecies = a.nspecies;
-  c->last_species0 = (mode == MODE_ETD2 || mode == MODE_RK2) ? 0 : species;
+  c->last_species0 = all ? 0 : species;
   if (!stats) return ETD_OK;
   return copy_stats(c, stats);
+}
+
+// ETD3RK and ETD4RK (Sec. 3.2) as a sequence of stage launches.  Each stage
+// is one combination phi_0(h C) v_0 + h phi_1(h C) g_1 + h phi_2(h C) g_2
+// + h phi_3(h C) g_3 with h = dt or dt / 2, v_0 = U_n or a_n, and g_j linear
+// combinations of F(U_n), F(a_n), F(b_n), F(c_n) (U + h phi_1(h C) C U =
+// phi_0(h C) U).  The paper's phi_3 (Eq. 3.7) is twice the standard phi_3
+// that the kernel evaluates, so the tables hold the paper's phi_3
+// coefficients times two.
+struct RkStage {
+  double dt_factor;
+  int p;
+  StageDesc d;
+};
+static const RkStage kEtd3rk[3] = {
+    // a_n = U_n + dt/2 phi_1(dt C / 2)(F_n + C U_n)
+    {0.5, 2, {0, 1, {{1, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}}},
+    // b_n = U_n + dt phi_1(dt C)(C U_n + 2 F(a_n) - F_n)
+    {1.0, 2, {0, 2, {{-1, 2, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}}},
+    // U_{n+1}: phi_1 (F_n), phi_2 (-3 F_n + 4 F(a_n) - F(b_n)), phi_3 2 x (2, -4, 2)
+    {1.0, 3, {0, 0, {{1, 0, 0, 0}, {-3, 4, -1, 0}, {4, -8, 4, 0}}}}};
+static const RkStage kEtd4rk[4] = {
+    // a_n = U_n + dt/2 phi_1(dt C / 2)(F_n + C U_n)
+    {0.5, 2, {0, 1, {{1, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}}},
+    // b_n = U_n + dt/2 phi_1(dt C / 2)(F(a_n) + C U_n)
+    {0.5, 2, {0, 2, {{0, 1, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}}},
+    // c_n = a_n + dt/2 phi_1(dt C / 2)(2 F(b_n) - F_n + C a_n)
+    {0.5, 2, {1, 3, {{-1, 0, 2, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}}},
+    // U_{n+1}: phi_1 (F_n), phi_2 (-3 F_n + 2 F(a_n) + 2 F(b_n) - F(c_n)),
+    // phi_3 2 x (2, -2, -2, 2)
+    {1.0, 3, {0, 0, {{1, 0, 0, 0}, {-3, 2, 2, -1}, {4, -4, -4, 4}}}}};
+
+etd_status step_rk34(etd_ctx* c, int scheme, double dt, double* const* u, etd_step_stats* stats) {
+  for (int s = 0; s < c->par.nspecies; ++s)
+    if (c->sp[s].src[0] || c->sp[s].bval[0])
+      return fail(c, ETD_ERR_ARG, "ETD3RK and ETD4RK take the reaction term only (no source, no boundary data)");
+  const RkStage* tab = scheme == ETD_SCHEME_ETD3RK ? kEtd3rk : kEtd4rk;
+  const int ns = scheme == ETD_SCHEME_ETD3RK ? 3 : 4;
+  for (int i = 0; i < ns; ++i) {
+    etd_step_stats* st = i == ns - 1 ? stats : nullptr;  // statistics of all stages
+    const double h = tab[i].dt_factor * dt;
+    etd_status r = c->fp32 ? run_phipm<float>(c, MODE_STAGE, h, u, 0, nullptr, st, false, i > 0, tab[i].p, &tab[i].d)
+                           : run_phipm<double>(c, MODE_STAGE, h, u, 0, nullptr, st, false, i > 0, tab[i].p, &tab[i].d);
+    if (r != ETD_OK) return r;
+  }
+  return ETD_OK;
 }
 
 }  // namespace
@@ -400,18 +464,20 @@ etd_status etd_init_domain(etd_ctx* c, int species, const double* phi, const dou
   ca.kind = b.kind;
   ca.tile_count = c->tile_count;
   ca.st = c->st;
-  ca.nzero = 4;
+  ca.nzero = 5;
   if (c->fp32) {
     ca.zero_f32[0] = (float*)b.Yg;
     ca.zero_f32[1] = (float*)b.W1g;
     ca.zero_f32[2] = (float*)b.Z[0];
     ca.zero_f32[3] = (float*)b.Z[1];
+    ca.zero_f32[4] = (float*)b.W2g;
     ca.basis_f32 = (float*)b.V;
   } else {
     ca.zero_f64[0] = (double*)b.Yg;
     ca.zero_f64[1] = (double*)b.W1g;
     ca.zero_f64[2] = (double*)b.Z[0];
     ca.zero_f64[3] = (double*)b.Z[1];
+    ca.zero_f64[4] = (double*)b.W2g;
     ca.basis_f64 = (double*)b.V;
   }
   ca.nbasis = c->par.m_max + 1;
@@ -445,6 +511,7 @@ etd_status etd_step(etd_ctx* c, double dt, double* const* u, etd_step_stats* sta
     if (!c->sp[s].ready) return fail(c, ETD_ERR_ARG, "etd_init_domain not called for every species");
   }
   const int scheme = c->par.scheme == 0 ? ETD_SCHEME_ETD2 : c->par.scheme;
+  if (scheme == ETD_SCHEME_ETD3RK || scheme == ETD_SCHEME_ETD4RK) return step_rk34(c, scheme, dt, u, stats);
   if (scheme != ETD_SCHEME_ETD2RK) {
     const bool etd1 = scheme == ETD_SCHEME_ETD1;
     return c->fp32 ? run_phipm<float>(c, MODE_ETD2, dt, u, 0, nullptr, stats, etd1)
@@ -469,6 +536,19 @@ etd_status etd_phi_combination(etd_ctx* c, int species, double dt, const double*
   double* out[1] = {y};
   return c->fp32 ? run_phipm<float>(c, MODE_GIVEN, dt, out, species, given, stats)
                  : run_phipm<double>(c, MODE_GIVEN, dt, out, species, given, stats);
+}
+
+etd_status etd_phi_combination3(etd_ctx* c, int species, double dt, const double* v0, const double* v1,
+                                const double* v2, const double* v3, double* y, etd_step_stats* stats) {
+  if (!c) return ETD_ERR_ARG;
+  if (species < 0 || species >= c->par.nspecies || !v0 || !v1 || !v2 || !v3 || !y || !(dt > 0.0))
+    return fail(c, ETD_ERR_ARG, "bad arguments");
+  if (c->par.m_max > MAX_M - 1) return fail(c, ETD_ERR_ARG, "a phi_3 combination needs m_max <= 60");
+  if (!c->sp[species].ready) return fail(c, ETD_ERR_ARG, "etd_init_domain not called");
+  const double* given[4] = {v0, v1, v2, v3};
+  double* out[1] = {y};
+  return c->fp32 ? run_phipm<float>(c, MODE_GIVEN, dt, out, species, given, stats, false, false, 3)
+                 : run_phipm<double>(c, MODE_GIVEN, dt, out, species, given, stats, false, false, 3);
 }
 
 etd_status etd_set_source(etd_ctx* c, int species, const double* src_n, const double* src_np1) {

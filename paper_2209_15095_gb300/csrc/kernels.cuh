@@ -13,8 +13,8 @@ struct ClassifyArgs {
   DevStatus* st;
   // stencil-input vectors whose entries must be zero off the computational set
   int nzero;
-  double* zero_f64[4];
-  float* zero_f32[4];
+  double* zero_f64[5];
+  float* zero_f32[5];
   int nbasis;
   double* basis_f64;
   float* basis_f32;
@@ -76,7 +76,12 @@ struct SpeciesDev {
   double* Yc;
   T* V1c;
   T* V2c;
+  T* V3c;   // v_3 (phi_3 combinations only)
+  T* W2g;   // full grid: w_2 (phi_3 combinations only; zero off the computational set)
   T* Z[2];  // full grid: A V_j of the last two basis vectors (unnormalised)
+  // stage fields a, b, c of the Runge-Kutta schemes (full grid, FP64; only
+  // the computational points are written and read)
+  double* stg[3];
   // caller's source (full grid) and boundary data for this launch: F gains
   // src[p] + sum over the point's face slots of bco * bval (nullptr: none)
   const double* src;
@@ -93,6 +98,16 @@ enum : int {
                       // v2 = dt (F(u_n) - F(u_{n-1})); writes the output field
   MODE_RK2 = 3,       // second ETD2RK stage: v0 = v1 = 0, v2 = dt (F(u) - F_prev);
                       // u <- u + result
+  MODE_STAGE = 4,     // a stage of ETD3RK / ETD4RK (StageDesc); reaction term only
+};
+
+// One stage of ETD3RK / ETD4RK: fields 0 = u, 1..3 = the stage fields a, b, c.
+// v_0 = field v0_field; v_j = dt sum_i coef[j-1][i] F(field i), j = 1..3;
+// the result goes to field out_field.
+struct StageDesc {
+  int v0_field;
+  int out_field;
+  double coef[3][4];
 };
 
 template <typename T>
@@ -107,8 +122,10 @@ struct PhipmArgs {
   int reaction;
   double rp[4];
   SpeciesDev<T> sp[2];
-  const double* given[3];  // MODE_GIVEN: v0, v1, v2 on the grid (species 0)
+  const double* given[4];  // MODE_GIVEN: v0 .. v_p on the grid (species 0)
   int etd1;                // MODE_ETD2: v2 = 0 (the ETD1 step)
+  int p;                   // highest phi index of the combination: 2 or 3
+  StageDesc stage;         // MODE_STAGE
   double* part;
   DevStatus* st;
   StatsDev* stats;

@@ -1,8 +1,8 @@
-// Adaptive Krylov evaluation of y = phi_0(A) v_0 + phi_1(A) v_1 + phi_2(A) v_2
-// (Sec. 3.3, Eq. 3.9) by time-stepping the equivalent ODE of Eq. 3.10
-// (y' = A y + v_1 + t v_2, y(0) = v_0, y = y(1)), A = dt C with C the
-// matrix-free embedded-boundary operator of Sec. 2, and the ETD2 step of
-// Sec. 3.1 built on it.
+// Adaptive Krylov evaluation of y = phi_0(A) v_0 + phi_1(A) v_1 + ... + phi_p(A) v_p,
+// p = 2 or 3 (Sec. 3.3, Eq. 3.9), by time-stepping the equivalent ODE of
+// Eq. 3.10 (y' = A y + v_1 + t v_2 + t^2/2 v_3, y(0) = v_0, y = y(1)), A = dt C
+// with C the matrix-free embedded-boundary operator of Sec. 2, and the ETD
+// steps of Sec. 3.1-3.2 built on it.
 //
 // One persistent cooperative kernel runs the whole call: the ETD2 right-hand
 // vectors, every substep (w_1, w_2 matvecs, the IOM2/Lanczos basis with fused
@@ -22,6 +22,9 @@
 //   on failure at m_max shrink tau <- tau max(0.2, 0.9 (tol tau |y| / err)^(1/(m+1)))
 //   y <- y + tau w_1 + tau^2 beta V_m phi_2(tau H_m) e_1
 //   tau_next = min(1 - t, tau min(2, 0.9 (tol tau |y| / err)^(1/(m+1))))
+// p = 3: w_1 = A y + v_1 + t_k v_2 + t_k^2/2 v_3, w_2 = A w_1 + v_2 + t_k v_3,
+// w_3 = A w_2 + v_3, beta = |w_3|, err = tau^4 beta h_{m+1,m} |e_m^T phi_4(tau H_m) e_1|,
+//   y <- y + tau w_1 + tau^2/2 w_2 + tau^3 beta V_m phi_3(tau H_m) e_1.
 // Basis vectors are stored unnormalised (v_j = V_j / |V_j|) so that the
 // normalisation costs no extra sweep.
 #include "common.cuh"
@@ -55,7 +58,7 @@ struct Ctl {
   double up[MAX_M + 2];
   double low[MAX_M + 2];
   double scale[MAX_M + 2];  // 1 / |V_j|
-  double coef[MAX_M + 2];   // tau^2 beta phi_2(tau H) e_1, times scale
+  double coef[MAX_M + 2];   // tau^p beta phi_p(tau H) e_1, times scale
   float chi[MAX_M + 2];     // coef as a sum of two floats (FP32 basis sum)
   float clo[MAX_M + 2];
   double yexp[64];
@@ -173,18 +176,19 @@ __device__ void small_expm_warp(Ctl& c, int m, int p, double tau) {
 }
 
 // After small_expm_warp: err and the combination coefficients (warp 0; the
-// coefficients come from phi_2(X) e_1 = X phi_3(X) e_1 + e_1 / 2).
-__device__ void finish_check(Ctl& c, int m, double tau) {
+// coefficients come from phi_p(X) e_1 = X phi_{p+1}(X) e_1 + e_1 / p!).
+__device__ void finish_check(Ctl& c, int m, int p, double tau) {
   const int lane = threadIdx.x & 31;
-  const double tau2 = tau * tau;
+  const double taup = p == 3 ? tau * tau * tau : tau * tau;
+  const double invf = p == 3 ? 1.0 / 6.0 : 0.5;
   for (int r = lane; r < m; r += 32) {
     double hy = c.alpha[r] * c.yexp[r];
     if (r > 0) hy = fma(c.low[r - 1], c.yexp[r - 1], hy);
     if (r + 1 < m) hy = fma(c.up[r + 1], c.yexp[r + 1], hy);
-    double phi2 = fma(tau, hy, r == 0 ? 0.5 : 0.0);
-    c.coef[r] = tau2 * c.beta * phi2 * c.scale[r];
+    const double php = fma(tau, hy, r == 0 ? invf : 0.0);
+    c.coef[r] = taup * c.beta * php * c.scale[r];
   }
-  if (lane == 0) c.err = tau2 * tau * c.beta * c.hn * fabs(c.yexp[m - 1]);
+  if (lane == 0) c.err = taup * tau * c.beta * c.hn * fabs(c.yexp[m - 1]);
   __syncwarp();
 }
 
@@ -357,6 +361,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   const T bc = (T)S.beta_c;
   const double anorm = a.dt * (*S.gersh);
   const int m_max = a.m_max;
+  const int P = a.p == 3 ? 3 : 2;  // highest phi index (any other value: 2)
   const long long vs = g.size;
   // large problems: split Lanczos pass (see SPLIT_MIN)
   const bool split = ncomp >= SPLIT_MIN<T>;
@@ -383,36 +388,61 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
     }
     __syncthreads();
     const double t = c.t;
-    // w_1 = A y + v_1 + t v_2
-    node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
-      constexpr int U = NL_U(kk);
-      T ay[U], a1[U], a2[U];
+    if (P == 3) {
+      // w_1 = A y + v_1 + t v_2 + t^2/2 v_3, w_2 = A w_1 + v_2 + t v_3,
+      // w_3 = A w_2 + v_3 -> V_0 (one point per thread: register bound)
+      const T tt = (T)t, th2 = (T)(0.5 * t * t);
+      node_loop<1>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
+        if (pp[0] < 0) return;
+        const T ay = stencil<T, N>(S.Yg, pp[0], g, diag_of<T>(S, (int)kk[0]), S.beta_field, bc, cfac);
+        const T a1 = __ldcg(S.V1c + kk[0]), a2 = __ldcg(S.V2c + kk[0]), a3 = __ldcg(S.V3c + kk[0]);
+        S.W1g[pp[0]] = ay + a1 + tt * a2 + th2 * a3;
+      });
+      if (!grid_barrier(a.st, bar, 10)) return false;
+      node_loop<1>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
+        if (pp[0] < 0) return;
+        const T aw = stencil<T, N>(S.W1g, pp[0], g, diag_of<T>(S, (int)kk[0]), S.beta_field, bc, cfac);
+        const T a2 = __ldcg(S.V2c + kk[0]), a3 = __ldcg(S.V3c + kk[0]);
+        S.W2g[pp[0]] = aw + a2 + tt * a3;
+      });
+      if (!grid_barrier(a.st, bar, 16)) return false;
+      node_loop<1>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
+        if (pp[0] < 0) return;
+        const T aw = stencil<T, N>(S.W2g, pp[0], g, diag_of<T>(S, (int)kk[0]), S.beta_field, bc, cfac);
+        S.V[pp[0]] = aw + __ldcg(S.V3c + kk[0]);
+      });
+    } else {
+      // w_1 = A y + v_1 + t v_2
+      node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
+        constexpr int U = NL_U(kk);
+        T ay[U], a1[U], a2[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (pp[u] < 0) continue;
-        ay[u] = stencil<T, N>(S.Yg, pp[u], g, diag_of<T>(S, (int)kk[u]), S.beta_field, bc, cfac);
-        a1[u] = __ldcg(S.V1c + kk[u]);
-        a2[u] = __ldcg(S.V2c + kk[u]);
-      }
+        for (int u = 0; u < U; ++u) {
+          if (pp[u] < 0) continue;
+          ay[u] = stencil<T, N>(S.Yg, pp[u], g, diag_of<T>(S, (int)kk[u]), S.beta_field, bc, cfac);
+          a1[u] = __ldcg(S.V1c + kk[u]);
+          a2[u] = __ldcg(S.V2c + kk[u]);
+        }
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (pp[u] >= 0) S.W1g[pp[u]] = ay[u] + a1[u] + (T)t * a2[u];
-    });
-    if (!grid_barrier(a.st, bar, 10)) return false;
-    // w_2 = A w_1 + v_2 -> V_0 (unnormalised)
-    node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
-      constexpr int U = NL_U(kk);
-      T aw[U], a2[U];
+        for (int u = 0; u < U; ++u)
+          if (pp[u] >= 0) S.W1g[pp[u]] = ay[u] + a1[u] + (T)t * a2[u];
+      });
+      if (!grid_barrier(a.st, bar, 10)) return false;
+      // w_2 = A w_1 + v_2 -> V_0 (unnormalised)
+      node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
+        constexpr int U = NL_U(kk);
+        T aw[U], a2[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (pp[u] < 0) continue;
-        aw[u] = stencil<T, N>(S.W1g, pp[u], g, diag_of<T>(S, (int)kk[u]), S.beta_field, bc, cfac);
-        a2[u] = __ldcg(S.V2c + kk[u]);
-      }
+        for (int u = 0; u < U; ++u) {
+          if (pp[u] < 0) continue;
+          aw[u] = stencil<T, N>(S.W1g, pp[u], g, diag_of<T>(S, (int)kk[u]), S.beta_field, bc, cfac);
+          a2[u] = __ldcg(S.V2c + kk[u]);
+        }
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (pp[u] >= 0) S.V[pp[u]] = aw[u] + a2[u];
-    });
+        for (int u = 0; u < U; ++u)
+          if (pp[u] >= 0) S.V[pp[u]] = aw[u] + a2[u];
+      });
+    }
     if (!grid_barrier(a.st, bar, 11)) return false;
     // P_0: Z_0 = A V_0, |V_0|^2, <Z_0, V_0>
     {
@@ -577,8 +607,8 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         const int m = c.m;
         if (m % CHECK_EVERY == 0 || m == m_max || c.breakdown) {
           if (threadIdx.x < 32) {
-            small_expm_warp(c, m, 2, c.tau);
-            finish_check(c, m, c.tau);
+            small_expm_warp(c, m, P, c.tau);
+            finish_check(c, m, P, c.tau);
             if (threadIdx.x == 0) {
               if (c.breakdown) c.err = 0.0;
               c.accepted = c.err <= a.tol * c.tau * c.ynorm;
@@ -606,8 +636,8 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
           __syncthreads();
           if (c.abort) return false;
           if (threadIdx.x < 32) {
-            small_expm_warp(c, m, 2, c.tau);
-            finish_check(c, m, c.tau);
+            small_expm_warp(c, m, P, c.tau);
+            finish_check(c, m, P, c.tau);
             if (threadIdx.x == 0) c.accepted = c.err <= a.tol * c.tau * c.ynorm;
           }
           __syncthreads();
@@ -645,6 +675,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
           for (int i = 0; i < m; ++i) sum = fma(c.coef[i], to_f64(__ldcg(S.V + (long long)i * vs + p)), sum);
         }
         double y = fma(tau, (double)__ldcg(S.W1g + p), __ldcg(S.Yc + k)) + sum;
+        if (P == 3) y = fma(0.5 * tau * tau, (double)__ldcg(S.W2g + p), y);
         S.Yc[k] = y;
         S.Yg[p] = (T)y;
         yn.add(y, y);
@@ -701,74 +732,134 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
   const GridDev& g = a.g;
   const long long gtid = dealt_tid();
   const long long gthreads = (long long)gridDim.x * blockDim.x;
-  // ---- set-up: y = v_0, v_1, v_2 for every species (reads every species'
-  // field before any is overwritten)
-  double sums[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  // ---- set-up: y = v_0, v_1 .. v_p for every species (reads every species'
+  // fields before any is overwritten)
+  double sums[2][4] = {{0.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 0.0, 0.0}};
+  // MODE_STAGE: which fields' F values the stage needs
+  bool need[4] = {false, false, false, false};
+  if (a.mode == MODE_STAGE)
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 3; ++j) need[i] = need[i] || a.stage.coef[j][i] != 0.0;
   for (int s = 0; s < a.nspecies; ++s) {
     const SpeciesDev<T>& S = a.sp[s];
     const int ncomp = *S.ncomp;
-    Acc<double> acc, acc1, acc2;
-    node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
-      constexpr int U = NL_U(kk);
-      double y[U], v1[U], v2[U];
+    Acc<double> acc, acc1, acc2, acc3;
+    if (a.mode == MODE_STAGE) {
+      // a stage of ETD3RK / ETD4RK: F of each needed field (with the other
+      // species' same field, masked to its computational set); one point per
+      // thread (register bound)
+      node_loop<1>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
+        if (pp[0] < 0) return;
+        const long long k = kk[0], p = pp[0];
+        double Fi[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-      for (int q = 0; q < U; ++q) {
-        if (pp[q] < 0) continue;
-        const long long p = pp[q];
-        if (a.mode == MODE_GIVEN) {
-          y[q] = a.given[0][p];
-          v1[q] = a.given[1][p];
-          v2[q] = a.given[2][p];
-        } else if (a.mode == MODE_EXPLICIT) {
-          const double u = a.given[0][p], um = a.given[1][p];
-          const double F = reaction(a.reaction, a.rp, 0, u, 0.0);
-          const double Fm = reaction(a.reaction, a.rp, 0, um, 0.0);
-          y[q] = u;
-          v1[q] = a.dt * F;
-          v2[q] = a.dt * (F - Fm);
-        } else {
-          // MODE_ETD2 (v2 = 0 for ETD1), or the second ETD2RK stage MODE_RK2
-          // (u holds a_n, F_prev holds F_n: v0 = v1 = 0, v2 = dt (F(a_n) - F_n))
-          const double u = S.u[p];
+        for (int i = 0; i < 4; ++i) {
+          if (!need[i]) continue;
+          const double ui = i == 0 ? S.u[p] : S.stg[i - 1][p];
           double other = 0.0;
           if (a.nspecies == 2) {
             const SpeciesDev<T>& O = a.sp[1 - s];
-            other = (O.kind[p] & 3) == K_COMP ? O.u[p] : 0.0;
+            if ((O.kind[p] & 3) == K_COMP) other = i == 0 ? O.u[p] : O.stg[i - 1][p];
           }
-          const double F = (s == 0 ? reaction(a.reaction, a.rp, 0, u, other) : reaction(a.reaction, a.rp, 1, other, u)) +
-                           extra_F<T, N>(S, kk[q], p);
-          const double Fp = S.fvalid[p] ? S.Fprev[p] : F;
-          const bool rk2 = a.mode == MODE_RK2;
-          y[q] = rk2 ? 0.0 : u;
-          v1[q] = rk2 ? 0.0 : a.dt * F;
-          v2[q] = a.etd1 ? 0.0 : a.dt * (F - Fp);
+          Fi[i] = s == 0 ? reaction(a.reaction, a.rp, 0, ui, other) : reaction(a.reaction, a.rp, 1, other, ui);
         }
-      }
+        const int f0 = a.stage.v0_field;
+        const double y = f0 == 0 ? S.u[p] : S.stg[f0 - 1][p];
+        double vv[3];
 #pragma unroll
-      for (int q = 0; q < U; ++q) {
-        if (pp[q] < 0) continue;
-        const long long k = kk[q], p = pp[q];
-        S.Yc[k] = y[q];
-        S.Yg[p] = (T)y[q];
-        S.V1c[k] = (T)v1[q];
-        S.V2c[k] = (T)v2[q];
-        acc.add(y[q], y[q]);
-        acc1.add(v1[q], v1[q]);
-        acc2.add(v2[q], v2[q]);
-      }
-    });
+        for (int j = 0; j < 3; ++j) {
+          double t = 0.0;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) t = fma(a.stage.coef[j][i], Fi[i], t);
+          vv[j] = a.dt * t;
+        }
+        S.Yc[k] = y;
+        S.Yg[p] = (T)y;
+        S.V1c[k] = (T)vv[0];
+        S.V2c[k] = (T)vv[1];
+        if (a.p == 3) S.V3c[k] = (T)vv[2];
+        acc.add(y, y);
+        acc1.add(vv[0], vv[0]);
+        acc2.add(vv[1], vv[1]);
+        acc3.add(vv[2], vv[2]);
+      });
+    } else {
+      node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
+        constexpr int U = NL_U(kk);
+        double y[U], v1[U], v2[U], v3[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+          if (pp[q] < 0) continue;
+          const long long p = pp[q];
+          v3[q] = 0.0;
+          if (a.mode == MODE_GIVEN) {
+            y[q] = a.given[0][p];
+            v1[q] = a.given[1][p];
+            v2[q] = a.given[2][p];
+            if (a.p == 3) v3[q] = a.given[3][p];
+          } else if (a.mode == MODE_EXPLICIT) {
+            const double u = a.given[0][p], um = a.given[1][p];
+            const double F = reaction(a.reaction, a.rp, 0, u, 0.0);
+            const double Fm = reaction(a.reaction, a.rp, 0, um, 0.0);
+            y[q] = u;
+            v1[q] = a.dt * F;
+            v2[q] = a.dt * (F - Fm);
+          } else {
+            // MODE_ETD2 (v2 = 0 for ETD1), or the second ETD2RK stage MODE_RK2
+            // (u holds a_n, F_prev holds F_n: v0 = v1 = 0, v2 = dt (F(a_n) - F_n))
+            const double u = S.u[p];
+            double other = 0.0;
+            if (a.nspecies == 2) {
+              const SpeciesDev<T>& O = a.sp[1 - s];
+              other = (O.kind[p] & 3) == K_COMP ? O.u[p] : 0.0;
+            }
+            const double F =
+                (s == 0 ? reaction(a.reaction, a.rp, 0, u, other) : reaction(a.reaction, a.rp, 1, other, u)) +
+                extra_F<T, N>(S, kk[q], p);
+            const double Fp = S.fvalid[p] ? S.Fprev[p] : F;
+            const bool rk2 = a.mode == MODE_RK2;
+            y[q] = rk2 ? 0.0 : u;
+            v1[q] = rk2 ? 0.0 : a.dt * F;
+            v2[q] = a.etd1 ? 0.0 : a.dt * (F - Fp);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+          if (pp[q] < 0) continue;
+          const long long k = kk[q], p = pp[q];
+          S.Yc[k] = y[q];
+          S.Yg[p] = (T)y[q];
+          S.V1c[k] = (T)v1[q];
+          S.V2c[k] = (T)v2[q];
+          if (a.p == 3) S.V3c[k] = (T)v3[q];
+          acc.add(y[q], y[q]);
+          acc1.add(v1[q], v1[q]);
+          acc2.add(v2[q], v2[q]);
+          acc3.add(v3[q], v3[q]);
+        }
+      });
+    }
     sums[s][0] = acc.value();
     sums[s][1] = acc1.value();
     sums[s][2] = acc2.value();
+    sums[s][3] = acc3.value();
   }
-  // |y(0)|^2, |v_1|^2, |v_2|^2 per species (one reduction each)
-  double tot[2][3];
+  // |y(0)|^2, |v_1|^2, |v_2|^2, |v_3|^2 per species (one grid barrier each;
+  // two block sums of two quantities into the halves of one partial buffer)
+  double tot[2][4];
   for (int s = 0; s < a.nspecies; ++s) {
-    double v[3] = {sums[s][0], sums[s][1], sums[s][2]};
+    double v01[2] = {sums[s][0], sums[s][1]}, v23[2] = {sums[s][2], sums[s][3]};
     pb = part_buf(a.part, red);
-    block_partials<3>(v, pb);
+    block_partials<2>(v01, pb);
+    block_partials<2>(v23, pb + 2 * MAX_BLOCKS);
     if (!grid_barrier(a.st, bar, 1)) return;
-    grid_totals<3>(pb, tot[s]);
+    double t01[2], t23[2];
+    grid_totals<2>(pb, t01);
+    grid_totals<2>(pb + 2 * MAX_BLOCKS, t23);
+    tot[s][0] = t01[0];
+    tot[s][1] = t01[1];
+    tot[s][2] = t23[0];
+    tot[s][3] = t23[1];
   }
   // F_{n-1} <- F_n after every species has read the fields
   if (a.mode == MODE_ETD2) {
@@ -792,7 +883,7 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
     }
   }
   for (int s = 0; s < a.nspecies; ++s) {
-    const double vscale = fmax(sqrt(tot[s][1]), sqrt(tot[s][2]));
+    const double vscale = fmax(fmax(sqrt(tot[s][1]), sqrt(tot[s][2])), sqrt(tot[s][3]));
     if (!phipm_species<T, N>(a, a.sp[s], s, c, bar, red, tot[s][0], vscale)) return;
   }
   if (!grid_barrier(a.st, bar, 2)) return;
@@ -801,6 +892,9 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
     const SpeciesDev<T>& S = a.sp[s];
     const int ncomp = *S.ncomp;
     const bool add = a.mode == MODE_RK2;  // u <- a_n + the second stage's result
+    // a stage of ETD3RK / ETD4RK may write a stage field instead of u
+    const int outf = a.mode == MODE_STAGE ? a.stage.out_field : 0;
+    double* const dst = outf == 0 ? S.u : S.stg[outf - 1];
     node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
       constexpr int U = NL_U(kk);
       double y[U], b[U];
@@ -812,8 +906,9 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
       }
 #pragma unroll
       for (int q = 0; q < U; ++q)
-        if (pp[q] >= 0) S.u[pp[q]] = add ? b[q] + y[q] : y[q];
+        if (pp[q] >= 0) dst[pp[q]] = add ? b[q] + y[q] : y[q];
     });
+    if (outf != 0) continue;  // stage fields are read at computational points only
     // 16 nodes per thread and iteration: one 16-byte load of kinds, the
     // validity flags rewritten from them, unconditional zero stores for u.
     const long long n16 = g.size >> 4;

@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
                 ("mu", ctypes.c_double * 2), ("beta", ctypes.c_double * 2), ("adjoint", ctypes.c_int),
                 ("scheme", ctypes.c_int), ("boundary_data", ctypes.c_int)]
 
-SCHEMES = {"etd1": 1, "etd2": 2, "etd2rk": 3}
+SCHEMES = {"etd1": 1, "etd2": 2, "etd2rk": 3, "etd3rk": 4, "etd4rk": 5}
 
 
 class StepStats(ctypes.Structure):
@@ -86,6 +86,7 @@ def library():
         "etd_init_domain": (I, [P, I, P, P]),
         "etd_step": (I, [P, D, ctypes.POINTER(P), ctypes.POINTER(StepStats)]),
         "etd_phi_combination": (I, [P, I, D, P, P, P, P, ctypes.POINTER(StepStats)]),
+        "etd_phi_combination3": (I, [P, I, D, P, P, P, P, P, ctypes.POINTER(StepStats)]),
         "etd_apply_operator": (I, [P, I, D, P, P]),
         "etd_set_reaction": (I, [P, I, ctypes.POINTER(D)]),
         "etd_step_explicit": (I, [P, I, D, P, P, P, ctypes.POINTER(StepStats)]),
@@ -205,6 +206,14 @@ class Context:
                                                  _ptr(v1, self.n, "v1"), _ptr(v2, self.n, "v2"),
                                                  _ptr(y, self.n, "y"),
                                                  ctypes.byref(st) if st is not None else None))
+        return st.as_dict(1)[0] if st is not None else None
+
+    def phi_combination3(self, species, dt, v0, v1, v2, v3, y, stats=False):
+        st = StepStats() if stats else None
+        self._check(self.lib.etd_phi_combination3(self.ctx, species, float(dt), _ptr(v0, self.n, "v0"),
+                                                  _ptr(v1, self.n, "v1"), _ptr(v2, self.n, "v2"),
+                                                  _ptr(v3, self.n, "v3"), _ptr(y, self.n, "y"),
+                                                  ctypes.byref(st) if st is not None else None))
         return st.as_dict(1)[0] if st is not None else None
 
     def poisson_solve(self, species, f, u, tol=1e-12, max_iter=100000):
