@@ -378,3 +378,38 @@ def test_levelset_step_mixed_precision(lib):
     assert np.max(np.abs(ph_g - ph_o)[near]) <= 1e-6 * g.h
     assert np.max(np.abs(ph_g - ph_o)) <= 1e-4 * g.h
     assert np.max(np.abs(du.cpu().numpy() - ue_o)) <= 1e-10 * np.max(np.abs(ue_o))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_star_free_boundary_at_matched_tolerance(lib, precision):
+    """The star-shaped 3D workload (48^3 on [-3, 3]^3) over 10 free-boundary
+    steps with two reinitialisations, GPU against the FP64 oracle at the same
+    Krylov tolerance.  Mixed precision stays within 1e-5 relative in u and
+    1e-2 h at the interface; its FP32 arithmetic contributes far less than a
+    looser Krylov tolerance would (on star3d, tolerance 1e-5 moves u by about
+    1.6e-5 in FP64 and in mixed precision alike)."""
+    from oracle.freeboundary import FreeBoundary, Species
+    from paper_2209_15095_gb300 import inputs
+
+    w = inputs.star3d(n=48, box=3.0)
+    g = Grid(w.n, w.lo, w.hi)
+    fb = FreeBoundary(g, [Species(w.phi0[0], w.u0[0], 1.0, w.mu[0])], w.reaction, w.rparams, w.tol, w.m_max,
+                      reinit_every=w.reinit_every, reinit_at_start=True)
+    ctx = _ctx(lib, g, precision=precision, tol=w.tol, m_max=w.m_max, mu=w.mu)
+    dph = _dev(w.phi0[0])
+    du = _dev(np.where(w.phi0[0] < 0, w.u0[0], 0.0))
+    ctx.levelset_prepare(dph, True)
+    ctx.init_domain(0, dph)
+    for k in range(10):
+        fb.step(w.dt)
+        ctx.levelset_advance(0, dph, du, w.dt, (k + 1) % w.reinit_every == 0)
+        ctx.init_domain(0, dph)
+        ctx.step(w.dt, [du])
+    ctx.sync()
+    ph_g, u_g = dph.cpu().numpy(), du.cpu().numpy()
+    ph_o, u_o = fb.sp[0].phi, fb.sp[0].u
+    assert ((ph_g < 0) == (ph_o < 0)).all()
+    near = np.abs(ph_o) < g.h
+    assert np.max(np.abs(ph_g - ph_o)[near]) <= (1e-6 if precision == "fp64" else 1e-2) * g.h
+    bound = 10 * w.tol if precision == "fp64" else 1e-5
+    assert np.max(np.abs(u_g - u_o)) <= bound * np.max(np.abs(u_o))
