@@ -27,6 +27,8 @@ struct SpeciesBufs {
   void* W2g = nullptr;
   void* Z[2] = {nullptr, nullptr};
   double* stg[3] = {nullptr, nullptr, nullptr};  // ETD3RK / ETD4RK stage fields
+  int* qidx = nullptr;  // FP32 contexts: aligned 4-node groups of the large split passes
+  int* qk = nullptr;
   const double* beta_field = nullptr;
   // boundary data (params.boundary_data): per point, face and slot
   double* bco = nullptr;
@@ -200,6 +202,10 @@ size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
     b.W2g = cv.take<char>(s * G);
     if (p.scheme == ETD_SCHEME_ETD3RK || p.scheme == ETD_SCHEME_ETD4RK)
       for (int i = 0; i < 3; ++i) b.stg[i] = cv.take<double>(G);
+    if (f32) {
+      b.qidx = cv.take<int>(G / 4 + 1);
+      b.qk = cv.take<int>(G / 4 + 1);
+    }
     if (c) c->sp[sp] = b;
   }
   LevelsetBufs lb = levelset_carve(g, [&](size_t bytes) { return cv.take<char>(bytes); });
@@ -306,6 +312,8 @@ SpeciesDev<T> species_dev(etd_ctx* c, int s, double* u, int stage = 0) {
   d.Z[0] = (T*)b.Z[0];
   d.Z[1] = (T*)b.Z[1];
   for (int i = 0; i < 3; ++i) d.stg[i] = b.stg[i];
+  d.qidx = sizeof(T) == 4 ? b.qidx : nullptr;
+  d.qk = sizeof(T) == 4 ? b.qk : nullptr;
   return d;
 }
 

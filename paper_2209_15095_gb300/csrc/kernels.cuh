@@ -82,6 +82,12 @@ struct SpeciesDev {
   // stage fields a, b, c of the Runge-Kutta schemes (full grid, FP64; only
   // the computational points are written and read)
   double* stg[3];
+  // FP32 contexts: the aligned groups of 4 nodes along the last axis that
+  // hold computational points ("quads"; group index = node >> 2), in order,
+  // and the list index of each group's first computational point (size /
+  // 4 + 1 entries each; nullptr: no quad path)
+  int* qidx;
+  int* qk;
   // caller's source (full grid) and boundary data for this launch: F gains
   // src[p] + sum over the point's face slots of bco * bval (nullptr: none)
   const double* src;

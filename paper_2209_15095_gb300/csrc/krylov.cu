@@ -66,6 +66,7 @@ struct Ctl {
   double t, tau, ynorm, beta, err, hn;
   int m, accepted, breakdown, last, abort, nrej;
   int trace0;  // trace entries of earlier launches of the step (block 0)
+  int nquad, qoff;  // quad list: length, and this block's first entry
 };
 
 // ---------------------------------------------------------------------------
@@ -333,21 +334,271 @@ __device__ __forceinline__ double* part_buf(double* part, int& red) {
 // by TwoSum, all error terms (and clo_i V_i) in a second float.  About 2^-46
 // relative to sum |coef_i V_i|, at FP32 rate instead of one FP64 FMA per
 // basis vector.
+__device__ __forceinline__ void dot2_step(float& s, float& e, float chi, float clo, float a) {
+  const float pr = __fmul_rn(chi, a);
+  const float pe = __fmaf_rn(chi, a, -pr);
+  const float t = __fadd_rn(s, pr);
+  const float z = __fsub_rn(t, s);
+  const float te = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(pr, z));
+  s = t;
+  e = __fadd_rn(e, __fadd_rn(te, __fmaf_rn(clo, a, pe)));
+}
+
 __device__ __forceinline__ double basis_sum_f32(const Ctl& c, const float* __restrict__ V, long long vs, long long p,
                                                 int m) {
   float s = 0.f, e = 0.f;
 #pragma unroll 4
-  for (int i = 0; i < m; ++i) {
-    const float a = __ldcg(V + (long long)i * vs + p);
-    const float pr = __fmul_rn(c.chi[i], a);
-    const float pe = __fmaf_rn(c.chi[i], a, -pr);
-    const float t = __fadd_rn(s, pr);
-    const float z = __fsub_rn(t, s);
-    const float te = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(pr, z));
-    s = t;
-    e = __fadd_rn(e, __fadd_rn(te, __fmaf_rn(c.clo[i], a, pe)));
-  }
+  for (int i = 0; i < m; ++i) dot2_step(s, e, c.chi[i], c.clo[i], __ldcg(V + (long long)i * vs + p));
   return to_f64(s) + to_f64(e);
+}
+
+// ---------------------------------------------------------------------------
+// Quad path of the split Lanczos passes (FP32 vectors, constant beta, last
+// axis a multiple of 4 nodes).  The passes run over the aligned groups of 4
+// nodes that hold computational points, with 16-byte loads and stores of
+// the grid vectors and no per-point index: every grid vector is zero off the
+// computational set (the set-up zeroes them, the passes keep them so), so
+// the other lanes of a group compute zeros.  More bytes in flight per
+// thread than the per-point loop, whose dependent index-then-data loads
+// keep the passes latency-bound.
+constexpr int QA_U = 2;  // groups in flight per thread, pass A
+constexpr int QB_U = 1;  // pass B
+
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void st4(float* p, float4 v) { __stcg(reinterpret_cast<float4*>(p), v); }
+
+// Pass A on groups of 4 nodes: V_j = ca Z_{j-1} + cb V_{j-1} + cc V_{j-2}.
+// Out of line: the Lanczos loop around the call is near the register limit.
+__device__ __noinline__ void quad_pass_a(const float* __restrict__ Zp, const float* __restrict__ V1,
+                                         const float* __restrict__ V2, float* __restrict__ Vj, float ca, float cb,
+                                         float cc, const int* __restrict__ qidx, int nq, long long gtid, long long gth) {
+  node_loop<QA_U>(gtid, gth, nq, qidx, [&](const auto& kk, const auto& pp) {
+    constexpr int U = NL_U(kk);
+    float4 zv[U], v1v[U], v2v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (pp[u] < 0) continue;
+      const long long p4 = (long long)pp[u] << 2;
+      zv[u] = ld4(Zp + p4);
+      v1v[u] = ld4(V1 + p4);
+      v2v[u] = ld4(V2 + p4);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (pp[u] < 0) continue;
+      const long long p4 = (long long)pp[u] << 2;
+      st4(Vj + p4, make_float4(ca * zv[u].x + cb * v1v[u].x + cc * v2v[u].x,
+                               ca * zv[u].y + cb * v1v[u].y + cc * v2v[u].y,
+                               ca * zv[u].z + cb * v1v[u].z + cc * v2v[u].z,
+                               ca * zv[u].w + cb * v1v[u].w + cc * v2v[u].w));
+    }
+  });
+}
+
+struct QuadSums {
+  double d1, d2, d3;
+};
+
+// Pass B on groups of 4 nodes: Z_j = A V_j at the computational points (0 at
+// the group's other nodes), |V_j|^2, <Z_j, V_j>, <Z_j, V_{j-1}> (this
+// thread's FP32 Dot2 sums).  The group's computational points are
+// consecutive in the list, so their diagonals follow the group's first list
+// index.  Out of line, as pass A.
+template <int N>
+__device__ __noinline__ QuadSums quad_pass_b(const float* __restrict__ Vj, const float* __restrict__ V1,
+                                             float* __restrict__ Zn, const uint8_t* __restrict__ kind,
+                                             const float* __restrict__ diagf, const int* __restrict__ qidx,
+                                             const int* __restrict__ qk, int nq, const GridDev& g, float cfac,
+                                             float bc, long long gtid, long long gth) {
+  long long st[N > 1 ? N - 1 : 1];
+#pragma unroll
+  for (int d = 0; d < N - 1; ++d) st[d] = g.stride[d];
+  Acc<float> d1, d2, d3;
+  node_loop<QB_U>(gtid, gth, nq, qidx, [&](const auto& kk, const auto& pp) {
+    constexpr int U = NL_U(kk);
+    float4 vc[U], sm[U], w1[U], dg[U];
+    float vl[U], vr[U];
+    unsigned kw[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (pp[u] < 0) continue;
+      const long long p4 = (long long)pp[u] << 2;
+      const int k0 = __ldg(qk + kk[u]);
+      vc[u] = ld4(Vj + p4);
+      vl[u] = __ldcg(Vj + p4 - 1);
+      vr[u] = __ldcg(Vj + p4 + 4);
+      float4 sacc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int d = 0; d < N - 1; ++d) {
+        const float4 m = ld4(Vj + p4 - st[d]), q = ld4(Vj + p4 + st[d]);
+        sacc.x += m.x + q.x;
+        sacc.y += m.y + q.y;
+        sacc.z += m.z + q.z;
+        sacc.w += m.w + q.w;
+      }
+      sm[u] = sacc;
+      w1[u] = ld4(V1 + p4);
+      kw[u] = __ldg(reinterpret_cast<const unsigned*>(kind + p4));
+      dg[u] = make_float4(__ldg(diagf + k0), __ldg(diagf + k0 + 1), __ldg(diagf + k0 + 2), __ldg(diagf + k0 + 3));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (pp[u] < 0) continue;
+      const long long p4 = (long long)pp[u] << 2;
+      const float v[4] = {vc[u].x, vc[u].y, vc[u].z, vc[u].w};
+      const float so[4] = {sm[u].x, sm[u].y, sm[u].z, sm[u].w};
+      const float sx[4] = {vl[u] + vc[u].y, vc[u].x + vc[u].z, vc[u].y + vc[u].w, vc[u].z + vr[u]};
+      const float wv[4] = {w1[u].x, w1[u].y, w1[u].z, w1[u].w};
+      float z[4];
+      int rank = 0;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const bool comp = ((kw[u] >> (8 * l)) & 3u) == K_COMP;
+        const float D = rank == 0 ? dg[u].x : rank == 1 ? dg[u].y : rank == 2 ? dg[u].z : dg[u].w;
+        // as stencil(): the last axis is added last
+        z[l] = comp ? cfac * (bc * (so[l] + sx[l]) - D * v[l]) : 0.f;
+        rank += comp ? 1 : 0;
+      }
+      st4(Zn + p4, make_float4(z[0], z[1], z[2], z[3]));
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        d1.add(v[l], v[l]);
+        d2.add(z[l], v[l]);
+        d3.add(z[l], wv[l]);
+      }
+    }
+  });
+  return QuadSums{d1.value(), d2.value(), d3.value()};
+}
+
+// The combination y <- y + tau w_1 (+ tau^2/2 w_2) + sum_i coef_i V_i on
+// groups of 4 nodes: per computational point the arithmetic of the per-point
+// loop (the same Dot2 basis sum in the same order, so the same bits), with
+// 16-byte loads of the basis vectors, eight in flight.  Writes y (compact,
+// FP64) and its FP32 grid copy (0 at the group's other nodes); returns this
+// thread's sum of y^2.
+__device__ __noinline__ double quad_combination(const float* __restrict__ chi, const float* __restrict__ clo, int m,
+                                                double tau, const float* __restrict__ V, long long vs,
+                                                const float* __restrict__ W1g, const float* __restrict__ W2g,
+                                                double* __restrict__ Yc, float* __restrict__ Yg,
+                                                const uint8_t* __restrict__ kind, const int* __restrict__ qidx,
+                                                const int* __restrict__ qk, int nq, long long gtid, long long gth) {
+  double yn = 0.0;
+  const double h2 = 0.5 * tau * tau;
+  for (long long q = gtid; q < nq; q += gth) {
+    const long long p4 = (long long)__ldg(qidx + q) << 2;
+    const int k0 = __ldg(qk + q);
+    const unsigned kw = __ldg(reinterpret_cast<const unsigned*>(kind + p4));
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < m; ++i) {
+      const float4 a4 = ld4(V + (long long)i * vs + p4);
+      const float ch = chi[i], cl = clo[i];
+      dot2_step(s0, e0, ch, cl, a4.x);
+      dot2_step(s1, e1, ch, cl, a4.y);
+      dot2_step(s2, e2, ch, cl, a4.z);
+      dot2_step(s3, e3, ch, cl, a4.w);
+    }
+    const float4 w1 = ld4(W1g + p4);
+    const float4 w2 = W2g ? ld4(W2g + p4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float sl[4] = {s0, s1, s2, s3}, el[4] = {e0, e1, e2, e3};
+    const float w1l[4] = {w1.x, w1.y, w1.z, w1.w}, w2l[4] = {w2.x, w2.y, w2.z, w2.w};
+    float yo[4];
+    int rank = 0;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      yo[l] = 0.f;
+      if (((kw >> (8 * l)) & 3u) != K_COMP) continue;
+      const long long k = k0 + rank;
+      ++rank;
+      double y = fma(tau, (double)w1l[l], __ldcg(Yc + k)) + (to_f64(sl[l]) + to_f64(el[l]));
+      if (W2g) y = fma(h2, (double)w2l[l], y);
+      Yc[k] = y;
+      yo[l] = (float)y;
+      yn = fma(y, y, yn);
+    }
+    st4(Yg + p4, make_float4(yo[0], yo[1], yo[2], yo[3]));
+  }
+  return yn;
+}
+
+// Builds the quad list from the sorted list of computational points: each
+// warp takes a contiguous range of list indices (ranges in block, then warp
+// order); a list index starts a group when its group differs from the
+// previous index's.  Counts per warp, one grid barrier for the per-block
+// totals, then ordered writes at the warp's offset (warp ballots, no block
+// barrier in the loop).  Eight 32-index loads in flight per warp.  Returns
+// false if the kernel must stop.
+template <typename T>
+__device__ bool build_quads(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int ncomp, Ctl& c, unsigned& bar,
+                            int& red) {
+  constexpr int QU = 8;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const long long nwt = (long long)gridDim.x * nw;
+  const long long per = ((long long)ncomp + nwt - 1) / nwt;
+  const long long gw = (long long)blockIdx.x * nw + wid;
+  const long long kw0 = min((long long)ncomp, gw * per);
+  const long long kw1 = min((long long)ncomp, kw0 + per);
+  const int* __restrict__ idx = S.idx;
+  __shared__ int s_wc[32];
+  int cnt = 0;
+  for (long long kb = kw0; kb < kw1; kb += 32 * QU) {
+    int q[QU], qp[QU];
+#pragma unroll
+    for (int u = 0; u < QU; ++u) {
+      const long long k = kb + u * 32 + lane;
+      q[u] = k < kw1 ? (__ldg(idx + k) >> 2) : -1;
+      qp[u] = (k < kw1 && k > 0) ? (__ldg(idx + k - 1) >> 2) : -2;
+    }
+#pragma unroll
+    for (int u = 0; u < QU; ++u) cnt += (q[u] >= 0 && qp[u] != q[u]) ? 1 : 0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) s_wc[wid] = cnt;
+  __syncthreads();
+  double* pb = part_buf(a.part, red);
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int w = 0; w < nw; ++w) tot += s_wc[w];
+    pb[blockIdx.x] = (double)tot;
+  }
+  if (!grid_barrier(a.st, bar, 20)) return false;
+  if (threadIdx.x == 0) {
+    long long off = 0, tot = 0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      const long long x = (long long)__ldcg(pb + b);
+      if (b < (int)blockIdx.x) off += x;
+      tot += x;
+    }
+    c.qoff = (int)off;
+    c.nquad = (int)tot;
+  }
+  __syncthreads();
+  int base = c.qoff;
+  for (int w = 0; w < wid; ++w) base += s_wc[w];
+  const unsigned below = (1u << lane) - 1u;
+  for (long long kb = kw0; kb < kw1; kb += 32 * QU) {
+    int q[QU], qp[QU];
+#pragma unroll
+    for (int u = 0; u < QU; ++u) {
+      const long long k = kb + u * 32 + lane;
+      q[u] = k < kw1 ? (__ldg(idx + k) >> 2) : -1;
+      qp[u] = (k < kw1 && k > 0) ? (__ldg(idx + k - 1) >> 2) : -2;
+    }
+#pragma unroll
+    for (int u = 0; u < QU; ++u) {
+      const bool head = q[u] >= 0 && qp[u] != q[u];
+      const unsigned bal = __ballot_sync(0xffffffffu, head);
+      if (head) {
+        const int pos = base + __popc(bal & below);
+        S.qidx[pos] = q[u];
+        S.qk[pos] = (int)(kb + u * 32 + lane);
+      }
+      base += __popc(bal);
+    }
+  }
+  return true;
 }
 
 template <typename T, int N>
@@ -363,8 +614,12 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   const int m_max = a.m_max;
   const int P = a.p == 3 ? 3 : 2;  // highest phi index (any other value: 2)
   const long long vs = g.size;
-  // large problems: split Lanczos pass (see SPLIT_MIN)
+  // large problems: split Lanczos pass (see SPLIT_MIN), on aligned groups of
+  // 4 nodes where the layout allows
   const bool split = ncomp >= SPLIT_MIN<T>;
+  const bool quad = sizeof(T) == 4 && split && S.qidx != nullptr && S.beta_field == nullptr &&
+                    (g.n[N - 1] & 3) == 0;
+  if (quad && !build_quads<T>(a, S, ncomp, c, bar, red)) return false;
   // the statistics accumulate over the launches of one step (zeroed by the host)
   if (blockIdx.x == 0 && threadIdx.x == 0) c.trace0 = a.stats ? a.stats->trace_len[sidx] : 0;
   double* pb = nullptr;
@@ -508,7 +763,21 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         const T* V1 = S.V + (long long)(j - 1) * vs;
         const T* V2 = S.V + (long long)(j >= 2 ? j - 2 : 0) * vs;
         T* Vj = S.V + (long long)j * vs;
-        if (split) {
+        bool quad_done = false;
+        if constexpr (sizeof(T) == 4) {
+          if (quad) {
+            const int nq = c.nquad;
+            quad_pass_a(Zp, V1, V2, Vj, ca, cb, cc, S.qidx, nq, gtid, gthreads);
+            if (!grid_barrier(a.st, bar, 15)) return false;
+            const QuadSums qs = quad_pass_b<N>(Vj, V1, Zn, S.kind, S.diagf, S.qidx, S.qk, nq, g, cfac, bc, gtid, gthreads);
+            double v[3] = {qs.d1, qs.d2, qs.d3};
+            pb = part_buf(a.part, red);
+            block_partials<3>(v, pb);
+            quad_done = true;
+          }
+        }
+        if (quad_done) {
+        } else if (split) {
           // pass A_j: V_j = w_j at the own points only
           constexpr int U = SPLIT_U<T>;
           node_loop<U>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
@@ -665,7 +934,15 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         }
         __syncthreads();
       }
-      for (long long k = gtid; k < ncomp; k += gthreads) {
+      bool qdone = false;
+      if constexpr (sizeof(T) == 4) {
+        if (quad) {
+          yn.s = quad_combination(c.chi, c.clo, m, tau, S.V, vs, S.W1g, P == 3 ? S.W2g : nullptr, S.Yc, S.Yg, S.kind,
+                                  S.qidx, S.qk, c.nquad, gtid, gthreads);
+          qdone = true;
+        }
+      }
+      for (long long k = qdone ? (long long)ncomp : gtid; k < ncomp; k += gthreads) {
         const long long p = __ldg(S.idx + k);
         double sum;
         if constexpr (sizeof(T) == 4) {

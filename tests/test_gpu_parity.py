@@ -413,3 +413,29 @@ def test_star_free_boundary_at_matched_tolerance(lib, precision):
     assert np.max(np.abs(ph_g - ph_o)[near]) <= (1e-6 if precision == "fp64" else 1e-2) * g.h
     bound = 10 * w.tol if precision == "fp64" else 1e-5
     assert np.max(np.abs(u_g - u_o)) <= bound * np.max(np.abs(u_o))
+
+
+@pytest.mark.parametrize("ndim,n", [(2, 944), (3, 139), (4, 56)])
+def test_phi_combination_mixed_large_layouts(lib, ndim, n):
+    """Large FP32 problems (at least 2^18 points): with the last axis a
+    multiple of 4 nodes (944, 56) the split Lanczos passes run on aligned
+    groups of 4 nodes; with 139 they keep the per-point loop.  Both against
+    the FP64 oracle at 1e-5, one and two calls on the same context."""
+    g = Grid((n,) * ndim, (-2.0,) * ndim, (2.0,) * ndim)
+    ph = np.sqrt(sum(c * c for c in g.coords())) - 1.24
+    op = EBOperator(g, ph, 1.0)
+    assert op.ncomp >= 1 << 18
+    ctx = _ctx(lib, g, precision="mixed", tol=1e-7, m_max=40)
+    ctx.init_domain(0, _dev(ph))
+    rng = np.random.default_rng(23)
+    u = rng.uniform(0, 1, op.ncomp)
+    dt = g.h * g.h
+    vs = [u, dt * u * (1 - u), 0.1 * dt * u * (1 - u)]
+    yo, _ = krylov.phipm(lambda x: dt * (op.C @ x), vs, 1e-12, 40, dt * op.gershgorin())
+    for _ in range(2):
+        y = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+        st = ctx.phi_combination(0, dt, *[_dev(op.to_grid(v)) for v in vs], y, stats=True)
+        assert st["krylov_iters"] >= 5
+        yg = op.from_grid(y.cpu().numpy())
+        assert np.max(np.abs(yg - yo)) <= 1e-5 * np.max(np.abs(yo))
+        assert np.all(y.cpu().numpy()[~op.comp] == 0.0)
