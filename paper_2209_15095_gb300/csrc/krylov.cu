@@ -471,6 +471,73 @@ __device__ __noinline__ QuadSums quad_pass_b(const float* __restrict__ Vj, const
   return QuadSums{d1.value(), d2.value(), d3.value()};
 }
 
+// out = A X + a1 + c2 a2 + c3 a3 on groups of 4 nodes (the first NT terms;
+// a1, a2, a3 compact, at the group's list indices), 0 at the group's other
+// nodes: the w_j passes and P_0.  With SUMS: |X|^2 and <out, X> (this
+// thread's FP32 Dot2 sums).  Out of line, as pass A.
+template <int N, int NT, bool SUMS>
+__device__ __noinline__ QuadSums quad_stencil(const float* __restrict__ X, float* __restrict__ out,
+                                              const float* __restrict__ a1, const float* __restrict__ a2,
+                                              const float* __restrict__ a3, float c2, float c3,
+                                              const uint8_t* __restrict__ kind, const float* __restrict__ diagf,
+                                              const int* __restrict__ qidx, const int* __restrict__ qk, int nq,
+                                              const GridDev& g, float cfac, float bc, long long gtid, long long gth) {
+  long long st[N > 1 ? N - 1 : 1];
+#pragma unroll
+  for (int d = 0; d < N - 1; ++d) st[d] = g.stride[d];
+  Acc<float> d1, d2;
+  for (long long q = gtid; q < nq; q += gth) {
+    const long long p4 = (long long)__ldg(qidx + q) << 2;
+    const int k0 = __ldg(qk + q);
+    const float4 vc = ld4(X + p4);
+    const float vl = __ldcg(X + p4 - 1), vr = __ldcg(X + p4 + 4);
+    float4 sacc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int d = 0; d < N - 1; ++d) {
+      const float4 m = ld4(X + p4 - st[d]), pq = ld4(X + p4 + st[d]);
+      sacc.x += m.x + pq.x;
+      sacc.y += m.y + pq.y;
+      sacc.z += m.z + pq.z;
+      sacc.w += m.w + pq.w;
+    }
+    const unsigned kw = __ldg(reinterpret_cast<const unsigned*>(kind + p4));
+    float dg[4], t1[4], t2[4], t3[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      dg[r] = __ldg(diagf + k0 + r);
+      t1[r] = NT >= 1 ? __ldcg(a1 + k0 + r) : 0.f;
+      t2[r] = NT >= 2 ? __ldcg(a2 + k0 + r) : 0.f;
+      t3[r] = NT >= 3 ? __ldcg(a3 + k0 + r) : 0.f;
+    }
+    const float v[4] = {vc.x, vc.y, vc.z, vc.w};
+    const float so[4] = {sacc.x, sacc.y, sacc.z, sacc.w};
+    const float sx[4] = {vl + vc.y, vc.x + vc.z, vc.y + vc.w, vc.z + vr};
+    float z[4];
+    int rank = 0;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      z[l] = 0.f;
+      if (((kw >> (8 * l)) & 3u) != K_COMP) continue;
+      const int r = rank++;
+      const float D = r == 0 ? dg[0] : r == 1 ? dg[1] : r == 2 ? dg[2] : dg[3];
+      float w = cfac * (bc * (so[l] + sx[l]) - D * v[l]);
+      if (NT >= 1) w = w + (r == 0 ? t1[0] : r == 1 ? t1[1] : r == 2 ? t1[2] : t1[3]);
+      if (NT >= 2) w = w + c2 * (r == 0 ? t2[0] : r == 1 ? t2[1] : r == 2 ? t2[2] : t2[3]);
+      if (NT >= 3) w = w + c3 * (r == 0 ? t3[0] : r == 1 ? t3[1] : r == 2 ? t3[2] : t3[3]);
+      z[l] = w;
+    }
+    st4(out + p4, make_float4(z[0], z[1], z[2], z[3]));
+    if (SUMS) {
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        d1.add(v[l], v[l]);
+        d2.add(z[l], v[l]);
+      }
+    }
+  }
+  return QuadSums{d1.value(), d2.value(), 0.0};
+}
+
 // The combination y <- y + tau w_1 (+ tau^2/2 w_2) + sum_i coef_i V_i on
 // groups of 4 nodes: per computational point the arithmetic of the per-point
 // loop (the same Dot2 basis sum in the same order, so the same bits), with
@@ -643,6 +710,33 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
     }
     __syncthreads();
     const double t = c.t;
+    bool qw = false;
+    if constexpr (sizeof(T) == 4) {
+      if (quad) {
+        // the w_j passes on groups of 4 nodes
+        const int nq = c.nquad;
+        const float tt = (float)t;
+        if (P == 3) {
+          quad_stencil<N, 3, false>(S.Yg, S.W1g, S.V1c, S.V2c, S.V3c, tt, (float)(0.5 * t * t), S.kind, S.diagf,
+                          S.qidx, S.qk, nq, g, cfac, bc, gtid, gthreads);
+          if (!grid_barrier(a.st, bar, 10)) return false;
+          quad_stencil<N, 2, false>(S.W1g, S.W2g, S.V2c, S.V3c, nullptr, tt, 0.f, S.kind, S.diagf, S.qidx, S.qk, nq, g,
+                          cfac, bc, gtid, gthreads);
+          if (!grid_barrier(a.st, bar, 16)) return false;
+          quad_stencil<N, 1, false>(S.W2g, S.V, S.V3c, nullptr, nullptr, 0.f, 0.f, S.kind, S.diagf, S.qidx, S.qk, nq, g,
+                          cfac, bc, gtid, gthreads);
+        } else {
+          quad_stencil<N, 2, false>(S.Yg, S.W1g, S.V1c, S.V2c, nullptr, tt, 0.f, S.kind, S.diagf, S.qidx, S.qk, nq, g,
+                          cfac, bc, gtid, gthreads);
+          if (!grid_barrier(a.st, bar, 10)) return false;
+          quad_stencil<N, 1, false>(S.W1g, S.V, S.V2c, nullptr, nullptr, 0.f, 0.f, S.kind, S.diagf, S.qidx, S.qk, nq, g,
+                          cfac, bc, gtid, gthreads);
+        }
+        qw = true;
+      }
+    }
+    if (qw) {
+    } else
     if (P == 3) {
       // w_1 = A y + v_1 + t v_2 + t^2/2 v_3, w_2 = A w_1 + v_2 + t v_3,
       // w_3 = A w_2 + v_3 -> V_0 (one point per thread: register bound)
@@ -700,7 +794,18 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
     }
     if (!grid_barrier(a.st, bar, 11)) return false;
     // P_0: Z_0 = A V_0, |V_0|^2, <Z_0, V_0>
-    {
+    bool qp0 = false;
+    if constexpr (sizeof(T) == 4) {
+      if (quad) {
+        const QuadSums qs = quad_stencil<N, 0, true>(S.V, S.Z[0], nullptr, nullptr, nullptr, 0.f, 0.f, S.kind, S.diagf,
+                                            S.qidx, S.qk, c.nquad, g, cfac, bc, gtid, gthreads);
+        double v[2] = {qs.d1, qs.d2};
+        pb = part_buf(a.part, red);
+        block_partials<2>(v, pb);
+        qp0 = true;
+      }
+    }
+    if (!qp0) {
       Acc<T> d1, d2;
       node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
         constexpr int U = NL_U(kk);
@@ -1094,6 +1199,12 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
                 (s == 0 ? reaction(a.reaction, a.rp, 0, u, other) : reaction(a.reaction, a.rp, 1, other, u)) +
                 extra_F<T, N>(S, kk[q], p);
             const double Fp = S.fvalid[p] ? S.Fprev[p] : F;
+            if (a.mode == MODE_ETD2) {
+              // F_{n-1} <- F_n in place: only this thread reads this
+              // species' F_{n-1} at p (the other species reads u)
+              S.Fprev[p] = F;
+              S.fvalid[p] = 1;
+            }
             const bool rk2 = a.mode == MODE_RK2;
             y[q] = rk2 ? 0.0 : u;
             v1[q] = rk2 ? 0.0 : a.dt * F;
@@ -1137,27 +1248,6 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
     tot[s][1] = t01[1];
     tot[s][2] = t23[0];
     tot[s][3] = t23[1];
-  }
-  // F_{n-1} <- F_n after every species has read the fields
-  if (a.mode == MODE_ETD2) {
-    for (int s = 0; s < a.nspecies; ++s) {
-      const SpeciesDev<T>& S = a.sp[s];
-      const int ncomp = *S.ncomp;
-      for (long long k = gtid; k < ncomp; k += gthreads) {
-        const long long p = __ldg(S.idx + k);
-        // F_n = v_1 / dt recomputed exactly as in the set-up
-        const double u = S.u[p];
-        double other = 0.0;
-        if (a.nspecies == 2) {
-          const SpeciesDev<T>& O = a.sp[1 - s];
-          other = (O.kind[p] & 3) == K_COMP ? O.u[p] : 0.0;
-        }
-        const double F = (s == 0 ? reaction(a.reaction, a.rp, 0, u, other) : reaction(a.reaction, a.rp, 1, other, u)) +
-                         extra_F<T, N>(S, k, p);
-        S.Fprev[p] = F;
-        S.fvalid[p] = 1;
-      }
-    }
   }
   for (int s = 0; s < a.nspecies; ++s) {
     const double vscale = fmax(fmax(sqrt(tot[s][1]), sqrt(tot[s][2])), sqrt(tot[s][3]));
