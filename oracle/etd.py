@@ -19,6 +19,15 @@ are those of Eq. 3.7, phi_k(z) = int_0^1 e^{(1-l) z} l^{k-1} dl, so its phi_3
 is twice the standard phi_3 (which carries 1 / 2!); the paper's recursion,
 Eq. 3.8, confirms that normalisation.  The combinations here use the standard
 phi_k, so the phi_3 vector of the final stage is the paper's times two.
+Multistep ETD3 (Eq. 3.8b with s = 3): the weights g_m are defined by integrals,
+so they do not depend on the phi normalisation; with the standard phi_k,
+g_0 = phi_1, g_1 = phi_2 and g_2 = phi_3 + phi_2 / 2 (the binomial
+(-lambda choose 2) = lambda (lambda + 1) / 2).  With the backward differences
+of F this is one combination:
+    v_0 = U_n, v_1 = dt F_n, v_2 = dt (3/2 F_n - 2 F_{n-1} + 1/2 F_{n-2}),
+    v_3 = dt (F_n - 2 F_{n-1} + F_{n-2}).
+Start-up (a reading, extending the ETD2 one): with one earlier F the step is
+ETD2, with none it is ETD1.
 """
 import numpy as np
 
@@ -136,11 +145,22 @@ def etd4rk_step(op, u_n, F_of, t_n, dt, tol=1e-10, m_max=40, exact=False):
     return u, (a, b, c), (tr_a, tr_b, tr_c, tr_u)
 
 
+def etd3_vectors(u_n, F_n, F_nm1, F_nm2, dt):
+    """(v_0, v_1, v_2, v_3) of the multistep ETD3 step (Eq. 3.8b, s = 3)."""
+    return [u_n, dt * F_n, dt * (1.5 * F_n - 2.0 * F_nm1 + 0.5 * F_nm2), dt * (F_n - 2.0 * F_nm1 + F_nm2)]
+
+
+def etd3_step(op, u_n, F_n, F_nm1, F_nm2, dt, tol=1e-10, m_max=40, exact=False):
+    """One multistep ETD3 step.  Returns (U_{n+1}, trace)."""
+    return combination(op, etd3_vectors(u_n, F_n, F_nm1, F_nm2, dt), dt, tol, m_max, exact)
+
+
 def run_fixed_domain(op, u0, dt, nsteps, F_of, tol=1e-10, m_max=40, exact=False, scheme="etd2"):
-    """nsteps steps of `scheme` (etd1, etd2, etd2rk, etd3rk or etd4rk) on a fixed domain.
+    """nsteps steps of `scheme` (etd1, etd2, etd2rk, etd3rk, etd4rk or etd3) on a fixed domain.
     F_of(U, t) -> F vector.  Returns U at t = nsteps dt."""
     u = np.array(u0, dtype=np.float64, copy=True)
     F_prev = None
+    hist = []  # etd3: F_n, F_{n-1}, F_{n-2}
     t = 0.0
     for _ in range(nsteps):
         if scheme == "etd2rk":
@@ -148,6 +168,14 @@ def run_fixed_domain(op, u0, dt, nsteps, F_of, tol=1e-10, m_max=40, exact=False,
         elif scheme in ("etd3rk", "etd4rk"):
             step = etd3rk_step if scheme == "etd3rk" else etd4rk_step
             u, _, _ = step(op, u, F_of, t, dt, tol=tol, m_max=m_max, exact=exact)
+        elif scheme == "etd3":
+            F_n = F_of(u, t)
+            hist.insert(0, F_n)
+            if len(hist) >= 3:
+                u, _ = etd3_step(op, u, hist[0], hist[1], hist[2], dt, tol=tol, m_max=m_max, exact=exact)
+            else:
+                u, _ = etd2_step(op, u, hist[0], hist[-1], dt, tol=tol, m_max=m_max, exact=exact)
+            del hist[3:]
         else:
             F_n = F_of(u, t)
             if F_prev is None or scheme == "etd1":

@@ -280,3 +280,81 @@ def test_etdrk34_stiff_system_orders():
     assert math.log2(e3[1] / e3[2]) > 2.6, e3
     e2 = err("etd2rk", 64)
     assert e4[1] < 5e-3 * e2 and err("etd3rk", 64) < 5e-3 * e2
+
+
+# ---- multistep ETD3 (Eq. 3.8b, s = 3)
+
+def _g_m(m, z):
+    """g_m(z) of Eq. 3.8b by quadrature: (-1)^m int_0^1 e^{(1-l) z} binom(-l, m) dl."""
+    from scipy.integrate import quad
+
+    def binom(x, k):
+        out = 1.0
+        for i in range(k):
+            out *= (x - i) / (i + 1)
+        return out
+
+    return (-1) ** m * quad(lambda l: math.exp((1.0 - l) * z) * binom(-l, m), 0.0, 1.0, epsabs=1e-15,
+                            epsrel=1e-14)[0]
+
+
+def test_etd3_multistep_matches_eq38b():
+    # one scalar step from the vectors against Eq. 3.8b written out with the
+    # quadrature weights and the backward differences of F
+    for c, dt in ((-3.0, 0.2), (-40.0, 0.05), (0.5, 0.1)):
+        op = _ScalarOp(c)
+        u, F0, F1, F2 = 0.4, 0.7, -0.2, 1.1  # F_n, F_{n-1}, F_{n-2}
+        z = c * dt
+        d1, d2 = F0 - F1, F0 - 2 * F1 + F2
+        want = math.exp(z) * u + dt * (_g_m(0, z) * F0 + _g_m(1, z) * d1 + _g_m(2, z) * d2)
+        got = etd.etd3_step(op, np.array([u]), np.array([F0]), np.array([F1]), np.array([F2]), dt, tol=1e-14,
+                            m_max=8)[0][0]
+        assert abs(got - want) <= 1e-13 * max(1.0, abs(want)), (c, got, want)
+
+
+def test_etd3_multistep_exact_for_quadratic_forcing():
+    # with exact history the step integrates the quadratic through
+    # t_{n-2}, t_{n-1}, t_n, so a forcing quadratic in t is exact
+    c, coef, t0, dt, u0 = -3.0, (0.7, -1.3, 0.9), 0.3, 0.2, 0.4
+    op = _ScalarOp(c)
+    q = lambda t: coef[0] + coef[1] * t + coef[2] * t * t
+    got = etd.etd3_step(op, np.array([u0]), np.array([q(t0)]), np.array([q(t0 - dt)]), np.array([q(t0 - 2 * dt)]),
+                        dt, tol=1e-14, m_max=8)[0][0]
+    assert abs(got - _poly_forced_exact(c, coef, t0, u0, dt)) < 1e-14
+    # ETD2 with the same data is not exact (its interpolant is linear)
+    e2 = etd.etd2_step(op, np.array([u0]), np.array([q(t0)]), np.array([q(t0 - dt)]), dt, tol=1e-14, m_max=8)[0][0]
+    assert abs(e2 - _poly_forced_exact(c, coef, t0, u0, dt)) > 1e-6
+
+
+def test_etd3_multistep_order_3():
+    # the Bernoulli equation u' = c u + u (1 - u), started from the closed form
+    # at t_0, t_1, t_2 (exact history), then multistep ETD3 steps to T
+    c, u0, T = -2.0, 0.6, 1.0
+    r = 1.0 + c
+    exact = lambda t: r * u0 * math.exp(r * t) / (r + u0 * (math.exp(r * t) - 1.0))
+    op = _ScalarOp(c)
+    F = lambda u: u * (1.0 - u)
+    errs = []
+    for n in (10, 20, 40, 80):
+        dt = T / n
+        us = [exact(0.0), exact(dt), exact(2 * dt)]
+        for k in range(2, n):
+            Fs = [F(np.array([us[k - i]])) for i in range(3)]
+            us.append(etd.etd3_step(op, np.array([us[k]]), Fs[0], Fs[1], Fs[2], dt, tol=1e-14, m_max=8)[0][0])
+        errs.append(abs(us[n] - exact(T)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(1, 3)]
+    assert min(orders) > 2.7, (errs, orders)
+
+
+def test_etd3_multistep_start_up_reading():
+    # with no earlier F the first step is ETD1, with one it is ETD2
+    g = Grid((14, 14), (-2, -2), (2, 2))
+    op = EBOperator(g, g.radius() - 1.3, 1.0)
+    u0 = np.random.default_rng(6).uniform(0, 1, op.ncomp)
+    F_of = lambda u, t: u * (1.0 - u)
+    dt = 0.05
+    u1 = etd.run_fixed_domain(op, u0, dt, 1, F_of, tol=1e-12, scheme="etd3")
+    assert np.max(np.abs(u1 - etd.etd1_step(op, u0, F_of(u0, 0), dt, tol=1e-12)[0])) <= 1e-14
+    u2 = etd.run_fixed_domain(op, u0, dt, 2, F_of, tol=1e-12, scheme="etd3")
+    want = etd.etd2_step(op, u1, F_of(u1, dt), F_of(u0, 0), dt, tol=1e-12)[0]
+    assert np.max(np.abs(u2 - want)) <= 1e-14
