@@ -58,7 +58,14 @@ typedef struct {
 
 enum { ETD_REACTION_NONE = 0, ETD_REACTION_LOGISTIC = 1, ETD_REACTION_LOGISTIC_AK = 2, ETD_REACTION_COMPETITION = 3 };
 enum { ETD_PRECISION_FP64 = 0, ETD_PRECISION_MIXED = 1 };
-enum { ETD_SCHEME_ETD1 = 1, ETD_SCHEME_ETD2 = 2, ETD_SCHEME_ETD2RK = 3, ETD_SCHEME_ETD3RK = 4, ETD_SCHEME_ETD4RK = 5 };
+enum {
+  ETD_SCHEME_ETD1 = 1,
+  ETD_SCHEME_ETD2 = 2,
+  ETD_SCHEME_ETD2RK = 3,
+  ETD_SCHEME_ETD3RK = 4,
+  ETD_SCHEME_ETD4RK = 5,
+  ETD_SCHEME_ETD3 = 6
+};
 
 /* Method parameters.
  *   nspecies    1 or 2
@@ -81,10 +88,11 @@ enum { ETD_SCHEME_ETD1 = 1, ETD_SCHEME_ETD2 = 2, ETD_SCHEME_ETD2RK = 3, ETD_SCHE
  *   adjoint     1 to reserve the workspace of etd_adjoint_step (species 0)
  *   scheme      time integrator of etd_step (Sec. 3.1-3.2): ETD_SCHEME_ETD1,
  *               ETD_SCHEME_ETD2 (also selected by 0), ETD_SCHEME_ETD2RK,
- *               ETD_SCHEME_ETD3RK or ETD_SCHEME_ETD4RK (the last two need
+ *               ETD_SCHEME_ETD3RK, ETD_SCHEME_ETD4RK (these two need
  *               m_max <= 60, reserve three more full-grid FP64 fields per
  *               species, and step the reaction term only: no source, no
- *               boundary data)
+ *               boundary data) or ETD_SCHEME_ETD3 (multistep, third order;
+ *               m_max <= 60, one more full-grid FP64 field per species)
  *   boundary_data  1 to reserve the workspace of nonzero Dirichlet data
  *               (etd_boundary_points / etd_set_boundary_values) */
 typedef struct {
@@ -150,7 +158,12 @@ etd_status etd_init_domain(etd_ctx* ctx, int species, const double* phi, const d
  *   ETD3RK, ETD4RK (Sec. 3.2)  the stages a_n, b_n (and c_n) with dt / 2 or
  *                      dt, then U_{n+1} by one combination up to phi_3: three
  *                      and four Krylov evaluations.  The paper's phi_3 is that
- *                      of Eq. 3.7, twice the standard phi_3.
+ *                      of Eq. 3.7, twice the standard phi_3;
+ *   ETD3 (Eq. 3.8b, s = 3)  U_{n+1} = phi_0 U_n + dt phi_1 F_n
+ *                      + dt phi_2 (3/2 F_n - 2 F_{n-1} + 1/2 F_{n-2})
+ *                      + dt phi_3 (F_n - 2 F_{n-1} + F_{n-2}) (standard phi_k);
+ *                      where a point lacks F_{n-2} the step is ETD2 there,
+ *                      and where it also lacks F_{n-1}, ETD1.
  * Each phi-combination (Eq. 3.9) is evaluated by adaptive Krylov
  * time-stepping of the ODE of Eq. 3.10.  u[s] (device, full grid, in/out):
  * read at the computational points of species s; on return it holds U_{n+1}

@@ -16,6 +16,7 @@ struct SpeciesBufs {
   double* diag = nullptr;
   float* diagf = nullptr;
   double* Fprev = nullptr;
+  double* Fprev2 = nullptr;  // multistep ETD3
   uint8_t* fvalid = nullptr;
   void* V = nullptr;
   void* Yg = nullptr;
@@ -143,12 +144,13 @@ bool check_params(const etd_params* p, std::string& why) {
     why = "krylov_tol must be positive";
     return false;
   }
-  if (p->scheme < 0 || p->scheme > ETD_SCHEME_ETD4RK) {
+  if (p->scheme < 0 || p->scheme > ETD_SCHEME_ETD3) {
     why = "unknown scheme";
     return false;
   }
-  if ((p->scheme == ETD_SCHEME_ETD3RK || p->scheme == ETD_SCHEME_ETD4RK) && p->m_max > MAX_M - 1) {
-    why = "ETD3RK and ETD4RK need m_max <= 60";
+  if ((p->scheme == ETD_SCHEME_ETD3RK || p->scheme == ETD_SCHEME_ETD4RK || p->scheme == ETD_SCHEME_ETD3) &&
+      p->m_max > MAX_M - 1) {
+    why = "ETD3RK, ETD4RK and ETD3 need m_max <= 60";
     return false;
   }
   if (p->reaction < 0 || p->reaction > 3 || (p->reaction == ETD_REACTION_COMPETITION && p->nspecies != 2)) {
@@ -189,6 +191,7 @@ size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
     b.diag = cv.take<double>(G);
     b.diagf = f32 ? cv.take<float>(G) : nullptr;
     b.Fprev = cv.take<double>(G);
+    b.Fprev2 = p.scheme == ETD_SCHEME_ETD3 ? cv.take<double>(G) : nullptr;
     b.fvalid = cv.take<uint8_t>(G);
     b.V = cv.take<char>(s * G * (p.m_max + 1));
     b.Yg = cv.take<char>(s * G);
@@ -300,6 +303,7 @@ SpeciesDev<T> species_dev(etd_ctx* c, int s, double* u, int stage = 0) {
   d.gersh = &c->st->gersh[s];
   d.u = u;
   d.Fprev = b.Fprev;
+  d.Fprev2 = b.Fprev2;
   d.fvalid = b.fvalid;
   d.V = (T*)b.V;
   d.Yg = (T*)b.Yg;
@@ -332,7 +336,8 @@ etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int spec
   a.reaction = c->par.reaction;
   for (int i = 0; i < 4; ++i) a.rp[i] = c->par.rp[i];
   a.etd1 = etd1 ? 1 : 0;
-  a.p = p;
+  a.ms3 = mode == MODE_ETD2 && c->par.scheme == ETD_SCHEME_ETD3 ? 1 : 0;
+  a.p = a.ms3 ? 3 : p;
   if (stage) a.stage = *stage;
   const bool all = mode == MODE_ETD2 || mode == MODE_RK2 || mode == MODE_STAGE;
   if (all) {

@@ -65,8 +65,10 @@ struct SpeciesDev {
   const double* gersh;
   // caller's field (full grid, FP64); other species' field for coupling
   double* u;
-  // F_{n-1} on the grid and its validity flags
+  // F_{n-1} (and, for multistep ETD3, F_{n-2}) on the grid, and their
+  // validity bits (bit 0: F_{n-1}, bit 1: F_{n-2})
   double* Fprev;
+  double* Fprev2;
   uint8_t* fvalid;
   // full-grid stencil inputs (zero off the computational set)
   T* V;   // m_max + 1 slots, slot stride = grid size
@@ -131,6 +133,7 @@ struct PhipmArgs {
   const double* given[4];  // MODE_GIVEN: v0 .. v_p on the grid (species 0)
   int etd1;                // MODE_ETD2: v2 = 0 (the ETD1 step)
   int p;                   // highest phi index of the combination: 2 or 3
+  int ms3;                 // MODE_ETD2: multistep ETD3 (Eq. 3.8b, s = 3; p = 3)
   StageDesc stage;         // MODE_STAGE
   double* part;
   DevStatus* st;

@@ -1198,17 +1198,24 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
             const double F =
                 (s == 0 ? reaction(a.reaction, a.rp, 0, u, other) : reaction(a.reaction, a.rp, 1, other, u)) +
                 extra_F<T, N>(S, kk[q], p);
-            const double Fp = S.fvalid[p] ? S.Fprev[p] : F;
+            const unsigned fv = S.fvalid[p];
+            const double Fp = (fv & 1u) ? S.Fprev[p] : F;
+            // multistep ETD3 with both earlier values: F_{n-2}
+            const bool three = a.ms3 && (fv & 2u);
+            const double Fpp = three ? S.Fprev2[p] : Fp;
             if (a.mode == MODE_ETD2) {
-              // F_{n-1} <- F_n in place: only this thread reads this
-              // species' F_{n-1} at p (the other species reads u)
+              // F_{n-2} <- F_{n-1} <- F_n in place: only this thread reads
+              // this species' history at p (the other species reads u)
+              if (a.ms3 && (fv & 1u)) S.Fprev2[p] = Fp;
               S.Fprev[p] = F;
-              S.fvalid[p] = 1;
+              S.fvalid[p] = a.ms3 ? (uint8_t)(1u | ((fv & 1u) << 1)) : (uint8_t)1;
             }
             const bool rk2 = a.mode == MODE_RK2;
             y[q] = rk2 ? 0.0 : u;
             v1[q] = rk2 ? 0.0 : a.dt * F;
-            v2[q] = a.etd1 ? 0.0 : a.dt * (F - Fp);
+            // ETD3 from two earlier values, else ETD2 from one (ETD1: none)
+            v2[q] = a.etd1 ? 0.0 : three ? a.dt * (1.5 * F - 2.0 * Fp + 0.5 * Fpp) : a.dt * (F - Fp);
+            if (three) v3[q] = a.dt * (F - 2.0 * Fp + Fpp);
           }
         }
 #pragma unroll
@@ -1277,7 +1284,8 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
     });
     if (outf != 0) continue;  // stage fields are read at computational points only
     // 16 nodes per thread and iteration: one 16-byte load of kinds, the
-    // validity flags rewritten from them, unconditional zero stores for u.
+    // validity bits cleared off the computational set, unconditional zero
+    // stores for u.
     const long long n16 = g.size >> 4;
     const uint4* kind16 = reinterpret_cast<const uint4*>(S.kind);
     uint4* valid16 = reinterpret_cast<uint4*>(S.fvalid);
@@ -1297,12 +1305,17 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
             else S.u[base + 4 * q + b] = 0.0;
           }
         }
-        if (a.mode == MODE_ETD2) valid16[c] = make_uint4(fv[0], fv[1], fv[2], fv[3]);
+        // the set-up wrote the bits of the computational points; 0 elsewhere
+        if (a.mode == MODE_ETD2) {
+          const uint4 old = valid16[c];
+          valid16[c] = make_uint4(old.x & (fv[0] * 0xffu), old.y & (fv[1] * 0xffu), old.z & (fv[2] * 0xffu),
+                                  old.w & (fv[3] * 0xffu));
+        }
       } else {
         for (long long p = base; p < g.size; ++p) {
           const bool comp = (__ldg(S.kind + p) & 3) == K_COMP;
           if (!comp) S.u[p] = 0.0;
-          if (a.mode == MODE_ETD2) S.fvalid[p] = comp ? 1 : 0;
+          if (a.mode == MODE_ETD2 && !comp) S.fvalid[p] = 0;
         }
       }
     }

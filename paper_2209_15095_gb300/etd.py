@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
                 ("mu", ctypes.c_double * 2), ("beta", ctypes.c_double * 2), ("adjoint", ctypes.c_int),
                 ("scheme", ctypes.c_int), ("boundary_data", ctypes.c_int)]
 
-SCHEMES = {"etd1": 1, "etd2": 2, "etd2rk": 3, "etd3rk": 4, "etd4rk": 5}
+SCHEMES = {"etd1": 1, "etd2": 2, "etd2rk": 3, "etd3rk": 4, "etd4rk": 5, "etd3": 6}
 
 
 class StepStats(ctypes.Structure):

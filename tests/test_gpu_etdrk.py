@@ -257,3 +257,67 @@ def test_rk34_argument_checks(lib):
     ctx.set_source(0, torch.ones_like(z))
     with pytest.raises(lib.EtdError):
         ctx.step(0.01, [torch.zeros_like(z)])
+
+
+def _oracle_etd3(op, uo, hist, F_n, dt):
+    """One step of the oracle's multistep ETD3 with the start-up reading."""
+    hist.insert(0, F_n)
+    del hist[3:]
+    if len(hist) == 3:
+        return oetd.etd3_step(op, uo, hist[0], hist[1], hist[2], dt, tol=1e-12, m_max=40)[0]
+    return oetd.etd2_step(op, uo, hist[0], hist[-1], dt, tol=1e-12, m_max=40)[0]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_etd3_multistep_steps(lib, precision, tol):
+    """Four multistep ETD3 steps (Eq. 3.8b, s = 3) through etd_step: ETD1, ETD2,
+    then ETD3 from the stored F_{n-1}, F_{n-2}, against the oracle."""
+    g, ph = _ellipsoid(3, 26, 2.0)
+    op = EBOperator(g, ph, 1.0)
+    ctx = _ctx(lib, g, precision=precision, tol=1e-10 if precision == "fp64" else 1e-6, scheme="etd3")
+    ctx.init_domain(0, _dev(ph))
+    rng = np.random.default_rng(12)
+    u0 = op.to_grid(rng.uniform(0, 1, op.ncomp))
+    du = _dev(u0)
+    dt = 0.02
+    uo, hist = op.from_grid(u0), []
+    for _ in range(4):
+        ctx.step(dt, [du])
+        uo = _oracle_etd3(op, uo, hist, uo * (1 - uo), dt)
+        ug = du.cpu().numpy()
+        assert np.max(np.abs(op.from_grid(ug) - uo)) <= tol * np.max(np.abs(uo)) * 10
+        assert np.all(ug[~op.comp] == 0.0)
+
+
+def test_etd3_multistep_with_boundary_data(lib):
+    """ETD3 on the peanut problem of Table 1 (Sec. 4.2.1): a source and nonzero
+    Dirichlet data enter F and the stored history; three steps against the
+    oracle with the same readings."""
+    n = 61
+    g = Grid((n, n), (-1.0, -1.0), (1.0, 1.0))
+    x, y = g.coords()
+    rho = 0.5 - np.exp(-20 * (x ** 2 + (y - 0.25) ** 2)) - np.exp(-20 * (x ** 2 + (y + 0.25) ** 2))
+    beta = 0.25 - x ** 2 - y ** 2
+    r2 = x ** 2 + y ** 2
+    op = EBOperator(g, rho, beta, boundary_data=True)
+    ctx = lib.Context(g.n, g.lo, g.hi, precision="fp64", tol=1e-12, m_max=40, reaction="none", mu=(0.0,),
+                      beta=(1.0,), boundary_data=True, scheme="etd3")
+    ctx.init_domain(0, _dev(rho), _dev(beta))
+    P = ctx.boundary_points(0).cpu().numpy()
+    u_gamma = lambda Q, t: np.exp(-t) * (np.sum(Q ** 2, axis=-1) - 0.25)
+    source = lambda rr, t: math.exp(-t) * (28 * rr - 3) / 4
+    rc = op.from_grid(r2)
+    du = _dev(op.to_grid(rc - 0.25))
+    uo, hist, t, dt = rc - 0.25, [], 0.0, g.h
+    keep = []
+    for _ in range(3):
+        vals, src = _dev(u_gamma(P, t)), _dev(source(r2, t))
+        keep.append((vals, src))  # the library reads them during the step
+        ctx.set_boundary_values(0, vals)
+        ctx.set_source(0, src)
+        ctx.step(dt, [du])
+        F_n = source(rc, t) + op.boundary_rhs(lambda Q: u_gamma(Q, t))
+        uo = _oracle_etd3(op, uo, hist, F_n, dt)
+        t += dt
+        ug = op.from_grid(du.cpu().numpy())
+        assert np.max(np.abs(ug - uo)) <= 1e-10 * np.max(np.abs(uo))
