@@ -194,25 +194,27 @@ __device__ void finish_check(Ctl& c, int m, int p, double tau) {
 }
 
 // ---------------------------------------------------------------------------
-template <typename T, int N>
+// (A x)_p with A = cfac (beta S - D) (SCALED), or (B x)_p = (A x)_p / cfac.
+template <typename T, int N, bool SCALED = true>
 __device__ __forceinline__ T stencil(const T* __restrict__ x, long long p, const GridDev& g, T Dk,
                                      const double* __restrict__ bfield, T bc, T cfac) {
   const T xp = __ldcg(x + p);
+  // the sums start from -0: x + (-0) == x exactly, so the first add is free
   if (bfield == nullptr) {
-    T s = T(0);
+    T s = T(-0.0);
 #pragma unroll
     for (int d = 0; d < N; ++d) s += __ldcg(x + p - g.stride[d]) + __ldcg(x + p + g.stride[d]);
-    return cfac * (bc * s - Dk * xp);
+    return SCALED ? cfac * (bc * s - Dk * xp) : bc * s - Dk * xp;
   }
   const double bp = __ldg(bfield + p);
-  T s = T(0);
+  T s = T(-0.0);
 #pragma unroll
   for (int d = 0; d < N; ++d) {
     const long long st = g.stride[d];
     s += T(0.5 * (bp + __ldg(bfield + p - st))) * __ldcg(x + p - st);
     s += T(0.5 * (bp + __ldg(bfield + p + st))) * __ldcg(x + p + st);
   }
-  return cfac * (s - Dk * xp);
+  return SCALED ? cfac * (s - Dk * xp) : s - Dk * xp;
 }
 
 __device__ __forceinline__ double reaction(int kind, const double* rp, int species, double u, double v) {
@@ -427,7 +429,7 @@ __device__ __noinline__ QuadSums quad_pass_b(const float* __restrict__ Vj, const
       vc[u] = ld4(Vj + p4);
       vl[u] = __ldcg(Vj + p4 - 1);
       vr[u] = __ldcg(Vj + p4 + 4);
-      float4 sacc = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 sacc = make_float4(-0.f, -0.f, -0.f, -0.f);  // as stencil()
 #pragma unroll
       for (int d = 0; d < N - 1; ++d) {
         const float4 m = ld4(Vj + p4 - st[d]), q = ld4(Vj + p4 + st[d]);
@@ -491,7 +493,7 @@ __device__ __noinline__ QuadSums quad_stencil(const float* __restrict__ X, float
     const int k0 = __ldg(qk + q);
     const float4 vc = ld4(X + p4);
     const float vl = __ldcg(X + p4 - 1), vr = __ldcg(X + p4 + 4);
-    float4 sacc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 sacc = make_float4(-0.f, -0.f, -0.f, -0.f);  // as stencil()
 #pragma unroll
     for (int d = 0; d < N - 1; ++d) {
       const float4 m = ld4(X + p4 - st[d]), pq = ld4(X + p4 + st[d]);
@@ -685,6 +687,10 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   // large problems: split Lanczos pass (see SPLIT_MIN), on aligned groups of
   // 4 nodes where the layout allows
   const bool split = ncomp >= SPLIT_MIN<T>;
+  // FP64 split passes: Z_j = B V_j with B = A / cfac (one FP64 multiply less
+  // per point); the Lanczos scalars take the factor: zfac = cfac
+  const bool zb = sizeof(T) == 8 && split;
+  const double zfac = zb ? a.cfac : 1.0;
   const bool quad = sizeof(T) == 4 && split && S.qidx != nullptr && S.beta_field == nullptr &&
                     (g.n[N - 1] & 3) == 0;
   if (quad && !build_quads<T>(a, S, ncomp, c, bar, red)) return false;
@@ -815,7 +821,8 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         for (int u = 0; u < U; ++u) {
           if (pp[u] < 0) continue;
           vv[u] = __ldcg(S.V + pp[u]);
-          zz[u] = stencil<T, N>(S.V, pp[u], g, diag_of<T>(S, (int)kk[u]), S.beta_field, bc, cfac);
+          zz[u] = zb ? stencil<T, N, false>(S.V, pp[u], g, diag_of<T>(S, (int)kk[u]), S.beta_field, bc, cfac)
+                     : stencil<T, N>(S.V, pp[u], g, diag_of<T>(S, (int)kk[u]), S.beta_field, bc, cfac);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -841,7 +848,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         }
         const double s0 = c.beta > 0.0 ? 1.0 / c.beta : 0.0;
         c.scale[0] = s0;
-        c.alpha[0] = tot[1] * s0 * s0;
+        c.alpha[0] = zfac * tot[1] * s0 * s0;
         c.up[0] = 0.0;
         c.m = 0;
         c.accepted = 0;
@@ -861,7 +868,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
       // the same classical Gram-Schmidt coefficients as z = A v_j,
       // <z, v_j>, <z, v_{j-1}>, with the normalisation deferred.
       for (int j = 1; j <= m_max; ++j) {
-        const T ca = (T)c.scale[j - 1];                       // coefficient of Z_{j-1}
+        const T ca = (T)(c.scale[j - 1] * zfac);              // coefficient of Z_{j-1}
         const T cb = (T)(-c.alpha[j - 1] * c.scale[j - 1]);    // of V_{j-1}
         const T cc = j >= 2 ? (T)(-c.up[j - 1] * c.scale[j - 2]) : T(0);  // of V_{j-2}
         const T* Zp = S.Z[(j - 1) & 1];
@@ -908,7 +915,8 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
 #pragma unroll
             for (int u = 0; u < UB; ++u) {
               if (pp[u] < 0) continue;
-              zv[u] = stencil<T, N>(Vj, pp[u], g, diag_of<T>(S, (int)kk[u]), S.beta_field, bc, cfac);
+              zv[u] = zb ? stencil<T, N, false>(Vj, pp[u], g, diag_of<T>(S, (int)kk[u]), S.beta_field, bc, cfac)
+                         : stencil<T, N>(Vj, pp[u], g, diag_of<T>(S, (int)kk[u]), S.beta_field, bc, cfac);
               wv[u] = __ldcg(Vj + pp[u]);
               v1v[u] = __ldcg(V1 + pp[u]);
             }
@@ -930,7 +938,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
             const long long p = __ldg(S.idx + k);
             const T w = wval<T>(Zp, V1, V2, p, ca, cb, cc);
             const T v1 = __ldcg(V1 + p);
-            T s = T(0);
+            T s = T(-0.0);  // as stencil()
             const double* bf = S.beta_field;
             if (bf == nullptr) {
 #pragma unroll
@@ -973,8 +981,8 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
             c.breakdown = hn < BREAKDOWN_REL * anorm;
             const double sj = c.breakdown ? 0.0 : 1.0 / hn;
             c.scale[j] = sj;
-            c.alpha[j] = tot[1] * sj * sj;
-            c.up[j] = tot[2] * sj * c.scale[j - 1];
+            c.alpha[j] = zfac * tot[1] * sj * sj;
+            c.up[j] = zfac * tot[2] * sj * c.scale[j - 1];
           }
           __syncthreads();
           if (c.abort) return false;
