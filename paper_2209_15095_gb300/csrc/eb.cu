@@ -209,11 +209,19 @@ __device__ void metadata_phase(const MetaArgs& a, int ncomp) {
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   double gmax = 0.0;
   int nclamp = 0;
+  // interior rows (every face to a computational point) with a constant
+  // beta: D = 2N beta and the Gershgorin row sum 4N beta / h^2, without the
+  // FP64 face sums (FP64 warp instructions are what this phase spends)
+  const bool cbeta = a.beta_field == nullptr;
+  const double D_int = (double)FPR * a.beta_c;
+  const unsigned row_mask = ((1u << FPR) - 1u) << lead;
+  bool seen_interior = false;
   for (long long w = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5); w * RPW < ncomp;
        w += nwarps) {
     const long long k = w * RPW + slot;
     const bool act = slot < RPW && k < ncomp;
     double cD = 0.0, cOff = 0.0;
+    bool face_comp = false;
     if (act) {
       const long long p = __ldcg(a.idx + k);
       int ip[N];
@@ -242,6 +250,7 @@ __device__ void metadata_phase(const MetaArgs& a, int ncomp) {
       if ((__ldcg(a.kind + q) & 3) == K_COMP) {
         cD = bf;
         cOff = bf;
+        face_comp = true;
       } else if (iq <= 0 || iq >= g.n[d] - 1) {
         // ghost on the box boundary: the domain-margin error is already
         // flagged by the classification; keep every access in bounds
@@ -293,18 +302,32 @@ __device__ void metadata_phase(const MetaArgs& a, int ncomp) {
         }
       }
     }
-    double D = 0.0, off = 0.0;
+    const unsigned fc = __ballot_sync(0xffffffffu, act && face_comp);
+    const bool interior = cbeta && (fc & row_mask) == row_mask;
+    // the face sums only where some row of this warp iteration has a ghost face
+    const unsigned need = __ballot_sync(0xffffffffu, act && f == 0 && !interior);
+    double D = D_int, off = D_int;
+    if (need) {
+      double Ds = 0.0, os = 0.0;
 #pragma unroll
-    for (int j = 0; j < FPR; ++j) {
-      D += __shfl_sync(0xffffffffu, cD, lead + j);
-      off += __shfl_sync(0xffffffffu, cOff, lead + j);
+      for (int j = 0; j < FPR; ++j) {
+        Ds += __shfl_sync(0xffffffffu, cD, lead + j);
+        os += __shfl_sync(0xffffffffu, cOff, lead + j);
+      }
+      if (!interior) {
+        D = Ds;
+        off = os;
+      }
     }
     if (act && f == 0) {
       a.diag[k] = D;
       if (a.diagf) a.diagf[k] = (float)D;
-      gmax = fmax(gmax, (D + off) / h2);
+      if (!interior) gmax = fmax(gmax, (D + off) / h2);
+      seen_interior = seen_interior || interior;
     }
   }
+  // the interior rows' Gershgorin sum, once for all of those this thread wrote
+  if (seen_interior) gmax = fmax(gmax, (D_int + D_int) / h2);
   for (int o = 16; o > 0; o >>= 1) {
     gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
     nclamp += __shfl_xor_sync(0xffffffffu, nclamp, o);
