@@ -543,8 +543,10 @@ __device__ __noinline__ QuadSums quad_stencil(const float* __restrict__ X, float
 // The combination y <- y + tau w_1 (+ tau^2/2 w_2) + sum_i coef_i V_i on
 // groups of 4 nodes: per computational point the arithmetic of the per-point
 // loop (the same Dot2 basis sum in the same order, so the same bits), with
-// 16-byte loads of the basis vectors, sixteen in flight (measured at 512^3:
-// 4 in flight 14.14 ms per launch, 8 13.99, 16 13.64).  Writes y (compact,
+// 16-byte loads of the basis vectors, ten in flight: the basis size is a
+// multiple of 5 but for m_max or a breakdown (the error check runs every 5
+// vectors).  Measured per launch at 256^3 / 512^3 (10 / 20 vectors): 5 in
+// flight 1.378 / 14.11 ms, 8 1.376 / 14.01, 10 1.342 / 13.51, 16 1.390 / 13.72.  Writes y (compact,
 // FP64) and its FP32 grid copy (0 at the group's other nodes); returns this
 // thread's sum of y^2.
 __device__ __noinline__ double quad_combination(const float* __restrict__ chi, const float* __restrict__ clo, int m,
@@ -560,7 +562,7 @@ __device__ __noinline__ double quad_combination(const float* __restrict__ chi, c
     const int k0 = __ldg(qk + q);
     const unsigned kw = __ldg(reinterpret_cast<const unsigned*>(kind + p4));
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
-#pragma unroll 16
+#pragma unroll 10
     for (int i = 0; i < m; ++i) {
       const float4 a4 = ld4(V + (long long)i * vs + p4);
       const float ch = chi[i], cl = clo[i];
