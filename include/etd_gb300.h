@@ -76,7 +76,7 @@ enum {
  *               H, the small exponential, the controller, u and F stay FP64.
  *               In the level set, phi, u, the extension, the Stefan speed and
  *               the RK updates stay FP64; the HJ-WENO5/Godunov arithmetic is
- *               FP32 for the advection and, beyond 3h from the interface, for
+ *               FP32 for the advection and, beyond 2h from the interface, for
  *               the reinitialisation.
  *   krylov_tol  relative tolerance of the adaptive Krylov evaluation
  *   m_max       largest Krylov basis, 5 <= m_max <= 61

@@ -359,7 +359,7 @@ def test_two_species_competition_multistep(lib):
 
 def test_levelset_step_mixed_precision(lib):
     """FP32-mixed path: WENO5/Godunov arithmetic in FP32 except the
-    reinitialisation within 3h of the interface; against the FP64 oracle."""
+    reinitialisation within 2h of the interface; against the FP64 oracle."""
     g, ph0 = _shape_phi(3, 28, 3.0, "ellipsoid")
     ph = levelset.reinit(levelset.clamp(ph0, g.h), g.h)
     op = EBOperator(g, ph, 1.0)
