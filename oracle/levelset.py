@@ -14,9 +14,7 @@ Extension of u (Aslam 2004 quadratic extrapolation in the normal direction):
   are valid0, valid2 likewise from valid1.  u_n = n . grad u (central) on
   valid1, u_nn = n . grad u_n on valid2.  Then three pseudo-time sweeps of
   q_tau + n . grad q = s, first-order upwind in the direction of n, forward
-  Euler with step h/(2 sqrt N), ceil(6 sqrt N) steps (pseudo-time >= 3h: the
-  extended values are consumed within about 2h outside the front, by the
-  Stefan speed's interpolation and by the nodes the front crosses in a step):
+  Euler with step h/(2 sqrt N), ceil(12 sqrt N) steps (pseudo-time >= 6h):
   u_nn (s = 0) on T minus valid2, then u_n (s = u_nn) on T minus valid1, then
   u (s = u_n) on T minus valid0.  Unknown values start at 0.
 Stefan speed (closest-point extension): at every node of T,
@@ -44,13 +42,7 @@ GRAD_FLOOR = 1e-12
 
 
 def pseudo_steps(ndim):
-    """Pseudo-steps of the reinitialisation (pseudo-time >= 6h, the band)."""
     return int(math.ceil(12.0 * math.sqrt(ndim)))
-
-
-def extension_steps(ndim):
-    """Pseudo-steps of each extension sweep (pseudo-time >= 3h)."""
-    return int(math.ceil(6.0 * math.sqrt(ndim)))
 
 
 def tube(phi, h):
@@ -136,7 +128,7 @@ def _sweep(q, src, n, h, region):
     ndim = q.ndim
     dtau = h / (2.0 * math.sqrt(ndim))
     q = np.where(region, 0.0, q)
-    for _ in range(extension_steps(ndim)):
+    for _ in range(pseudo_steps(ndim)):
         q = np.where(region, q - dtau * (_n_dot_grad_upwind(q, n, h) - src), q)
     return q
 
