@@ -97,6 +97,7 @@ LevelsetBufs levelset_carve(const GridDev& g, const std::function<char*(size_t)>
   for (int i = 0; i < 6; ++i) b.q[i] = (double*)take(G * sizeof(double));
   b.p1 = (double*)take(G * sizeof(double));
   b.p2 = (double*)take(G * sizeof(double));
+  b.gidx = (int*)take(G * sizeof(int));
   return b;
 }
 
@@ -435,6 +436,306 @@ __device__ __forceinline__ int sweep_level(uint8_t f) {
   return (f & F_V2) ? 0 : 1;
 }
 
+// Extension sweeps of the mixed variant: the same first-order upwind
+// iteration as the FP64 sweeps (three sweeps of K Jacobi passes over the
+// regions of levels >= 1, >= 2, 3; each sweep's result is the next one's
+// source), in FP32 arithmetic on FP32 copies of the fields, two passes per
+// grid barrier.  One pass at a region entry p is
+//   q'(p) = c0 q(p) + sum_d a_d q(u_d) + ds,   a_d = dtau |n_d| / h, c0 = 1 - sum_d a_d,
+// with u_d the upwind neighbour along d and ds = dtau s(p); nodes off the
+// region keep their values.  Two passes in one update from the values before
+// both:
+//   q''(p) = c0 q'(p) + sum_d a_d q'(u_d) + ds
+//          = D + c0^2 q(p) + sum_d a_d (c0 + c0(u_d)) q(u_d) + sum_de a_d a_e(u_d) q(u_de),
+//   D = (1 + c0) ds + sum_d a_d ds(u_d),
+// where a neighbour u_d off the region contributes a_d (c0 + 1) q(u_d) and
+// nothing else.  A node met twice (u_de = u_ed; u_dd = p where the upwind
+// direction turns) keeps one term with the summed weight.  Each region entry
+// has a thread of its own when the region is at most one entry per thread;
+// larger regions take one pass per barrier.  The fields arrive in FP64 and the
+// extended u leaves in FP64.
+template <int N>
+__device__ bool ext_sweeps_f32(const LsArgs& a, LsCtx& c, int n, long long cap, int K, double dtau, double dth,
+                               const double* const* Q0) {
+  constexpr int NTM = 1 + N + N * N;  // terms of a two-pass update
+  const GridDev& g = a.g;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gth = (long long)gridDim.x * blockDim.x;
+  const long long jt = dealt_tid();
+  const int* const swl = a.b.slist;
+  const int sc1 = __ldcg(a.b.sw + 1), sc2 = __ldcg(a.b.sw + 2), sc3 = __ldcg(a.b.sw + 3);
+  const long long len0 = (long long)sc1 + sc2 + sc3;
+  const float dtf = (float)dtau, dthf = (float)dth;
+  // FP32 ping-pong fields of the three sweeps in the FP64 ping-pong partners,
+  // which this path leaves unused (each holds two FP32 fields)
+  float* const F[6] = {reinterpret_cast<float*>(a.b.q[1]), reinterpret_cast<float*>(a.b.q[1]) + cap,
+                       reinterpret_cast<float*>(a.b.q[3]), reinterpret_cast<float*>(a.b.q[3]) + cap,
+                       reinterpret_cast<float*>(a.b.q[5]), reinterpret_cast<float*>(a.b.q[5]) + cap};
+  for (long long i = gtid; i < n; i += gth) {
+    const long long p = __ldcg(a.b.list + i);
+#pragma unroll
+    for (int sw = 0; sw < 3; ++sw) {
+      const float v = (float)__ldcg(Q0[sw] + p);
+      F[2 * sw][p] = v;
+      F[2 * sw + 1][p] = v;
+    }
+  }
+  // The thread's region entry is the same node in every sweep (the regions
+  // are prefixes of one sweep list): its upwind nodes and coefficients, and
+  // those of its upwind neighbours with their sweep levels, once.
+  int p = 0, up[N], lev[N], tu[N][N];
+  float c0 = 0.f, ad[N], c0u[N], au[N][N];
+  if (jt < len0) {
+    const long long i = __ldcg(swl + jt);
+    p = __ldcg(a.b.list + i);
+    int ix[N];
+    unpack<N>(__ldcg(a.b.lcoord + i), ix);
+    float asum = 0.f;
+#pragma unroll
+    for (int d = 0; d < N; ++d) {
+      const double nd = __ldcg(a.b.nrm + d * cap + i);
+      up[d] = (int)nbr(g, p, ix, d, nd > 0.0 ? -1 : 1);
+      ad[d] = dthf * fabsf((float)nd);
+      asum += ad[d];
+    }
+    c0 = 1.f - asum;
+    int gi[N];
+#pragma unroll
+    for (int d = 0; d < N; ++d) gi[d] = __ldcg(a.b.gidx + up[d]);
+#pragma unroll
+    for (int d = 0; d < N; ++d) {
+      const bool ok = gi[d] >= 0 && gi[d] < n;
+      const int lp = ok ? __ldcg(a.b.list + gi[d]) : -1;
+      const uint8_t f = ok ? __ldcg(a.b.lflag + gi[d]) : (uint8_t)0;
+      int ixu[N];
+      unpack<N>(ok ? __ldcg(a.b.lcoord + gi[d]) : make_ushort4(0, 0, 0, 0), ixu);
+      lev[d] = ok && lp == up[d] ? sweep_level(f) : 0;
+      float as = 0.f;
+#pragma unroll
+      for (int e = 0; e < N; ++e) {
+        const float ne = ok ? (float)__ldcg(a.b.nrm + e * cap + gi[d]) : 0.f;
+        au[d][e] = dthf * fabsf(ne);
+        tu[d][e] = (int)nbr(g, up[d], ixu, e, ne > 0.f ? -1 : 1);
+        as += au[d][e];
+      }
+      c0u[d] = 1.f - as;
+    }
+  }
+  if (!grid_barrier(a.st, c.bar, 53)) return false;
+  int si = -1;  // field holding the source (the previous sweep's result)
+  for (int sw = 0; sw < 3; ++sw) {
+    const long long len = sw == 0 ? len0 : (sw == 1 ? sc2 + sc3 : sc3);
+    const bool two = K >= 2 && len <= gth;
+    float* const X[2] = {F[2 * sw], F[2 * sw + 1]};
+    const float* const src = si < 0 ? nullptr : F[si];
+    const bool has = two && jt < len;
+    // this sweep's update: membership of the neighbours, source terms (no
+    // barrier: nothing written here is read by another thread)
+    int ti[NTM];
+    float ds = 0.f, cq = 0.f, D = 0.f, tw[NTM];
+    unsigned live = 0u;
+    if (has) {
+      float sd[N];
+#pragma unroll
+      for (int d = 0; d < N; ++d) sd[d] = src ? __ldcg(src + up[d]) : 0.f;
+      ds = src ? dtf * __ldcg(src + p) : 0.f;
+      cq = __ldcg(X[0] + p);
+      ti[0] = p;
+      tw[0] = c0 * c0;
+      live = 1u;
+      D = fmaf(c0, ds, ds);
+#pragma unroll
+      for (int d = 0; d < N; ++d) {
+        const bool in = lev[d] > sw;
+#pragma unroll
+        for (int e = 0; e < N; ++e) {
+          ti[1 + N + d * N + e] = tu[d][e];
+          tw[1 + N + d * N + e] = ad[d] * au[d][e];
+        }
+        if (in) {
+          D = fmaf(ad[d], dtf * sd[d], D);
+          live |= ((1u << N) - 1u) << (1 + N + d * N);
+        }
+        ti[1 + d] = up[d];
+        tw[1 + d] = ad[d] * (c0 + (in ? c0u[d] : 1.f));
+        live |= 1u << (1 + d);
+      }
+#pragma unroll
+      for (int k = 1; k < NTM; ++k) {
+        bool done = !((live >> k) & 1u);
+#pragma unroll
+        for (int k2 = 0; k2 < k; ++k2) {
+          if (!done && ((live >> k2) & 1u) && ti[k2] == ti[k]) {
+            tw[k2] += tw[k];
+            live &= ~(1u << k);
+            done = true;
+          }
+        }
+      }
+    }
+    int cur = 0, it = 0;
+    if (two) {
+      for (; it + 2 <= K; it += 2) {
+        if (has) {
+          const float* const qc = X[cur];
+          float qv[NTM];
+#pragma unroll
+          for (int k = 0; k < NTM; ++k) qv[k] = ((live >> k) & 1u) ? __ldcg(qc + ti[k]) : 0.f;
+          float t = D;
+#pragma unroll
+          for (int k = 0; k < NTM; ++k) t = fmaf(tw[k], qv[k], t);
+          cq = t;
+          X[cur ^ 1][p] = t;
+        }
+        if (!grid_barrier(a.st, c.bar, 56)) return false;
+        cur ^= 1;
+      }
+    }
+    for (; it < K; ++it) {
+      const float* const qc = X[cur];
+      float* const qn = X[cur ^ 1];
+      if (has) {
+        float t = fmaf(c0, cq, ds);
+#pragma unroll
+        for (int d = 0; d < N; ++d) t = fmaf(ad[d], __ldcg(qc + up[d]), t);
+        cq = t;
+        qn[p] = t;
+      } else if (!two) {
+        for (long long j = jt; j < len; j += gth) {
+          const long long i = __ldcg(swl + j);
+          const long long q = __ldcg(a.b.list + i);
+          int ix[N];
+          unpack<N>(__ldcg(a.b.lcoord + i), ix);
+          float asum = 0.f, qu[N], aw[N];
+#pragma unroll
+          for (int d = 0; d < N; ++d) {
+            const double nd = __ldcg(a.b.nrm + d * cap + i);
+            qu[d] = __ldcg(qc + nbr(g, q, ix, d, nd > 0.0 ? -1 : 1));
+            aw[d] = dthf * fabsf((float)nd);
+            asum += aw[d];
+          }
+          float t = fmaf(1.f - asum, __ldcg(qc + q), src ? dtf * __ldcg(src + q) : 0.f);
+#pragma unroll
+          for (int d = 0; d < N; ++d) t = fmaf(aw[d], qu[d], t);
+          qn[q] = t;
+        }
+      }
+      if (!grid_barrier(a.st, c.bar, 57)) return false;
+      cur ^= 1;
+    }
+    si = 2 * sw + cur;
+  }
+  // the swept region of u (level 3) from FP32; the rest of the work list as
+  // the FP64 sweeps leave it (its initial values)
+  for (long long i = gtid; i < n; i += gth) {
+    const long long p = __ldcg(a.b.list + i);
+    a.u[p] = sweep_level(__ldcg(a.b.lflag + i)) == 3 ? (double)__ldcg(F[si] + p) : __ldcg(Q0[2] + p);
+  }
+  return true;
+}
+
+// Extension sweeps in FP64 (the plain and the reference arithmetic): three
+// sweeps of K Jacobi passes, one pass per grid barrier (see the caller for
+// the update).  The extended u goes to the caller's array on the work list.
+template <int N>
+__device__ bool ext_sweeps_f64(const LsArgs& a, LsCtx& c, int n, long long cap, int K, double dtau, double dth,
+                               double* const* UNN, double* const* UN, double* const* U) {
+  const GridDev& g = a.g;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gth = (long long)gridDim.x * blockDim.x;
+  double* const* bufs[3] = {UNN, UN, U};
+  const double* src = nullptr;
+  constexpr int SW_CACHE = 2;
+  const int* const swl = a.b.slist;
+  const int sc1 = __ldcg(a.b.sw + 1), sc2 = __ldcg(a.b.sw + 2), sc3 = __ldcg(a.b.sw + 3);
+  const long long jt = dealt_tid();
+  for (int sw = 0; sw < 3; ++sw) {
+    double* const* B = bufs[sw];
+    const long long len = sw == 0 ? sc1 + sc2 + sc3 : (sw == 1 ? sc2 + sc3 : sc3);
+    for (long long i = gtid; i < n; i += gth) {
+      const long long p = __ldcg(a.b.list + i);
+      B[1][p] = __ldcg(B[0] + p);
+    }
+    int cp[SW_CACHE], cup[SW_CACHE][N];
+    bool creg[SW_CACHE];
+    double cq[SW_CACHE], cds[SW_CACHE], cc0[SW_CACHE], ca[SW_CACHE][N];
+#pragma unroll
+    for (int r = 0; r < SW_CACHE; ++r) {
+      const long long j = jt + r * gth;
+      creg[r] = j < len;
+      cp[r] = 0;
+      cq[r] = cds[r] = cc0[r] = 0.0;
+#pragma unroll
+      for (int d = 0; d < N; ++d) {
+        cup[r][d] = 0;
+        ca[r][d] = 0.0;
+      }
+      if (creg[r]) {
+        const long long i = __ldcg(swl + j);
+        const long long p = __ldcg(a.b.list + i);
+        cp[r] = (int)p;
+        cq[r] = __ldcg(B[0] + p);
+        cds[r] = src ? dtau * __ldcg(src + p) : 0.0;
+        int ix[N];
+        unpack<N>(a.b.lcoord[i], ix);
+        double asum = 0.0;
+#pragma unroll
+        for (int d = 0; d < N; ++d) {
+          const double nd = __ldcg(a.b.nrm + d * cap + i);
+          cup[r][d] = (int)nbr(g, p, ix, d, nd > 0.0 ? -1 : 1);
+          ca[r][d] = dth * fabs(nd);
+          asum += ca[r][d];
+        }
+        cc0[r] = 1.0 - asum;
+      }
+    }
+    if (!grid_barrier(a.st, c.bar, 53)) return false;
+    int cur = 0;
+    for (int it = 0; it < K; ++it) {
+      const double* qc = B[cur];
+      double* qn = B[cur ^ 1];
+#pragma unroll
+      for (int r = 0; r < SW_CACHE; ++r) {
+        if (!creg[r]) continue;
+        double qu[N];
+#pragma unroll
+        for (int d = 0; d < N; ++d) qu[d] = __ldcg(qc + cup[r][d]);
+        double t = fma(cc0[r], cq[r], cds[r]);
+#pragma unroll
+        for (int d = 0; d < N; ++d) t = fma(ca[r][d], qu[d], t);
+        cq[r] = t;
+        qn[cp[r]] = t;
+      }
+      for (long long j = jt + SW_CACHE * gth; j < len; j += gth) {
+        const long long i = __ldcg(swl + j);
+        const long long p = __ldcg(a.b.list + i);
+        int ix[N];
+        unpack<N>(a.b.lcoord[i], ix);
+        double asum = 0.0, qu[N], ad[N];
+#pragma unroll
+        for (int d = 0; d < N; ++d) {
+          const double nd = __ldcg(a.b.nrm + d * cap + i);
+          qu[d] = __ldcg(qc + nbr(g, p, ix, d, nd > 0.0 ? -1 : 1));
+          ad[d] = dth * fabs(nd);
+          asum += ad[d];
+        }
+        const double ds = src ? dtau * __ldcg(src + p) : 0.0;
+        double t = fma(1.0 - asum, __ldcg(qc + p), ds);
+#pragma unroll
+        for (int d = 0; d < N; ++d) t = fma(ad[d], qu[d], t);
+        qn[p] = t;
+      }
+      if (!grid_barrier(a.st, c.bar, 53)) return false;
+      cur ^= 1;
+    }
+    src = B[cur];
+  }
+  // extended u back to the caller's array on the work list
+  for (long long i = gtid; i < n; i += gth) {
+    const long long p = __ldcg(a.b.list + i);
+    a.u[p] = __ldcg(src + p);
+  }
+  return true;
+}
+
 // TVD-RK3 on the nodes of T (list order); L(src, p) supplied by the caller.
 // Stage values p1/p2 hold phi off T (copied when the work set is built).
 // The stage list holds the work-list positions of the update set T: entries
@@ -601,6 +902,7 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
     lc1 += lev == 1;
     lc2 += lev == 2;
     lc3 += lev == 3;
+    if (a.mixed) a.b.gidx[p] = (int)i;
     U[0][p] = (f & F_V0) ? a.u[p] : 0.0;
     double un = 0.0;
     if ((f & F_V1) && (f & F_T2)) {
@@ -679,97 +981,11 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
   const int K = (int)ceil(12.0 * sqrt((double)N));
   const double dtau = h / (2.0 * sqrt((double)N));
   const double dth = dtau * inv_h;
-  double* const* bufs[3] = {UNN, UN, U};
-  const double* src = nullptr;
-  constexpr int SW_CACHE = 2;
-  const int* const swl = a.b.slist;
-  const int sc1 = __ldcg(a.b.sw + 1), sc2 = __ldcg(a.b.sw + 2), sc3 = __ldcg(a.b.sw + 3);
-  const long long jt = dealt_tid();
-  for (int sw = 0; sw < 3; ++sw) {
-    double* const* B = bufs[sw];
-    const long long len = sw == 0 ? sc1 + sc2 + sc3 : (sw == 1 ? sc2 + sc3 : sc3);
-    for (long long i = gtid; i < n; i += gth) {
-      const long long p = __ldcg(a.b.list + i);
-      B[1][p] = __ldcg(B[0] + p);
-    }
-    int cp[SW_CACHE], cup[SW_CACHE][N];
-    bool creg[SW_CACHE];
-    double cq[SW_CACHE], cds[SW_CACHE], cc0[SW_CACHE], ca[SW_CACHE][N];
-#pragma unroll
-    for (int r = 0; r < SW_CACHE; ++r) {
-      const long long j = jt + r * gth;
-      creg[r] = j < len;
-      cp[r] = 0;
-      cq[r] = cds[r] = cc0[r] = 0.0;
-#pragma unroll
-      for (int d = 0; d < N; ++d) {
-        cup[r][d] = 0;
-        ca[r][d] = 0.0;
-      }
-      if (creg[r]) {
-        const long long i = __ldcg(swl + j);
-        const long long p = __ldcg(a.b.list + i);
-        cp[r] = (int)p;
-        cq[r] = __ldcg(B[0] + p);
-        cds[r] = src ? dtau * __ldcg(src + p) : 0.0;
-        int ix[N];
-        unpack<N>(a.b.lcoord[i], ix);
-        double asum = 0.0;
-#pragma unroll
-        for (int d = 0; d < N; ++d) {
-          const double nd = __ldcg(a.b.nrm + d * cap + i);
-          cup[r][d] = (int)nbr(g, p, ix, d, nd > 0.0 ? -1 : 1);
-          ca[r][d] = dth * fabs(nd);
-          asum += ca[r][d];
-        }
-        cc0[r] = 1.0 - asum;
-      }
-    }
-    if (!grid_barrier(a.st, c.bar, 53)) return;
-    int cur = 0;
-    for (int it = 0; it < K; ++it) {
-      const double* qc = B[cur];
-      double* qn = B[cur ^ 1];
-#pragma unroll
-      for (int r = 0; r < SW_CACHE; ++r) {
-        if (!creg[r]) continue;
-        double qu[N];
-#pragma unroll
-        for (int d = 0; d < N; ++d) qu[d] = __ldcg(qc + cup[r][d]);
-        double t = fma(cc0[r], cq[r], cds[r]);
-#pragma unroll
-        for (int d = 0; d < N; ++d) t = fma(ca[r][d], qu[d], t);
-        cq[r] = t;
-        qn[cp[r]] = t;
-      }
-      for (long long j = jt + SW_CACHE * gth; j < len; j += gth) {
-        const long long i = __ldcg(swl + j);
-        const long long p = __ldcg(a.b.list + i);
-        int ix[N];
-        unpack<N>(a.b.lcoord[i], ix);
-        double asum = 0.0, qu[N], ad[N];
-#pragma unroll
-        for (int d = 0; d < N; ++d) {
-          const double nd = __ldcg(a.b.nrm + d * cap + i);
-          qu[d] = __ldcg(qc + nbr(g, p, ix, d, nd > 0.0 ? -1 : 1));
-          ad[d] = dth * fabs(nd);
-          asum += ad[d];
-        }
-        const double ds = src ? dtau * __ldcg(src + p) : 0.0;
-        double t = fma(1.0 - asum, __ldcg(qc + p), ds);
-#pragma unroll
-        for (int d = 0; d < N; ++d) t = fma(ad[d], qu[d], t);
-        qn[p] = t;
-      }
-      if (!grid_barrier(a.st, c.bar, 53)) return;
-      cur ^= 1;
-    }
-    src = B[cur];
-  }
-  // extended u back to the caller's array on the work list
-  for (long long i = gtid; i < n; i += gth) {
-    const long long p = __ldcg(a.b.list + i);
-    a.u[p] = __ldcg(src + p);
+  if (a.mixed) {
+    const double* const Q0[3] = {UNN[0], UN[0], U[0]};
+    if (!ext_sweeps_f32<N>(a, c, n, cap, K, dtau, dth, Q0)) return;
+  } else if (!ext_sweeps_f64<N>(a, c, n, cap, K, dtau, dth, UNN, UN, U)) {
+    return;
   }
   if (!grid_barrier(a.st, c.bar, 54)) return;
   // Stefan speed on T

@@ -24,12 +24,14 @@ struct LevelsetBufs {
   double* q[6];     // grid: extension ping-pong buffers (u_nn, u_n, u)
   double* p1;       // grid: RK stage values
   double* p2;
+  int* gidx;        // grid: work-list position of each work-set node (valid where list[gidx[p]] == p)
 };
 
 LevelsetBufs levelset_carve(const GridDev& g, const std::function<char*(size_t)>& take);
 
 // mixed: FP32 WENO/Godunov arithmetic except for the reinitialisation within
-// 2h of the interface (FP64 everywhere when false)
+// 2h of the interface, and FP32 extension sweeps with two passes per grid
+// barrier (FP64 everywhere when false)
 cudaError_t launch_levelset_advance(const GridDev& g, const LevelsetBufs& b, DevStatus* st, const uint8_t* kind,
                                     double* phi, double* u, double dt, double mu, bool reinit, bool mixed,
                                     cudaStream_t stream);

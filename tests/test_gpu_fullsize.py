@@ -172,7 +172,10 @@ def test_fullsize_levelset_step(lib, precision):
         near = np.abs(ph_o) < 2 * g.h
         assert np.max(np.abs(ph_g - ph_o)[near]) <= 1e-6 * g.h
         assert np.max(np.abs(ph_g - ph_o)) <= 1e-4 * g.h
-    assert np.max(np.abs(du.cpu().numpy() - ue_o)) <= 1e-9 * np.max(np.abs(ue_o))
+    # FP32 extension sweeps in the mixed path: at most 11 two-pass updates of
+    # at most 14 roundings each, 11 * 14 * 2^-24 = 9.2e-6 of max |u|
+    bound = 1e-9 if precision == "fp64" else 1e-5
+    assert np.max(np.abs(du.cpu().numpy() - ue_o)) <= bound * np.max(np.abs(ue_o))
 
 
 def test_fullsize_adjoint_steps(lib):

@@ -359,7 +359,12 @@ def test_two_species_competition_multistep(lib):
 
 def test_levelset_step_mixed_precision(lib):
     """FP32-mixed path: WENO5/Godunov arithmetic in FP32 except the
-    reinitialisation within 2h of the interface; against the FP64 oracle."""
+    reinitialisation within 2h of the interface, extension sweeps in FP32;
+    against the FP64 oracle.  Bound on the extended u: each FP32 two-pass
+    sweep update is a convex combination of at most 1 + N + N^2 = 13 terms,
+    rounded at most 14 times (unit roundoff 2^-24), and the passes do not
+    expand errors, so ceil(21 / 2) = 11 updates stay within
+    11 * 14 * 2^-24 = 9.2e-6 of max |u|."""
     g, ph0 = _shape_phi(3, 28, 3.0, "ellipsoid")
     ph = levelset.reinit(levelset.clamp(ph0, g.h), g.h)
     op = EBOperator(g, ph, 1.0)
@@ -377,7 +382,10 @@ def test_levelset_step_mixed_precision(lib):
     assert ((ph_g < 0) == (ph_o < 0)).all()
     assert np.max(np.abs(ph_g - ph_o)[near]) <= 1e-6 * g.h
     assert np.max(np.abs(ph_g - ph_o)) <= 1e-4 * g.h
-    assert np.max(np.abs(du.cpu().numpy() - ue_o)) <= 1e-10 * np.max(np.abs(ue_o))
+    assert np.max(np.abs(du.cpu().numpy() - ue_o)) <= 1e-5 * np.max(np.abs(ue_o))
+    # off the swept region u is the FP64 input, untouched
+    off = (np.abs(ue_o - u) == 0) & op.comp
+    assert np.array_equal(du.cpu().numpy()[off], u[off])
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
