@@ -341,7 +341,9 @@ __device__ void metadata_phase(const MetaArgs& a, int ncomp) {
 // The whole set-up as one persistent cooperative kernel (one CTA per SM):
 //   phase 1  classify this CTA's chunk of nodes (whole 32-node words), zero
 //            stale vector entries where a computational node stopped being
-//            one, count computational nodes;
+//            one, count computational nodes (when rows are whole words: a
+//            sign plane first, then, after a grid barrier, 32 nodes at a
+//            time from it);
 //   phase 2  (after a grid barrier) this CTA's offset from the counts of the
 //            CTAs before it, then the grid indices of its computational nodes
 //            in grid order;
@@ -362,27 +364,73 @@ __global__ void __launch_bounds__(INIT_NT, 1) init_domain_kernel(const ClassifyA
   __shared__ int s_off, s_tot;
   int cnt = 0;
   constexpr int UW = 4;  // words per warp and iteration: their loads overlap
-  for (long long w0 = wlo + (long long)wid * UW; w0 < whi; w0 += (long long)nwarp * UW) {
-    NodeLoad<N> L[UW];
-    uint8_t old[UW];
-    bool val[UW];
+  const int nx = g.n[N - 1];
+  if ((nx & 31) == 0) {
+    // Rows are whole 32-node words: classify a word at a time from a sign
+    // plane (bit set where phi < 0).  A node is computational when it and its
+    // 2N neighbours are inside and it is not on the box edge; the x
+    // neighbours are the word shifted by one bit (with the end bits of the
+    // adjacent words), the others the words one stride away.
+    uint32_t* const sbits = cbits + nw;
+    constexpr int US = 16;  // words per warp and iteration of the sign plane
+    for (long long w0 = wlo + (long long)wid * US; w0 < whi; w0 += (long long)nwarp * US) {
+      double v[US];
 #pragma unroll
-    for (int u = 0; u < UW; ++u) {
-      const long long p = 32 * (w0 + u) + lane;
-      val[u] = w0 + u < whi && p < g.size;
-      old[u] = K_OUT;
-      if (val[u]) {
-        node_load<N>(g, ca.phi, p, L[u]);
-        old[u] = ca.kind[p] & 3;
+      for (int u = 0; u < US; ++u) v[u] = w0 + u < whi ? ca.phi[32 * (w0 + u) + lane] : 1.0;
+#pragma unroll
+      for (int u = 0; u < US; ++u) {
+        const unsigned b = __ballot_sync(0xffffffffu, negative(v[u]));
+        if (lane == 0 && w0 + u < whi) sbits[w0 + u] = b;
       }
     }
+    if (!grid_barrier(ca.st, bar, 62)) return;
+    // a thread per word: its 32 kinds are written as two 16-byte stores
+    for (long long w = wlo + threadIdx.x; w < whi; w += blockDim.x) {
+      // axis indices of the word's first node
+      int ix[N];
+      unsigned rem = (unsigned)(32 * w);
 #pragma unroll
-    for (int u = 0; u < UW; ++u) {
-      const long long p = 32 * (w0 + u) + lane;
-      const uint8_t k = val[u] ? node_class<N>(L[u]) : K_OUT;
-      if (val[u]) {
-        if (k != K_OUT && L[u].near) atomicOr(&ca.st->err, ERRF_DOMAIN);
-        if (old[u] == K_COMP && k != K_COMP) {
+      for (int d = 0; d < N; ++d) {
+        ix[d] = (int)g.sdiv[d].div(rem);
+        rem -= (unsigned)ix[d] * (unsigned)g.stride[d];
+      }
+      const int x0 = ix[N - 1];
+      const unsigned s0 = __ldcg(sbits + w);
+      const unsigned sl = x0 > 0 ? __ldcg(sbits + w - 1) : 0u;
+      const unsigned sr = x0 + 32 < nx ? __ldcg(sbits + w + 1) : 0u;
+      unsigned all = s0 & ((s0 << 1) | (sl >> 31)) & ((s0 >> 1) | (sr << 31));
+      unsigned nearm = 0u;  // nodes within 3 nodes of the box edge
+#pragma unroll
+      for (int d = 0; d < N - 1; ++d) {
+        const long long ws = g.stride[d] >> 5;
+        all &= ix[d] > 0 ? __ldcg(sbits + w - ws) : 0u;
+        all &= ix[d] < g.n[d] - 1 ? __ldcg(sbits + w + ws) : 0u;
+        if (ix[d] < 3 || ix[d] > g.n[d] - 4) nearm = 0xffffffffu;
+      }
+      if (x0 == 0) {
+        all &= ~1u;
+        nearm |= 0x7u;
+      }
+      if (x0 + 32 == nx) {
+        all &= 0x7fffffffu;
+        nearm |= 0xe0000000u;
+      }
+      if (s0 & nearm) atomicOr(&ca.st->err, ERRF_DOMAIN);
+      // kind byte = inside bit + computational bit (K_OUT 0, K_GHOST 1,
+      // K_COMP 2); a nibble spreads to one bit per byte by a multiply
+      uint4* const kp = reinterpret_cast<uint4*>(ca.kind + 32 * w);
+      const uint4 o0 = kp[0], o1 = kp[1];
+      const unsigned ow[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+      unsigned kw[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        kw[q] = ((((s0 >> (4 * q)) & 15u) * 0x204081u) & 0x01010101u) +
+                ((((all >> (4 * q)) & 15u) * 0x204081u) & 0x01010101u);
+        // nodes that stop being computational: zero their vector entries
+        unsigned z = (ow[q] >> 1) & ~(kw[q] >> 1) & 0x01010101u;
+        while (z) {
+          const long long p = 32 * w + 4 * q + ((__ffs(z) - 1) >> 3);
+          z &= z - 1u;
           for (int s = 0; s < ca.nzero; ++s) {
             if (ca.zero_f64[s]) ca.zero_f64[s][p] = 0.0;
             if (ca.zero_f32[s]) ca.zero_f32[s][p] = 0.0f;
@@ -392,12 +440,51 @@ __global__ void __launch_bounds__(INIT_NT, 1) init_domain_kernel(const ClassifyA
             if (ca.basis_f32) ca.basis_f32[(long long)j * g.size + p] = 0.0f;
           }
         }
-        ca.kind[p] = k;
       }
-      const unsigned bal = __ballot_sync(0xffffffffu, val[u] && k == K_COMP);
-      if (lane == 0 && w0 + u < whi) {
-        cbits[w0 + u] = bal;
-        cnt += __popc(bal);
+      kp[0] = make_uint4(kw[0], kw[1], kw[2], kw[3]);
+      kp[1] = make_uint4(kw[4], kw[5], kw[6], kw[7]);
+      cbits[w] = all;
+      cnt += __popc(all);
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  } else {
+    for (long long w0 = wlo + (long long)wid * UW; w0 < whi; w0 += (long long)nwarp * UW) {
+      NodeLoad<N> L[UW];
+      uint8_t old[UW];
+      bool val[UW];
+  #pragma unroll
+      for (int u = 0; u < UW; ++u) {
+        const long long p = 32 * (w0 + u) + lane;
+        val[u] = w0 + u < whi && p < g.size;
+        old[u] = K_OUT;
+        if (val[u]) {
+          node_load<N>(g, ca.phi, p, L[u]);
+          old[u] = ca.kind[p] & 3;
+        }
+      }
+  #pragma unroll
+      for (int u = 0; u < UW; ++u) {
+        const long long p = 32 * (w0 + u) + lane;
+        const uint8_t k = val[u] ? node_class<N>(L[u]) : K_OUT;
+        if (val[u]) {
+          if (k != K_OUT && L[u].near) atomicOr(&ca.st->err, ERRF_DOMAIN);
+          if (old[u] == K_COMP && k != K_COMP) {
+            for (int s = 0; s < ca.nzero; ++s) {
+              if (ca.zero_f64[s]) ca.zero_f64[s][p] = 0.0;
+              if (ca.zero_f32[s]) ca.zero_f32[s][p] = 0.0f;
+            }
+            for (int j = 0; j < ca.nbasis; ++j) {
+              if (ca.basis_f64) ca.basis_f64[(long long)j * g.size + p] = 0.0;
+              if (ca.basis_f32) ca.basis_f32[(long long)j * g.size + p] = 0.0f;
+            }
+          }
+          ca.kind[p] = k;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, val[u] && k == K_COMP);
+        if (lane == 0 && w0 + u < whi) {
+          cbits[w0 + u] = bal;
+          cnt += __popc(bal);
+        }
       }
     }
   }
@@ -463,9 +550,9 @@ __global__ void __launch_bounds__(INIT_NT, 1) init_domain_kernel(const ClassifyA
   metadata_phase<N>(ma, ncomp);
 }
 
-// ints of scratch the set-up kernel needs: one count per CTA, then one bit
-// per node
-int init_scratch_ints(long long size) { return MAX_BLOCKS + (int)((size + 31) / 32); }
+// ints of scratch the set-up kernel needs: one count per CTA, then two bit
+// planes (computational nodes, signs of phi) of one bit per node
+int init_scratch_ints(long long size) { return MAX_BLOCKS + 2 * (int)((size + 31) / 32); }
 
 template <int N>
 static void* init_fn() {
