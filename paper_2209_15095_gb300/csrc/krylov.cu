@@ -1294,40 +1294,36 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
         if (pp[q] >= 0) dst[pp[q]] = add ? b[q] + y[q] : y[q];
     });
     if (outf != 0) continue;  // stage fields are read at computational points only
-    // 16 nodes per thread and iteration: one 16-byte load of kinds, the
-    // validity bits cleared off the computational set, unconditional zero
-    // stores for u.
-    const long long n16 = g.size >> 4;
-    const uint4* kind16 = reinterpret_cast<const uint4*>(S.kind);
-    uint4* valid16 = reinterpret_cast<uint4*>(S.fvalid);
-    for (long long c = gtid; c <= n16; c += gthreads) {
-      const long long base = c << 4;
-      if (c < n16) {
-        const uint4 kv = __ldg(kind16 + c);
-        const unsigned w[4] = {kv.x, kv.y, kv.z, kv.w};
-        unsigned fv[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          fv[q] = 0;
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const bool comp = ((w[q] >> (8 * b)) & 3u) == K_COMP;
-            if (comp) fv[q] |= 1u << (8 * b);
-            else S.u[base + 4 * q + b] = 0.0;
-          }
-        }
-        // the set-up wrote the bits of the computational points; 0 elsewhere
-        if (a.mode == MODE_ETD2) {
-          const uint4 old = valid16[c];
-          valid16[c] = make_uint4(old.x & (fv[0] * 0xffu), old.y & (fv[1] * 0xffu), old.z & (fv[2] * 0xffu),
-                                  old.w & (fv[3] * 0xffu));
-        }
+    // Off the computational set: u = 0 and the validity bits cleared.  A
+    // lane per pair of nodes, consecutive pairs on consecutive lanes (2-byte
+    // kind and validity accesses, 16-byte zero stores where u is 16-byte
+    // aligned); a pair with one computational node stores the other alone.
+    const long long npair = g.size >> 1;
+    const bool u16 = (reinterpret_cast<uintptr_t>(S.u) & 15u) == 0;
+    const uchar2* kind2 = reinterpret_cast<const uchar2*>(S.kind);
+    uchar2* valid2 = reinterpret_cast<uchar2*>(S.fvalid);
+    const long long ptid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long c = ptid; c < npair; c += gthreads) {
+      const uchar2 kv = __ldg(kind2 + c);
+      const bool c0 = (kv.x & 3) == K_COMP, c1 = (kv.y & 3) == K_COMP;
+      const long long p = c << 1;
+      if (!c0 && !c1 && u16) {
+        reinterpret_cast<double2*>(S.u)[c] = make_double2(0.0, 0.0);
       } else {
-        for (long long p = base; p < g.size; ++p) {
-          const bool comp = (__ldg(S.kind + p) & 3) == K_COMP;
-          if (!comp) S.u[p] = 0.0;
-          if (a.mode == MODE_ETD2 && !comp) S.fvalid[p] = 0;
-        }
+        if (!c0) S.u[p] = 0.0;
+        if (!c1) S.u[p + 1] = 0.0;
+      }
+      // the set-up wrote the bits of the computational points; 0 elsewhere
+      if (a.mode == MODE_ETD2 && !(c0 && c1)) {
+        const uchar2 old = valid2[c];
+        valid2[c] = make_uchar2(c0 ? old.x : (unsigned char)0, c1 ? old.y : (unsigned char)0);
+      }
+    }
+    if ((g.size & 1) && ptid == 0) {
+      const long long p = g.size - 1;
+      if ((__ldg(S.kind + p) & 3) != K_COMP) {
+        S.u[p] = 0.0;
+        if (a.mode == MODE_ETD2) S.fvalid[p] = 0;
       }
     }
   }

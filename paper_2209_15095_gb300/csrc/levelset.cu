@@ -256,20 +256,37 @@ __device__ bool build_work_set(const LsArgs& a, LsCtx& c, bool with_valid, int s
     rstr[d] = (unsigned)(g.stride[d] / bg.nx);
     rsw[d] = (long long)rstr[d] * bg.W;
   }
-  // pass A: one warp per word, a lane per node
-  for (long long w = c.wlo + wid; w < c.whi; w += nwarp) {
-    const unsigned r = g.wdiv.div((unsigned)w);
-    const int x = (int)((unsigned)w - r * (unsigned)bg.W) * 32 + lane;
-    bool sb = false, vb = false;
-    if (x < bg.nx) {
-      const long long p = (long long)r * bg.nx + x;
-      sb = abs_below(a.phi[p], Gbits);
-      vb = with_valid && (a.kind[p] & 3) == K_COMP;
+  // pass A: a lane per node, UA consecutive words per warp and iteration
+  // (their loads issued before any is used; where rows are whole words, a
+  // word's nodes are 32 w .. 32 w + 31 and every load is a predicated select)
+  constexpr int UA = 8;
+  const bool whole = bg.nx == 32 * bg.W;
+  for (long long w0 = c.wlo + (long long)wid * UA; w0 < c.whi; w0 += (long long)nwarp * UA) {
+    double ph[UA];
+    uint8_t kd[UA];
+    bool in[UA];
+#pragma unroll
+    for (int u = 0; u < UA; ++u) {
+      const long long w = w0 + u;
+      long long p = 32 * w + lane;
+      in[u] = w < c.whi;
+      if (!whole && in[u]) {
+        const unsigned r = g.wdiv.div((unsigned)w);
+        const int x = (int)((unsigned)w - r * (unsigned)bg.W) * 32 + lane;
+        in[u] = x < bg.nx;
+        p = (long long)r * bg.nx + x;
+      }
+      ph[u] = in[u] ? a.phi[p] : 0.0;
+      kd[u] = in[u] && with_valid ? a.kind[p] : (uint8_t)0;
     }
-    const unsigned ws = __ballot_sync(0xffffffffu, sb), wv = __ballot_sync(0xffffffffu, vb);
-    if (lane == 0) {
-      pl[P_S * bg.nw + w] = ws;
-      if (with_valid) pl[P_V0 * bg.nw + w] = wv;
+#pragma unroll
+    for (int u = 0; u < UA; ++u) {
+      const unsigned ws = __ballot_sync(0xffffffffu, in[u] && abs_below(ph[u], Gbits));
+      const unsigned wv = __ballot_sync(0xffffffffu, in[u] && (kd[u] & 3) == K_COMP);
+      if (lane == 0 && w0 + u < c.whi) {
+        pl[P_S * bg.nw + w0 + u] = ws;
+        if (with_valid) pl[P_V0 * bg.nw + w0 + u] = wv;
+      }
     }
   }
   if (!grid_barrier(a.st, c.bar, 20)) return false;
@@ -454,8 +471,19 @@ __device__ __forceinline__ int sweep_level(uint8_t f) {
 // has a thread of its own when the region is at most one entry per thread;
 // larger regions take one pass per barrier.  The fields arrive in FP64 and the
 // extended u leaves in FP64.
-template <int N>
-__device__ bool ext_sweeps_f32(const LsArgs& a, LsCtx& c, int n, long long cap, int K, double dtau, double dth,
+template <typename T>
+__device__ __forceinline__ T tfma(T x, T y, T z) {
+  if constexpr (sizeof(T) == 4) return fmaf(x, y, z);
+  else return fma(x, y, z);
+}
+template <typename T>
+__device__ __forceinline__ T tabs(T x) {
+  if constexpr (sizeof(T) == 4) return fabsf(x);
+  else return fabs(x);
+}
+
+template <int N, typename T>
+__device__ bool ext_sweeps_pair(const LsArgs& a, LsCtx& c, int n, long long cap, int K, double dtau, double dth,
                                const double* const* Q0) {
   constexpr int NTM = 1 + N + N * N;  // terms of a two-pass update
   const GridDev& g = a.g;
@@ -464,18 +492,28 @@ __device__ bool ext_sweeps_f32(const LsArgs& a, LsCtx& c, int n, long long cap, 
   const int* const swl = a.b.slist;
   const int sc1 = __ldcg(a.b.sw + 1), sc2 = __ldcg(a.b.sw + 2), sc3 = __ldcg(a.b.sw + 3);
   const long long len0 = (long long)sc1 + sc2 + sc3;
-  const float dtf = (float)dtau, dthf = (float)dth;
-  // FP32 ping-pong fields of the three sweeps in the FP64 ping-pong partners,
-  // which this path leaves unused (each holds two FP32 fields)
-  float* const F[6] = {reinterpret_cast<float*>(a.b.q[1]), reinterpret_cast<float*>(a.b.q[1]) + cap,
-                       reinterpret_cast<float*>(a.b.q[3]), reinterpret_cast<float*>(a.b.q[3]) + cap,
-                       reinterpret_cast<float*>(a.b.q[5]), reinterpret_cast<float*>(a.b.q[5]) + cap};
+  constexpr bool F32 = sizeof(T) == 4;
+  const T dtf = (T)dtau, dthf = (T)dth;
+  // ping-pong fields of the three sweeps: in FP64 the fields' own buffers;
+  // in FP32 copies in the FP64 ping-pong partners, which that path leaves
+  // unused (each holds two FP32 fields)
+  T* F[6];
+  if constexpr (F32) {
+#pragma unroll
+    for (int sw = 0; sw < 3; ++sw) {
+      F[2 * sw] = reinterpret_cast<T*>(a.b.q[2 * sw + 1]);
+      F[2 * sw + 1] = F[2 * sw] + cap;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) F[i] = reinterpret_cast<T*>(a.b.q[i]);
+  }
   for (long long i = gtid; i < n; i += gth) {
     const long long p = __ldcg(a.b.list + i);
 #pragma unroll
     for (int sw = 0; sw < 3; ++sw) {
-      const float v = (float)__ldcg(Q0[sw] + p);
-      F[2 * sw][p] = v;
+      const T v = (T)__ldcg(Q0[sw] + p);
+      if (F32) F[2 * sw][p] = v;
       F[2 * sw + 1][p] = v;
     }
   }
@@ -483,21 +521,21 @@ __device__ bool ext_sweeps_f32(const LsArgs& a, LsCtx& c, int n, long long cap, 
   // are prefixes of one sweep list): its upwind nodes and coefficients, and
   // those of its upwind neighbours with their sweep levels, once.
   int p = 0, up[N], lev[N], tu[N][N];
-  float c0 = 0.f, ad[N], c0u[N], au[N][N];
+  T c0 = T(0), ad[N], c0u[N], au[N][N];
   if (jt < len0) {
     const long long i = __ldcg(swl + jt);
     p = __ldcg(a.b.list + i);
     int ix[N];
     unpack<N>(__ldcg(a.b.lcoord + i), ix);
-    float asum = 0.f;
+    T asum = T(0);
 #pragma unroll
     for (int d = 0; d < N; ++d) {
       const double nd = __ldcg(a.b.nrm + d * cap + i);
       up[d] = (int)nbr(g, p, ix, d, nd > 0.0 ? -1 : 1);
-      ad[d] = dthf * fabsf((float)nd);
+      ad[d] = dthf * tabs((T)nd);
       asum += ad[d];
     }
-    c0 = 1.f - asum;
+    c0 = T(1) - asum;
     int gi[N];
 #pragma unroll
     for (int d = 0; d < N; ++d) gi[d] = __ldcg(a.b.gidx + up[d]);
@@ -509,15 +547,15 @@ __device__ bool ext_sweeps_f32(const LsArgs& a, LsCtx& c, int n, long long cap, 
       int ixu[N];
       unpack<N>(ok ? __ldcg(a.b.lcoord + gi[d]) : make_ushort4(0, 0, 0, 0), ixu);
       lev[d] = ok && lp == up[d] ? sweep_level(f) : 0;
-      float as = 0.f;
+      T as = T(0);
 #pragma unroll
       for (int e = 0; e < N; ++e) {
-        const float ne = ok ? (float)__ldcg(a.b.nrm + e * cap + gi[d]) : 0.f;
-        au[d][e] = dthf * fabsf(ne);
-        tu[d][e] = (int)nbr(g, up[d], ixu, e, ne > 0.f ? -1 : 1);
+        const T ne = ok ? (T)__ldcg(a.b.nrm + e * cap + gi[d]) : T(0);
+        au[d][e] = dthf * tabs(ne);
+        tu[d][e] = (int)nbr(g, up[d], ixu, e, ne > T(0) ? -1 : 1);
         as += au[d][e];
       }
-      c0u[d] = 1.f - as;
+      c0u[d] = T(1) - as;
     }
   }
   if (!grid_barrier(a.st, c.bar, 53)) return false;
@@ -525,24 +563,24 @@ __device__ bool ext_sweeps_f32(const LsArgs& a, LsCtx& c, int n, long long cap, 
   for (int sw = 0; sw < 3; ++sw) {
     const long long len = sw == 0 ? len0 : (sw == 1 ? sc2 + sc3 : sc3);
     const bool two = K >= 2 && len <= gth;
-    float* const X[2] = {F[2 * sw], F[2 * sw + 1]};
-    const float* const src = si < 0 ? nullptr : F[si];
+    T* const X[2] = {F[2 * sw], F[2 * sw + 1]};
+    const T* const src = si < 0 ? nullptr : F[si];
     const bool has = two && jt < len;
     // this sweep's update: membership of the neighbours, source terms (no
     // barrier: nothing written here is read by another thread)
     int ti[NTM];
-    float ds = 0.f, cq = 0.f, D = 0.f, tw[NTM];
+    T ds = T(0), cq = T(0), D = T(0), tw[NTM];
     unsigned live = 0u;
     if (has) {
-      float sd[N];
+      T sd[N];
 #pragma unroll
-      for (int d = 0; d < N; ++d) sd[d] = src ? __ldcg(src + up[d]) : 0.f;
-      ds = src ? dtf * __ldcg(src + p) : 0.f;
+      for (int d = 0; d < N; ++d) sd[d] = src ? __ldcg(src + up[d]) : T(0);
+      ds = src ? dtf * __ldcg(src + p) : T(0);
       cq = __ldcg(X[0] + p);
       ti[0] = p;
       tw[0] = c0 * c0;
       live = 1u;
-      D = fmaf(c0, ds, ds);
+      D = tfma(c0, ds, ds);
 #pragma unroll
       for (int d = 0; d < N; ++d) {
         const bool in = lev[d] > sw;
@@ -552,11 +590,11 @@ __device__ bool ext_sweeps_f32(const LsArgs& a, LsCtx& c, int n, long long cap, 
           tw[1 + N + d * N + e] = ad[d] * au[d][e];
         }
         if (in) {
-          D = fmaf(ad[d], dtf * sd[d], D);
+          D = tfma(ad[d], dtf * sd[d], D);
           live |= ((1u << N) - 1u) << (1 + N + d * N);
         }
         ti[1 + d] = up[d];
-        tw[1 + d] = ad[d] * (c0 + (in ? c0u[d] : 1.f));
+        tw[1 + d] = ad[d] * (c0 + (in ? c0u[d] : T(1)));
         live |= 1u << (1 + d);
       }
 #pragma unroll
@@ -576,13 +614,13 @@ __device__ bool ext_sweeps_f32(const LsArgs& a, LsCtx& c, int n, long long cap, 
     if (two) {
       for (; it + 2 <= K; it += 2) {
         if (has) {
-          const float* const qc = X[cur];
-          float qv[NTM];
+          const T* const qc = X[cur];
+          T qv[NTM];
 #pragma unroll
-          for (int k = 0; k < NTM; ++k) qv[k] = ((live >> k) & 1u) ? __ldcg(qc + ti[k]) : 0.f;
-          float t = D;
+          for (int k = 0; k < NTM; ++k) qv[k] = ((live >> k) & 1u) ? __ldcg(qc + ti[k]) : T(0);
+          T t = D;
 #pragma unroll
-          for (int k = 0; k < NTM; ++k) t = fmaf(tw[k], qv[k], t);
+          for (int k = 0; k < NTM; ++k) t = tfma(tw[k], qv[k], t);
           cq = t;
           X[cur ^ 1][p] = t;
         }
@@ -591,12 +629,12 @@ __device__ bool ext_sweeps_f32(const LsArgs& a, LsCtx& c, int n, long long cap, 
       }
     }
     for (; it < K; ++it) {
-      const float* const qc = X[cur];
-      float* const qn = X[cur ^ 1];
+      const T* const qc = X[cur];
+      T* const qn = X[cur ^ 1];
       if (has) {
-        float t = fmaf(c0, cq, ds);
+        T t = tfma(c0, cq, ds);
 #pragma unroll
-        for (int d = 0; d < N; ++d) t = fmaf(ad[d], __ldcg(qc + up[d]), t);
+        for (int d = 0; d < N; ++d) t = tfma(ad[d], __ldcg(qc + up[d]), t);
         cq = t;
         qn[p] = t;
       } else if (!two) {
@@ -605,17 +643,17 @@ __device__ bool ext_sweeps_f32(const LsArgs& a, LsCtx& c, int n, long long cap, 
           const long long q = __ldcg(a.b.list + i);
           int ix[N];
           unpack<N>(__ldcg(a.b.lcoord + i), ix);
-          float asum = 0.f, qu[N], aw[N];
+          T asum = T(0), qu[N], aw[N];
 #pragma unroll
           for (int d = 0; d < N; ++d) {
             const double nd = __ldcg(a.b.nrm + d * cap + i);
             qu[d] = __ldcg(qc + nbr(g, q, ix, d, nd > 0.0 ? -1 : 1));
-            aw[d] = dthf * fabsf((float)nd);
+            aw[d] = dthf * tabs((T)nd);
             asum += aw[d];
           }
-          float t = fmaf(1.f - asum, __ldcg(qc + q), src ? dtf * __ldcg(src + q) : 0.f);
+          T t = tfma(T(1) - asum, __ldcg(qc + q), src ? dtf * __ldcg(src + q) : T(0));
 #pragma unroll
-          for (int d = 0; d < N; ++d) t = fmaf(aw[d], qu[d], t);
+          for (int d = 0; d < N; ++d) t = tfma(aw[d], qu[d], t);
           qn[q] = t;
         }
       }
@@ -902,7 +940,7 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
     lc1 += lev == 1;
     lc2 += lev == 2;
     lc3 += lev == 3;
-    if (a.mixed) a.b.gidx[p] = (int)i;
+    a.b.gidx[p] = (int)i;
     U[0][p] = (f & F_V0) ? a.u[p] : 0.0;
     double un = 0.0;
     if ((f & F_V1) && (f & F_T2)) {
@@ -981,11 +1019,16 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
   const int K = (int)ceil(12.0 * sqrt((double)N));
   const double dtau = h / (2.0 * sqrt((double)N));
   const double dth = dtau * inv_h;
-  if (a.mixed) {
+  {
     const double* const Q0[3] = {UNN[0], UN[0], U[0]};
-    if (!ext_sweeps_f32<N>(a, c, n, cap, K, dtau, dth, Q0)) return;
-  } else if (!ext_sweeps_f64<N>(a, c, n, cap, K, dtau, dth, UNN, UN, U)) {
-    return;
+    const long long len0 = (long long)__ldcg(a.b.sw + 1) + __ldcg(a.b.sw + 2) + __ldcg(a.b.sw + 3);
+    if (a.mixed) {
+      if (!ext_sweeps_pair<N, float>(a, c, n, cap, K, dtau, dth, Q0)) return;
+    } else if (N <= 3 && len0 <= gth) {
+      if (!ext_sweeps_pair<N, double>(a, c, n, cap, K, dtau, dth, Q0)) return;
+    } else if (!ext_sweeps_f64<N>(a, c, n, cap, K, dtau, dth, UNN, UN, U)) {
+      return;
+    }
   }
   if (!grid_barrier(a.st, c.bar, 54)) return;
   // Stefan speed on T
