@@ -4,7 +4,9 @@ a domain of 8 computational points (Krylov happy breakdown below 5 vectors),
 the largest Krylov basis (m_max = 61: an augmented matrix of 64 rows, with
 rejections at m_max), a domain reaching into the box margin (ETD_ERR_DOMAIN)
 and a non-finite field (ETD_ERR_NONFINITE): errors are reported, nothing
-hangs."""
+hangs.  Grids whose rows are whole 32-node words (the word-parallel
+classification), down to one word per row, in 2D-4D, with their margin
+error."""
 import numpy as np
 import pytest
 
@@ -139,3 +141,54 @@ def test_nonfinite_field_is_reported(lib):
     with pytest.raises(lib.EtdError) as e:
         ctx.step(0.01, [du], stats=True)
     assert e.value.name == "ETD_ERR_NONFINITE"
+
+
+def _aniso(shape, h=0.1):
+    """A grid of the given shape and spacing h, centred on the origin."""
+    half = [0.5 * h * (n - 1) for n in shape]
+    return Grid(tuple(shape), tuple(-x for x in half), tuple(half))
+
+
+@pytest.mark.parametrize("shape", [(40, 32), (24, 64), (20, 18, 32), (14, 16, 96), (14, 14, 14, 32)])
+def test_word_rows_domain(lib, shape):
+    """Rows of whole 32-node words take the word-parallel classification
+    (one word per row when the last axis is 32: both box edges in one word).
+    An ellipsoid 3.5 h from every edge and a random-sign interior: kinds,
+    indices, D_p and the Gershgorin bound against the oracle, bit-exact
+    where integer."""
+    g = _aniso(shape)
+    x = g.coords()
+    semi = [0.5 * g.h * (n - 1) - 3.5 * g.h for n in shape]
+    ph_ball = np.sqrt(sum((x[d] / semi[d]) ** 2 for d in range(len(shape)))) - 1.0
+    rng = np.random.default_rng(sum(shape))
+    ph_rand = np.ones(g.n)
+    inner = tuple(slice(4, n - 4) for n in shape)
+    ph_rand[inner] = rng.uniform(-1.0, 0.3, size=ph_rand[inner].shape)
+    for ph, full in ((ph_ball, True), (ph_rand, False)):
+        op = EBOperator(g, ph, 1.0)
+        ctx = _ctx(lib, g)
+        ctx.init_domain(0, _dev(ph))
+        dom = ctx.read_domain(0)
+        ref_kind = np.where(op.comp, 2, np.where(op.ghost, 1, 0)).astype(np.uint8)
+        assert np.array_equal(dom["kind"], ref_kind)
+        assert dom["ncomp"] == op.ncomp
+        assert np.array_equal(dom["idx"], op.index.astype(np.int32))
+        if full:
+            assert np.max(np.abs(dom["diag"] - op.diag) / np.abs(op.diag)) < 1e-12
+            assert abs(dom["gersh"] - op.gershgorin()) <= 1e-12 * op.gershgorin()
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (40, 64)])
+def test_word_rows_margin_is_reported(lib, shape):
+    """The word-parallel classification reports an inside node within 3
+    nodes of the box edge (ETD_ERR_DOMAIN), as the per-node one does."""
+    g = _aniso(shape)
+    x = g.coords()
+    # a ball touching the last axis' edge region: inside nodes at index 2
+    ph = np.sqrt(sum(c * c for c in x[:-1]) + (x[-1] - x[-1].max() + 2.5 * g.h) ** 2) - 0.45
+    assert (ph < 0)[..., -3].any()
+    ctx = _ctx(lib, g)
+    ctx.init_domain(0, _dev(ph))
+    with pytest.raises(lib.EtdError) as e:
+        ctx.sync()
+    assert e.value.name == "ETD_ERR_DOMAIN"
