@@ -187,9 +187,10 @@ __device__ __forceinline__ void weno5_pair(const C* q, C epsw, C& dm, C& dp) {
 
 // Godunov |grad phi| at node p from array src; positive: outward motion.
 // FP64 (C = double): undivided differences, eps scaled by h^2, one factor
-// 1/h at the end.  FP32-mixed (C = float): differences formed in FP64 and
-// divided by h, then WENO5 and Godunov in FP32 (an eps scaled by h^2 would
-// leave the FP32 normal range).
+// 1/h at the end.  FP32-mixed (C = float): the seven values rounded to FP32,
+// differences divided by h in FP32 (an eps scaled by h^2 would leave the
+// FP32 normal range), then WENO5 and Godunov in FP32; no FP64 arithmetic
+// (this GPU issues one FP64 warp instruction per ~20 cycles per SM).
 template <typename C, int N>
 __device__ double godunov(const GridDev& g, const double* __restrict__ src, long long p, const int* ix,
                           bool positive) {
@@ -203,8 +204,17 @@ __device__ double godunov(const GridDev& g, const double* __restrict__ src, long
 #pragma unroll
     for (int k = -3; k <= 3; ++k) f[k + 3] = __ldcg(src + nbr(g, p, ix, d, k));
     C q[6];
+    if constexpr (RAW) {
 #pragma unroll
-    for (int k = -2; k <= 3; ++k) q[k + 2] = RAW ? C(f[k + 3] - f[k + 2]) : C((f[k + 3] - f[k + 2]) * inv_h);
+      for (int k = -2; k <= 3; ++k) q[k + 2] = f[k + 3] - f[k + 2];
+    } else {
+      const C ih = C(inv_h);
+      C fc[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) fc[k] = C(f[k]);
+#pragma unroll
+      for (int k = -2; k <= 3; ++k) q[k + 2] = (fc[k + 3] - fc[k + 2]) * ih;
+    }
     C dm, dp;
     weno5_pair<C>(q, epsw, dm, dp);
     // outward: max(max(d-, 0)^2, min(d+, 0)^2) = max(d-, -d+, 0)^2 (a square
