@@ -74,12 +74,12 @@ enum {
  *               dot products / norms and the basis combination accumulated
  *               error-free in FP32 pairs and summed across the grid in FP64;
  *               H, the small exponential, the controller, u and F stay FP64.
- *               In the level set, phi, u, the Stefan speed and the RK updates
- *               stay FP64; the HJ-WENO5/Godunov arithmetic is FP32 for the
- *               advection and, beyond 2h from the interface, for the
- *               reinitialisation; the extension sweeps run in FP32 (the
- *               extended u off the interior differs from FP64 by rounding,
- *               within 1e-5 of max |u|).
+ *               In the level set, phi, u and the RK updates stay FP64; the
+ *               HJ-WENO5/Godunov arithmetic is FP32 for the advection and,
+ *               beyond 2h from the interface, for the reinitialisation; the
+ *               extension sweeps and the Stefan speed's interpolation run in
+ *               FP32 (the extended u off the interior differs from FP64 by
+ *               rounding, within 1e-5 of max |u|).
  *   krylov_tol  relative tolerance of the adaptive Krylov evaluation
  *   m_max       largest Krylov basis, 5 <= m_max <= 61
  *   reaction    f(u):  NONE 0;  LOGISTIC u(1-u);  LOGISTIC_AK rp[0] u (1 - u/rp[1]);

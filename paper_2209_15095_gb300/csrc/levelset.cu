@@ -784,6 +784,64 @@ __device__ bool ext_sweeps_f64(const LsArgs& a, LsCtx& c, int n, long long cap, 
   return true;
 }
 
+// Stefan speed of the mixed variant at tube node x (axis indices ix, unit
+// normal n, level set value phi): V = mu max(0, (4 u(y_1) - u(y_2)) / (2h)),
+// y_k = x - (phi + k h) n, u at y_k by N-linear interpolation; the same
+// formula as the FP64 path, in FP32.  The sample points are taken relative
+// to the node, in grid units (t_d = -(phi + k h) n_d / h, |t_d| <= about 8),
+// so that FP32 keeps the interpolation weights to ~1e-6; the cell index is
+// clamped in integers as the FP64 path clamps the coordinate to the box.
+template <int N>
+__device__ double stefan_speed_f32(const GridDev& g, const double* __restrict__ u, const int* ix, const double* nv,
+                                   double ph, double mu) {
+  const float inv_h = (float)(1.0 / g.h);
+  const float phf = (float)ph;
+  const float hf = (float)g.h;
+  float nf[N];
+#pragma unroll
+  for (int d = 0; d < N; ++d) nf[d] = (float)nv[d];
+  float us[2];
+#pragma unroll
+  for (int sidx = 0; sidx < 2; ++sidx) {
+    const float off = -(phf + (sidx == 0 ? hf : 2.f * hf)) * inv_h;
+    float fr[N];
+    long long q0 = 0;
+#pragma unroll
+    for (int d = 0; d < N; ++d) {
+      const float t = off * nf[d];
+      const float fl = floorf(t);
+      int ii = ix[d] + (int)fl;
+      float f = t - fl;
+      if (ii < 0) {
+        ii = 0;
+        f = 0.f;
+      } else if (ii > g.n[d] - 2) {
+        ii = g.n[d] - 2;
+        f = 1.f;
+      }
+      fr[d] = f;
+      q0 += (long long)ii * g.stride[d];
+    }
+    float cv[1 << N];
+#pragma unroll
+    for (int corner = 0; corner < (1 << N); ++corner) {
+      long long q = q0;
+#pragma unroll
+      for (int d = 0; d < N; ++d)
+        if ((corner >> d) & 1) q += g.stride[d];
+      cv[corner] = (float)u[q];
+    }
+#pragma unroll
+    for (int d = 0; d < N; ++d) {
+#pragma unroll
+      for (int corner = 0; corner < (1 << N); corner += 2 << d)
+        cv[corner] = fmaf(fr[d], cv[corner + (1 << d)] - cv[corner], cv[corner]);
+    }
+    us[sidx] = cv[0];
+  }
+  return (double)((float)mu * fmaxf(0.f, (4.f * us[0] - us[1]) * (0.5f * inv_h)));
+}
+
 // TVD-RK3 on the nodes of T (list order); L(src, p) supplied by the caller.
 // Stage values p1/p2 hold phi off T (copied when the work set is built).
 // The stage list holds the work-list positions of the update set T: entries
@@ -1049,49 +1107,54 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
       if (!(a.b.lflag[i] & F_T)) continue;
       int ix[N];
       unpack<N>(a.b.lcoord[i], ix);
-      double nv[N], xg[N];
+      double nv[N];
       const double ph = a.phi[p];
 #pragma unroll
-      for (int d = 0; d < N; ++d) {
-        nv[d] = __ldcg(a.b.nrm + d * cap + i);
-        xg[d] = (g.lo[d] + h * ix[d]) - ph * nv[d];
+      for (int d = 0; d < N; ++d) nv[d] = __ldcg(a.b.nrm + d * cap + i);
+      double V;
+      if (a.mixed) {
+        V = stefan_speed_f32<N>(g, a.u, ix, nv, ph, a.mu);
+      } else {
+        double xg[N];
+#pragma unroll
+        for (int d = 0; d < N; ++d) xg[d] = (g.lo[d] + h * ix[d]) - ph * nv[d];
+        double us[2];
+#pragma unroll
+        for (int sidx = 0; sidx < 2; ++sidx) {
+          const double dist = sidx == 0 ? h : 2.0 * h;
+          int i0[N];
+          double fr[N];
+          long long q0 = 0;
+#pragma unroll
+          for (int d = 0; d < N; ++d) {
+            double s = ((xg[d] - dist * nv[d]) - g.lo[d]) * inv_h;
+            s = fmin(fmax(s, 0.0), (double)(g.n[d] - 1));
+            int ii = (int)floor(s);
+            ii = min(ii, g.n[d] - 2);
+            i0[d] = ii;
+            fr[d] = s - ii;
+            q0 += (long long)ii * g.stride[d];
+          }
+          // N-linear interpolation one axis at a time (2^N - 1 lerps; the
+          // same value as the sum of corner weights times corner values)
+          double cv[1 << N];
+#pragma unroll
+          for (int corner = 0; corner < (1 << N); ++corner) {
+            long long q = q0;
+#pragma unroll
+            for (int d = 0; d < N; ++d)
+              if ((corner >> d) & 1) q += g.stride[d];
+            cv[corner] = a.u[q];
+          }
+#pragma unroll
+          for (int d = 0; d < N; ++d) {
+#pragma unroll
+            for (int corner = 0; corner < (1 << N); corner += 2 << d) cv[corner] = fma(fr[d], cv[corner + (1 << d)] - cv[corner], cv[corner]);
+          }
+          us[sidx] = cv[0];
+        }
+        V = a.mu * fmax(0.0, (4.0 * us[0] - us[1]) * inv_2h);
       }
-      double us[2];
-#pragma unroll
-      for (int sidx = 0; sidx < 2; ++sidx) {
-        const double dist = sidx == 0 ? h : 2.0 * h;
-        int i0[N];
-        double fr[N];
-        long long q0 = 0;
-#pragma unroll
-        for (int d = 0; d < N; ++d) {
-          double s = ((xg[d] - dist * nv[d]) - g.lo[d]) * inv_h;
-          s = fmin(fmax(s, 0.0), (double)(g.n[d] - 1));
-          int ii = (int)floor(s);
-          ii = min(ii, g.n[d] - 2);
-          i0[d] = ii;
-          fr[d] = s - ii;
-          q0 += (long long)ii * g.stride[d];
-        }
-        // N-linear interpolation one axis at a time (2^N - 1 lerps; the
-        // same value as the sum of corner weights times corner values)
-        double cv[1 << N];
-#pragma unroll
-        for (int corner = 0; corner < (1 << N); ++corner) {
-          long long q = q0;
-#pragma unroll
-          for (int d = 0; d < N; ++d)
-            if ((corner >> d) & 1) q += g.stride[d];
-          cv[corner] = a.u[q];
-        }
-#pragma unroll
-        for (int d = 0; d < N; ++d) {
-#pragma unroll
-          for (int corner = 0; corner < (1 << N); corner += 2 << d) cv[corner] = fma(fr[d], cv[corner + (1 << d)] - cv[corner], cv[corner]);
-        }
-        us[sidx] = cv[0];
-      }
-      const double V = a.mu * fmax(0.0, (4.0 * us[0] - us[1]) * inv_2h);
       a.b.V[i] = V;
       stage_push(a, (int)i, true);
       vm = fmax(vm, V);
