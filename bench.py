@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--rk-schemes", default="etd2rk,etd3rk,etd4rk,etd3",
                     help="comma-separated integrators other than ETD2 timed on the same step (FP64)")
     ap.add_argument("--no-poisson", action="store_true")
+    ap.add_argument("--mixed-tols", default="1e-6",
+                    help="extra FP32-mixed legs at these Krylov tolerances (comma-separated): speed-up and error in u")
     ap.add_argument("--clocks", default="on", choices=["on", "off"])
     ap.add_argument("--no-stress", action="store_true")
     ap.add_argument("--stress-steps", type=int, default=3)
@@ -299,6 +301,7 @@ def main():
     # the same mixed run at the FP64 run's Krylov tolerance: the error of the
     # FP32 arithmetic alone
     rmt = None if args.no_mixed or getattr(w, "tol_mixed", w.tol) == w.tol else run("mixed", tol=w.tol)
+    rsw = [] if args.no_mixed else [(float(t), run("mixed", tol=float(t))) for t in args.mixed_tols.split(",") if t]
     rks = {} if args.no_etd2rk else {sc: run("fp64", sc) for sc in args.rk_schemes.split(",") if sc}
     pois = None if args.no_poisson or rank != 0 else run_poisson(etd, stream, dev)
     e2e = None if args.no_e2e else run_e2e(args, w, make_ctx, initial_state, one_step, stream, flush, dev)
@@ -351,6 +354,13 @@ def main():
             "max_rel_err_u_vs_fp64": mixed_error(r64, rmt, nsp), "dtype": "f32+f64", "krylov_tol": w.tol,
             "note": "mixed precision at the FP64 run's Krylov tolerance; the error of the FP32 arithmetic alone",
             "breakdown_ms": {n: float(v) for n, v in zip(names, np.array(rmt["parts"]).mean(axis=0))}}
+    if rsw:
+        out["mixed_tol_sweep"] = []
+        for tol, rr in rsw:
+            tt = sum(rr["times"]) / 1e3
+            out["mixed_tol_sweep"].append({
+                "krylov_tol": tol, "value": rr["cells"] / tt / 1e6, "ms_per_step": 1e3 * tt / args.steps,
+                "speedup_vs_fp64": t64 / tt, "max_rel_err_u_vs_fp64": mixed_error(r64, rr, nsp)})
     if pois is not None:
         out["poisson"] = pois
     nevals = {"etd2rk": 2, "etd3rk": 3, "etd4rk": 4, "etd3": 1}

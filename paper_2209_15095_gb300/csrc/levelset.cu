@@ -988,34 +988,62 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
     int ix[N];
     unpack<N>(a.b.lcoord[i], ix);
     // central differences times 1/(2h), one reciprocal of |grad phi|: FP64
-    // divisions cost about ten FP64 instructions each
-    double gr[N];
-    double s2 = 0.0;
-#pragma unroll
-    for (int d = 0; d < N; ++d) {
-      gr[d] = (a.phi[nbr(g, p, ix, d, 1)] - a.phi[nbr(g, p, ix, d, -1)]) * inv_2h;
-      s2 += gr[d] * gr[d];
-    }
-    const double rn = 1.0 / fmax(sqrt(s2), GRAD_FLOOR);
-    double nv[N];
-#pragma unroll
-    for (int d = 0; d < N; ++d) {
-      nv[d] = gr[d] * rn;
-      a.b.nrm[d * cap + i] = nv[d];
-    }
+    // divisions cost about ten FP64 instructions each.  Mixed variant: the
+    // values rounded to FP32 and the arithmetic in FP32 (normals and u_n feed
+    // the FP32 extension sweeps and Stefan interpolation)
     const uint8_t f = a.b.lflag[i];
+    const bool want_un = (f & F_V1) && (f & F_T2);
+    double nv[N];
+    double un = 0.0;
+    if (a.mixed) {
+      const float ih2 = (float)inv_2h;
+      float gf[N], s2f = 0.f;
+#pragma unroll
+      for (int d = 0; d < N; ++d) {
+        gf[d] = ((float)a.phi[nbr(g, p, ix, d, 1)] - (float)a.phi[nbr(g, p, ix, d, -1)]) * ih2;
+        s2f = fmaf(gf[d], gf[d], s2f);
+      }
+      const float rnf = 1.f / fmaxf(sqrtf(s2f), (float)GRAD_FLOOR);
+      float nf[N];
+#pragma unroll
+      for (int d = 0; d < N; ++d) {
+        nf[d] = gf[d] * rnf;
+        nv[d] = (double)nf[d];
+        a.b.nrm[d * cap + i] = nv[d];
+      }
+      if (want_un) {
+        float uf = 0.f;
+#pragma unroll
+        for (int d = 0; d < N; ++d)
+          uf = fmaf(nf[d], (float)a.u[nbr(g, p, ix, d, 1)] - (float)a.u[nbr(g, p, ix, d, -1)], uf);
+        un = (double)(uf * ih2);
+      }
+    } else {
+      double gr[N];
+      double s2 = 0.0;
+#pragma unroll
+      for (int d = 0; d < N; ++d) {
+        gr[d] = (a.phi[nbr(g, p, ix, d, 1)] - a.phi[nbr(g, p, ix, d, -1)]) * inv_2h;
+        s2 += gr[d] * gr[d];
+      }
+      const double rn = 1.0 / fmax(sqrt(s2), GRAD_FLOOR);
+#pragma unroll
+      for (int d = 0; d < N; ++d) {
+        nv[d] = gr[d] * rn;
+        a.b.nrm[d * cap + i] = nv[d];
+      }
+      if (want_un) {
+#pragma unroll
+        for (int d = 0; d < N; ++d) un += nv[d] * (a.u[nbr(g, p, ix, d, 1)] - a.u[nbr(g, p, ix, d, -1)]);
+        un *= inv_2h;
+      }
+    }
     const int lev = sweep_level(f);
     lc1 += lev == 1;
     lc2 += lev == 2;
     lc3 += lev == 3;
     a.b.gidx[p] = (int)i;
     U[0][p] = (f & F_V0) ? a.u[p] : 0.0;
-    double un = 0.0;
-    if ((f & F_V1) && (f & F_T2)) {
-#pragma unroll
-      for (int d = 0; d < N; ++d) un += nv[d] * (a.u[nbr(g, p, ix, d, 1)] - a.u[nbr(g, p, ix, d, -1)]);
-      un *= inv_2h;
-    }
     UN[0][p] = un;
     a.b.p1[p] = a.phi[p];
     a.b.p2[p] = a.phi[p];
@@ -1050,11 +1078,20 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
         if ((f & F_V2) && (f & F_T1)) {
           int ix[N];
           unpack<N>(a.b.lcoord[i], ix);
+          if (a.mixed) {
+            float uf = 0.f;
 #pragma unroll
-          for (int d = 0; d < N; ++d)
-            unn += __ldcg(a.b.nrm + d * cap + i) *
-                   (__ldcg(UN[0] + nbr(g, p, ix, d, 1)) - __ldcg(UN[0] + nbr(g, p, ix, d, -1)));
-          unn *= inv_2h;
+            for (int d = 0; d < N; ++d)
+              uf = fmaf((float)__ldcg(a.b.nrm + d * cap + i),
+                        (float)__ldcg(UN[0] + nbr(g, p, ix, d, 1)) - (float)__ldcg(UN[0] + nbr(g, p, ix, d, -1)), uf);
+            unn = (double)(uf * (float)inv_2h);
+          } else {
+#pragma unroll
+            for (int d = 0; d < N; ++d)
+              unn += __ldcg(a.b.nrm + d * cap + i) *
+                     (__ldcg(UN[0] + nbr(g, p, ix, d, 1)) - __ldcg(UN[0] + nbr(g, p, ix, d, -1)));
+            unn *= inv_2h;
+          }
         }
         UNN[0][p] = unn;
       }
