@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--rk-schemes", default="etd2rk,etd3rk,etd4rk,etd3",
                     help="comma-separated integrators other than ETD2 timed on the same step (FP64)")
     ap.add_argument("--no-poisson", action="store_true")
-    ap.add_argument("--mixed-tols", default="1e-6",
+    ap.add_argument("--mixed-tols", default="1.1e-6",
                     help="extra FP32-mixed legs at these Krylov tolerances (comma-separated): speed-up and error in u")
     ap.add_argument("--clocks", default="on", choices=["on", "off"])
     ap.add_argument("--no-stress", action="store_true")
