@@ -76,7 +76,7 @@ enum {
  *               H, the small exponential, the controller, u and F stay FP64.
  *               In the level set, phi, u and the RK updates stay FP64; the
  *               HJ-WENO5/Godunov arithmetic is FP32 for the advection and,
- *               beyond 2h from the interface, for the reinitialisation; the
+ *               beyond h from the interface, for the reinitialisation; the
  *               extension sweeps and the Stefan speed's interpolation run in
  *               FP32 (the extended u off the interior differs from FP64 by
  *               rounding, within 1e-5 of max |u|).

@@ -185,6 +185,37 @@ __device__ __forceinline__ void weno5_pair(const C* q, C epsw, C& dm, C& dp) {
   }
 }
 
+// One axis of the Godunov |grad phi| (godunov, below): max(d-, -d+, 0) (outward) or its
+// mirror image, from the WENO5 pair on the seven values along axis d.
+// inv_h = 1/h; epsw the WENO epsilon of the arithmetic (see godunov).
+template <typename C, int N>
+__device__ __forceinline__ C godunov_mx(const GridDev& g, const double* __restrict__ src, long long p, const int* ix,
+                                        int d, bool positive, double inv_h, C epsw) {
+  constexpr bool RAW = sizeof(C) == 8;
+  double f[7];
+#pragma unroll
+  for (int k = -3; k <= 3; ++k) f[k + 3] = __ldcg(src + nbr(g, p, ix, d, k));
+  C q[6];
+  if constexpr (RAW) {
+#pragma unroll
+    for (int k = -2; k <= 3; ++k) q[k + 2] = f[k + 3] - f[k + 2];
+  } else {
+    const C ih = C(inv_h);
+    C fc[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) fc[k] = C(f[k]);
+#pragma unroll
+    for (int k = -2; k <= 3; ++k) q[k + 2] = (fc[k + 3] - fc[k + 2]) * ih;
+  }
+  C dm, dp;
+  weno5_pair<C>(q, epsw, dm, dp);
+  // outward: max(max(d-, 0)^2, min(d+, 0)^2) = max(d-, -d+, 0)^2 (a square
+  // is monotone on the non-negatives); inward: the mirror image.  Exact
+  // sign flips and no branch, so that no FP64 work of the other case is
+  // issued predicated off.
+  return fmax(fmax(positive ? dm : -dm, positive ? -dp : dp), C(0));
+}
+
 // Godunov |grad phi| at node p from array src; positive: outward motion.
 // FP64 (C = double): undivided differences, eps scaled by h^2, one factor
 // 1/h at the end.  FP32-mixed (C = float): the seven values rounded to FP32,
@@ -200,28 +231,7 @@ __device__ double godunov(const GridDev& g, const double* __restrict__ src, long
   C acc = C(0);
 #pragma unroll
   for (int d = 0; d < N; ++d) {
-    double f[7];
-#pragma unroll
-    for (int k = -3; k <= 3; ++k) f[k + 3] = __ldcg(src + nbr(g, p, ix, d, k));
-    C q[6];
-    if constexpr (RAW) {
-#pragma unroll
-      for (int k = -2; k <= 3; ++k) q[k + 2] = f[k + 3] - f[k + 2];
-    } else {
-      const C ih = C(inv_h);
-      C fc[7];
-#pragma unroll
-      for (int k = 0; k < 7; ++k) fc[k] = C(f[k]);
-#pragma unroll
-      for (int k = -2; k <= 3; ++k) q[k + 2] = (fc[k + 3] - fc[k + 2]) * ih;
-    }
-    C dm, dp;
-    weno5_pair<C>(q, epsw, dm, dp);
-    // outward: max(max(d-, 0)^2, min(d+, 0)^2) = max(d-, -d+, 0)^2 (a square
-    // is monotone on the non-negatives); inward: the mirror image.  Exact
-    // sign flips and no branch, so that no FP64 work of the other case is
-    // issued predicated off.
-    const C mx = fmax(fmax(positive ? dm : -dm, positive ? -dp : dp), C(0));
+    const C mx = godunov_mx<C, N>(g, src, p, ix, d, positive, inv_h, epsw);
     acc = fma(mx, mx, acc);
   }
   return RAW ? (double)sqrt(acc) * inv_h : (double)sqrt(acc);
@@ -852,8 +862,16 @@ __device__ __forceinline__ void stage_push(const LsArgs& a, int i, bool front) {
   else a.b.slist[a.g.size - 1 - atomicAdd(&a.b.count[2], 1)] = i;
 }
 
-template <int N, typename LFn>
-__device__ bool rk3(const LsArgs& a, LsCtx& c, double dt, bool clamp_last, LFn L) {
+// With SPLIT, the FP64 entries (the front of the stage list) have their N
+// axes evaluated on N lanes each (32 / N entries per warp): the per-axis
+// terms come back by shuffles and are summed in axis order as in godunov,
+// so the result is the same; a warp then issues a third (3D) of the FP64
+// instructions of a warp of whole entries.  This GPU issues about one FP64
+// warp instruction per 80 cycles per SM sub-partition, so a warp of FP64
+// entries sets the stage time on its sub-partition whatever its active lanes:
+// LAx(src, p, ix, i, d) gives the axis term, LFin(i, acc) the update value.
+template <int N, bool SPLIT, typename LFn, typename LAx, typename LFin>
+__device__ bool rk3(const LsArgs& a, LsCtx& c, double dt, bool clamp_last, LFn L, LAx LAxis, LFin LFinal) {
   const GridDev& g = a.g;
   const int nf = __ldcg(a.b.count + 1), nb = __ldcg(a.b.count + 2);
   const double G = BAND * g.h;
@@ -862,17 +880,13 @@ __device__ bool rk3(const LsArgs& a, LsCtx& c, double dt, bool clamp_last, LFn L
   const int lane = threadIdx.x & 31;
   const long long warp0 = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5);
   const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+  constexpr int NPW = 32 / N;  // split FP64 entries per warp
+  const long long cf = SPLIT ? ((long long)nf + NPW - 1) / NPW : 0;
+  const long long nfe = SPLIT ? nf : 0;
+  const long long nchunk = cf + ((long long)nf + nb - nfe + 31) / 32;
   for (int stage = 0; stage < 3; ++stage) {
     const double* src = stage == 0 ? a.phi : (stage == 1 ? a.b.p1 : a.b.p2);
-    for (long long chunk = warp0; 32 * chunk < nf + nb; chunk += wstride) {
-      const long long j = 32 * chunk + lane;
-      if (j >= nf + nb) continue;
-      const bool front = j < nf;
-      const long long i = __ldcg(a.b.slist + (front ? j : g.size - 1 - (j - nf)));
-      const long long p = __ldcg(a.b.list + i);
-      int ix[N];
-      unpack<N>(a.b.lcoord[i], ix);
-      const double Lv = L(src, p, ix, i, front);
+    auto update = [&](long long p, double Lv) {
       const double ph = a.phi[p];
       if (stage == 0) {
         a.b.p1[p] = ph + dt * Lv;
@@ -883,6 +897,38 @@ __device__ bool rk3(const LsArgs& a, LsCtx& c, double dt, bool clamp_last, LFn L
         if (clamp_last) v = fmin(fmax(v, -G), G);
         a.phi[p] = v;
       }
+    };
+    for (long long chunk = warp0; chunk < nchunk; chunk += wstride) {
+      if (SPLIT && chunk < cf) {
+        const int sub = lane / N, d = lane - sub * N;
+        const long long j = chunk * NPW + sub;
+        const bool valid = sub < NPW && j < nf;
+        long long i = 0, p = 0;
+        double mx = 0.0;
+        if (valid) {
+          i = __ldcg(a.b.slist + j);
+          p = __ldcg(a.b.list + i);
+          int ix[N];
+          unpack<N>(a.b.lcoord[i], ix);
+          mx = LAxis(src, p, ix, i, d);
+        }
+        double acc = 0.0;
+#pragma unroll
+        for (int e = 0; e < N; ++e) {
+          const double v = __shfl_sync(0xffffffffu, mx, sub * N + e);
+          acc = fma(v, v, acc);
+        }
+        if (valid && d == 0) update(p, LFinal(i, acc));
+        continue;
+      }
+      const long long j = nfe + 32 * (chunk - cf) + lane;
+      if (j >= (long long)nf + nb) continue;
+      const bool front = j < nf;
+      const long long i = __ldcg(a.b.slist + (front ? j : g.size - 1 - (j - nf)));
+      const long long p = __ldcg(a.b.list + i);
+      int ix[N];
+      unpack<N>(a.b.lcoord[i], ix);
+      update(p, L(src, p, ix, i, front));
     }
     if (!grid_barrier(a.st, c.bar, 30 + stage)) return false;
   }
@@ -913,11 +959,11 @@ __device__ bool reinitialise(const LsArgs& a, LsCtx& c) {
   const int n = __ldcg(a.b.count);
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x, gth = (long long)gridDim.x * blockDim.x;
   const double h = g.h;
-  // mixed path: FP64 within 2h of the interface (|phi_0| < 2h, i.e.
-  // |S| < 2/sqrt(5)), FP32 WENO/Godunov arithmetic further out (a 3h band
-  // measured the same error and 9% more level-set time); the two
-  // kinds go to the two ends of the stage list
-  const double near_s = 2.0 / sqrt(5.0);
+  // mixed path: FP64 within h of the interface (|phi_0| < h, i.e.
+  // |S| < 1/sqrt(2)), FP32 WENO/Godunov arithmetic further out; the two
+  // kinds go to the two ends of the stage list, the FP64 ones an axis per
+  // lane (see rk3)
+  const double near_s = 1.0 / sqrt(2.0);
   for (long long i = gtid; i < n; i += gth) {
     const long long p = __ldcg(a.b.list + i);
     const double ph = a.phi[p];
@@ -934,8 +980,20 @@ __device__ bool reinitialise(const LsArgs& a, LsCtx& c) {
     const double gr = fp64 ? godunov<double, N>(g, src, p, ix, S > 0.0) : godunov<float, N>(g, src, p, ix, S > 0.0);
     return -S * (gr - 1.0);
   };
+  // the FP64 entries of the mixed path, an axis per lane (see rk3)
+  const double inv_h = 1.0 / h;
+  const double epsw = 4.0 * WENO_EPS * h * h;
+  auto LAx = [&](const double* src, long long p, const int* ix, long long i, int d) {
+    return godunov_mx<double, N>(g, src, p, ix, d, __ldcg(a.b.S0 + i) > 0.0, inv_h, epsw);
+  };
+  auto LFin = [&](long long i, double acc) {
+    const double S = __ldcg(a.b.S0 + i);
+    return -S * (sqrt(acc) * inv_h - 1.0);
+  };
   for (int it = 0; it < K; ++it) {
-    if (!rk3<N>(a, c, dtau, it == K - 1, L)) return false;
+    if (!(a.mixed ? rk3<N, true>(a, c, dtau, it == K - 1, L, LAx, LFin)
+                  : rk3<N, false>(a, c, dtau, it == K - 1, L, LAx, LFin)))
+      return false;
   }
   return true;
 }
@@ -1220,7 +1278,9 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
       return -__ldcg(a.b.V + i) * gr;
     };
     for (int sub = 0; sub < nsub; ++sub) {
-      if (!rk3<N>(a, c, dts, sub == nsub - 1, L)) return;
+      auto LAx = [&](const double*, long long, const int*, long long, int) { return 0.0; };
+      auto LFin = [&](long long, double) { return 0.0; };
+      if (!rk3<N, false>(a, c, dts, sub == nsub - 1, L, LAx, LFin)) return;
     }
   }
   if (a.reinit) reinitialise<N>(a, c);

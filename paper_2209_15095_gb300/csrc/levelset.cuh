@@ -30,7 +30,7 @@ struct LevelsetBufs {
 LevelsetBufs levelset_carve(const GridDev& g, const std::function<char*(size_t)>& take);
 
 // mixed: FP32 WENO/Godunov arithmetic except for the reinitialisation within
-// 2h of the interface, FP32 extension sweeps and FP32 Stefan-speed
+// h of the interface, FP32 extension sweeps and FP32 Stefan-speed
 // interpolation (FP64 everywhere when false)
 cudaError_t launch_levelset_advance(const GridDev& g, const LevelsetBufs& b, DevStatus* st, const uint8_t* kind,
                                     double* phi, double* u, double dt, double mu, bool reinit, bool mixed,

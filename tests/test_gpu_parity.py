@@ -359,7 +359,7 @@ def test_two_species_competition_multistep(lib):
 
 def test_levelset_step_mixed_precision(lib):
     """FP32-mixed path: WENO5/Godunov arithmetic in FP32 except the
-    reinitialisation within 2h of the interface, extension sweeps in FP32;
+    reinitialisation within h of the interface, extension sweeps in FP32;
     against the FP64 oracle.  Bound on the extended u: each FP32 two-pass
     sweep update is a convex combination of at most 1 + N + N^2 = 13 terms,
     rounded at most 14 times (unit roundoff 2^-24), and the passes do not
