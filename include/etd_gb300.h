@@ -298,6 +298,15 @@ etd_status levelset_last_stats(etd_ctx* ctx, int* info);
  * that call would have received). */
 etd_status etd_last_stats(etd_ctx* ctx, etd_step_stats* stats);
 
+/* Limit of every bounded device wait (the grid barriers of the cooperative
+ * kernels) in this context's later launches, in seconds; 0 or less restores
+ * the default of 1 s.  A wait that reaches it stops its kernel (every CTA
+ * returns) and the next synchronising call returns ETD_ERR_TIMEOUT; the
+ * outputs of that launch are unspecified and the context stays usable.  For
+ * failure-detection tests and for callers that want an early timeout.
+ * Synchronises the stream. */
+etd_status etd_set_wait_limit(etd_ctx* ctx, double seconds);
+
 /* Wait for the stream and report any error raised on the device since the
  * last report. */
 etd_status etd_sync(etd_ctx* ctx);
@@ -328,14 +337,19 @@ const char* etd_last_error(const etd_ctx* ctx);
  *   y = phi_0(dt C) v0 + phi_1(dt C) v1 + phi_2(dt C) v2
  * on the computational points of {phi < 0}, y = 0 elsewhere.  grid, phi, v0,
  * v1, v2 and y are as for the context calls (device, full grid, FP64, owned by
- * the caller); stream is a cudaStream_t (NULL: legacy default stream).
+ * the caller); stream is a cudaStream_t (NULL: legacy default stream) of the
+ * current device (a stream of another device: ETD_ERR_ARG).
  * Scratch: one file-scope device array of ETD_NOALLOC_SCRATCH_BYTES (10 MiB)
  * that every GPU which loads the library holds until the process exits; no
  * cudaMalloc, cudaFree or other allocating call is made.  Limits: at most
  * ETD_NOALLOC_MAX_NODES grid nodes and m_max <= ETD_NOALLOC_MAX_M, else
- * ETD_ERR_WORKSPACE.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture.  Every call clears the part of the array it
+ * ETD_ERR_WORKSPACE; the largest such problem fits the array (checked when
+ * the library is compiled).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current) and keeps
+ * it for later calls; make that first call before any stream capture.  The
+ * kept address belongs to the device's primary context: after a
+ * cudaDeviceReset (or any reset of that context) the process must not call
+ * this entry point on that device again.  Every call clears the part of the array it
  * uses, then works in it; calls that overlap on the GPU (two streams, or two
  * host threads) share the array and race.  The call synchronises `stream` and
  * returns any device-side error. */

@@ -62,6 +62,7 @@ struct etd_ctx {
   bool fp32 = false;
   int last_nspecies = 0;
   int last_species0 = 0;
+  unsigned long long wait_ns = 0;  // host copy of the device-wait limit (0: default)
   std::string err;
 };
 
@@ -92,12 +93,13 @@ bool check_grid(const etd_grid* grid, GridDev& g, std::string& why) {
       why = "each axis needs 8 to 65535 nodes";
       return false;
     }
+    // checked before the product, which could otherwise wrap around
+    if (size > 2147483647LL / grid->n[d]) {
+      why = "grid larger than 2^31 - 1 nodes";
+      return false;
+    }
     g.n[d] = grid->n[d];
     size *= grid->n[d];
-  }
-  if (size > 2147483647LL) {
-    why = "grid larger than 2^31 - 1 nodes";
-    return false;
   }
   g.size = size;
   long long s = 1;
@@ -772,6 +774,21 @@ etd_status etd_apply_operator(etd_ctx* c, int species, double dt, const double* 
 etd_status etd_last_stats(etd_ctx* c, etd_step_stats* stats) {
   if (!c || !stats) return ETD_ERR_ARG;
   return copy_stats(c, stats);
+}
+
+etd_status etd_set_wait_limit(etd_ctx* c, double seconds) {
+  if (!c) return ETD_ERR_ARG;
+  if (!(seconds == seconds)) return fail(c, ETD_ERR_ARG, "wait limit is NaN");
+  // 0 or less: the default; at most ~584 years in ns
+  c->wait_ns = seconds <= 0.0 ? 0ull : (seconds >= 1.8e10 ? 18000000000000000000ull
+                                                            : (unsigned long long)(seconds * 1e9 + 0.5));
+  if (seconds > 0.0 && c->wait_ns == 0ull) c->wait_ns = 1ull;
+  cudaError_t e = cudaMemcpyAsync(&c->st->wait_ns, &c->wait_ns, sizeof(c->wait_ns), cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "wait limit write");
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
+  return ETD_OK;
 }
 
 etd_status etd_sync(etd_ctx* c) {

@@ -73,6 +73,7 @@ struct DevStatus {
   double gersh[2];      // Gershgorin bound of C per species (max row sum of |C|)
   unsigned int barrier; // grid-barrier arrival counter (reset before each cooperative launch)
   unsigned int pad2;
+  unsigned long long wait_ns;  // limit of every device wait in ns (0: BARRIER_LIMIT_NS)
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -97,9 +98,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // k * gridDim.x.  Ordering: __syncthreads orders the CTA's accesses before
 // thread 0's gpu-scope release add; the waiting thread's gpu-scope acquire
 // load and the following __syncthreads order them before every later access
-// of its CTA.  Every wait is bounded (~1 s of wall time); on timeout the
-// status word gets ERRF_TIMEOUT and the call returns false, after which the
-// kernel must return.
+// of its CTA.  Every wait is bounded: from the first unsuccessful poll, the
+// clock and the status word are checked every 16 polls; after st->wait_ns
+// (default BARRIER_LIMIT_NS, ~1 s) the status word gets ERRF_TIMEOUT and the
+// call returns false, after which the kernel must return.  A CTA that sees
+// another CTA's ERRF_TIMEOUT stops waiting too, so every CTA returns.
 constexpr unsigned long long BARRIER_LIMIT_NS = 1000000000ull;
 
 __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned& k, int site) {
@@ -110,13 +113,17 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned& k, int sit
     int ok = 1;
     red_release_add_u32(&st->barrier, 1u);
     const unsigned target = k * gridDim.x;
-    unsigned long long t0 = 0;
+    unsigned long long t0 = 0, w = 0;
     unsigned polls = 0;
     while (ld_acquire_u32(&st->barrier) < target) {
-      if (((++polls) & 255u) == 0u) {
-        unsigned long long now = global_ns();
-        if (t0 == 0) t0 = now;
-        else if (now - t0 > BARRIER_LIMIT_NS) {
+      if (polls == 0) {
+        // the limit is loaded here and first used 16 polls later, so that
+        // its load does not delay the next poll
+        t0 = global_ns();
+        w = *((volatile unsigned long long*)&st->wait_ns);
+      }
+      if (((++polls) & 15u) == 0u) {
+        if (global_ns() - t0 >= (w != 0ull ? w : BARRIER_LIMIT_NS)) {
           atomicOr(&st->err, ERRF_TIMEOUT);
           atomicExch(&st->timeout_site, site);
           ok = 0;

@@ -552,8 +552,6 @@ __global__ void __launch_bounds__(INIT_NT, 1) init_domain_kernel(const ClassifyA
 
 // ints of scratch the set-up kernel needs: one count per CTA, then two bit
 // planes (computational nodes, signs of phi) of one bit per node
-int init_scratch_ints(long long size) { return MAX_BLOCKS + 2 * (int)((size + 31) / 32); }
-
 template <int N>
 static void* init_fn() {
   return (void*)init_domain_kernel<N>;

@@ -37,7 +37,8 @@ struct MetaArgs {
   DevStatus* st;
 };
 
-int init_scratch_ints(long long size);  // per-CTA counts of the set-up kernel
+// ints of per-CTA counts and word scratch of the set-up kernel
+constexpr int init_scratch_ints(long long size) { return MAX_BLOCKS + 2 * (int)((size + 31) / 32); }
 cudaError_t launch_init_domain(const ClassifyArgs& ca, const MetaArgs& ma, int* tile_count, int* ncomp_dev,
                                cudaStream_t stream);
 

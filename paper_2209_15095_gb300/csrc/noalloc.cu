@@ -28,17 +28,44 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[ETD_NOALLOC_SCR
 
 namespace {
 
-struct NaCarver {
-  char* base;
-  size_t off = 0;
-  template <typename T>
-  T* take(size_t count) {
-    off = (off + 255) & ~size_t(255);
-    T* p = reinterpret_cast<T*>(base + off);
-    off += count * sizeof(T);
-    return p;
-  }
+// Byte offsets of the buffers in the fixed array for a grid of G nodes and
+// a basis of at most m vectors (each buffer 256-byte aligned).  constexpr, so
+// that the limits below are checked against the array size at compile time.
+struct NaLayout {
+  size_t st, stats, part, tiles, kind, idx, ncomp, diag, V, Yg, W1g, Yc, V1c, V2c, Z0, Z1, total;
 };
+constexpr size_t na_up(size_t o) { return (o + 255) & ~size_t(255); }
+constexpr NaLayout na_layout(size_t G, int m) {
+  NaLayout L{};
+  size_t o = 0;
+  L.st = o;
+  o = na_up(o + sizeof(DevStatus));
+  L.stats = o;
+  o = na_up(o + sizeof(StatsDev));
+  L.part = o;
+  o = na_up(o + sizeof(double) * 8 * MAX_BLOCKS);
+  L.tiles = o;
+  o = na_up(o + sizeof(int) * ((size_t)init_scratch_ints((long long)G) + 1));
+  L.kind = o;
+  o = na_up(o + G);
+  L.idx = o;
+  o = na_up(o + sizeof(int) * G);
+  L.ncomp = o;
+  o = na_up(o + sizeof(int));
+  L.diag = o;
+  o = na_up(o + sizeof(double) * G);
+  L.V = o;
+  o = na_up(o + sizeof(double) * G * (size_t)(m + 1));
+  size_t* vec[7] = {&L.Yg, &L.W1g, &L.Yc, &L.V1c, &L.V2c, &L.Z0, &L.Z1};
+  for (int i = 0; i < 7; ++i) {
+    *vec[i] = o;
+    o = na_up(o + sizeof(double) * G);
+  }
+  L.total = o;
+  return L;
+}
+static_assert(na_layout(ETD_NOALLOC_MAX_NODES, ETD_NOALLOC_MAX_M).total <= ETD_NOALLOC_SCRATCH_BYTES,
+              "the documented largest problem must fit the fixed scratch array");
 
 bool grid_of(const etd_grid* grid, GridDev& g) {
   if (!grid || grid->ndim < 2 || grid->ndim > 4) return false;
@@ -47,6 +74,8 @@ bool grid_of(const etd_grid* grid, GridDev& g) {
   long long size = 1;
   for (int d = 0; d < grid->ndim; ++d) {
     if (grid->n[d] < 8 || grid->n[d] > 65535) return false;
+    // no wrap-around: stop as soon as the size would pass 2^31 - 1
+    if (size > 2147483647LL / grid->n[d]) return false;
     g.n[d] = grid->n[d];
     size *= grid->n[d];
   }
@@ -81,9 +110,17 @@ extern "C" etd_status etd_phi_combination_noalloc(const etd_grid* grid, const do
   cudaStream_t st = (cudaStream_t)stream;
 
   // One-time set-up per device, with that device current: the host-side name
-  // of the array is not a device address, so look the address up.
+  // of the array is not a device address, so look the address up.  The
+  // cached address belongs to the device's primary context (see the header
+  // on resets).
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return ETD_ERR_CUDA;
+  if (st != nullptr) {
+    // the kernels run on the stream's device, the array is the current one's
+    int sdev = -1;
+    if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) return ETD_ERR_CUDA;
+    if (sdev != dev) return ETD_ERR_ARG;
+  }
   if (!g_scratch_ready[dev]) {
     void* addr = nullptr;
     if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) return ETD_ERR_CUDA;
@@ -92,26 +129,26 @@ extern "C" etd_status etd_phi_combination_noalloc(const etd_grid* grid, const do
   }
 
   // Carve the fixed array.
-  NaCarver cv{(char*)g_scratch_addr[dev]};
-  const size_t G = (size_t)g.size;
-  DevStatus* dst = cv.take<DevStatus>(1);
-  StatsDev* stats = cv.take<StatsDev>(1);
-  double* part = cv.take<double>(8 * MAX_BLOCKS);
-  int* tiles = cv.take<int>(init_scratch_ints(g.size) + 1);
-  uint8_t* kind = cv.take<uint8_t>(G);
-  int* idx = cv.take<int>(G);
-  int* ncomp = cv.take<int>(1);
-  double* diag = cv.take<double>(G);
-  double* V = cv.take<double>(G * (size_t)(m_max + 1));
-  double* Yg = cv.take<double>(G);
-  double* W1g = cv.take<double>(G);
-  double* Yc = cv.take<double>(G);
-  double* V1c = cv.take<double>(G);
-  double* V2c = cv.take<double>(G);
-  double* Z0 = cv.take<double>(G);
-  double* Z1 = cv.take<double>(G);
-  const size_t used = (cv.off + 255) & ~size_t(255);
-  if (used > NA_BYTES) return ETD_ERR_WORKSPACE;
+  const NaLayout L = na_layout((size_t)g.size, m_max);
+  if (L.total > NA_BYTES) return ETD_ERR_WORKSPACE;
+  char* base = (char*)g_scratch_addr[dev];
+  DevStatus* dst = reinterpret_cast<DevStatus*>(base + L.st);
+  StatsDev* stats = reinterpret_cast<StatsDev*>(base + L.stats);
+  double* part = reinterpret_cast<double*>(base + L.part);
+  int* tiles = reinterpret_cast<int*>(base + L.tiles);
+  uint8_t* kind = reinterpret_cast<uint8_t*>(base + L.kind);
+  int* idx = reinterpret_cast<int*>(base + L.idx);
+  int* ncomp = reinterpret_cast<int*>(base + L.ncomp);
+  double* diag = reinterpret_cast<double*>(base + L.diag);
+  double* V = reinterpret_cast<double*>(base + L.V);
+  double* Yg = reinterpret_cast<double*>(base + L.Yg);
+  double* W1g = reinterpret_cast<double*>(base + L.W1g);
+  double* Yc = reinterpret_cast<double*>(base + L.Yc);
+  double* V1c = reinterpret_cast<double*>(base + L.V1c);
+  double* V2c = reinterpret_cast<double*>(base + L.V2c);
+  double* Z0 = reinterpret_cast<double*>(base + L.Z0);
+  double* Z1 = reinterpret_cast<double*>(base + L.Z1);
+  const size_t used = L.total;
 
   // The array keeps the previous call's contents: start from zero (status,
   // node kinds, and the zero entries every stencil input needs off the

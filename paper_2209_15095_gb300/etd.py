@@ -94,6 +94,7 @@ def library():
         "levelset_advance": (I, [P, I, P, P, D, I]),
         "levelset_prepare": (I, [P, P, I]),
         "etd_sync": (I, [P]),
+        "etd_set_wait_limit": (I, [P, D]),
         "etd_last_stats": (I, [P, ctypes.POINTER(StepStats)]),
         "levelset_last_stats": (I, [P, ctypes.POINTER(I)]),
         "etd_read_domain": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), P, P, P, I]),
@@ -298,6 +299,11 @@ class Context:
 
     def sync(self):
         self._check(self.lib.etd_sync(self.ctx))
+
+    def set_wait_limit(self, seconds):
+        """Limit of every bounded device wait of later launches (<= 0: the
+        default 1 s); a wait that reaches it is reported as ETD_ERR_TIMEOUT."""
+        self._check(self.lib.etd_set_wait_limit(self.ctx, float(seconds)))
 
     def read_domain(self, species, arrays=True):
         import numpy as np

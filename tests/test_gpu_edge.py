@@ -3,8 +3,9 @@ an empty domain (no node inside), a domain whose inside nodes are all ghosts,
 a domain of 8 computational points (Krylov happy breakdown below 5 vectors),
 the largest Krylov basis (m_max = 61: an augmented matrix of 64 rows, with
 rejections at m_max), a domain reaching into the box margin (ETD_ERR_DOMAIN)
-and a non-finite field (ETD_ERR_NONFINITE): errors are reported, nothing
-hangs.  Grids whose rows are whole 32-node words (the word-parallel
+a non-finite field (ETD_ERR_NONFINITE), a device wait that reaches its
+limit (ETD_ERR_TIMEOUT) and a tolerance no substep can meet
+(ETD_ERR_KRYLOV): errors are reported, nothing hangs.  Grids whose rows are whole 32-node words (the word-parallel
 classification), down to one word per row, in 2D-4D, with their margin
 error."""
 import numpy as np
@@ -192,3 +193,60 @@ def test_word_rows_margin_is_reported(lib, shape):
     with pytest.raises(lib.EtdError) as e:
         ctx.sync()
     assert e.value.name == "ETD_ERR_DOMAIN"
+
+
+def test_device_wait_timeout_is_reported(lib):
+    """A device wait that reaches its limit: with a 1 ns limit on the grid
+    barriers, some barrier of the phi-combination gives up, every CTA
+    returns, and ETD_ERR_TIMEOUT is reported at the next synchronising call.
+    With the default limit restored, the same context gives the result of a
+    fresh context bit for bit.  No wait is unbounded, so nothing can hang."""
+    g = Grid((64, 64, 64), (-2.0,) * 3, (2.0,) * 3)
+    ph = g.radius() - 1.3
+    op = EBOperator(g, ph, 1.0)
+    rng = np.random.default_rng(41)
+    vs = [_dev(op.to_grid(rng.standard_normal(op.ncomp))) for _ in range(3)]
+    ctx = _ctx(lib, g, tol=1e-10)
+    ctx.init_domain(0, _dev(ph))
+    ctx.sync()
+    ctx.set_wait_limit(1e-9)
+    y = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    names = []
+    for _ in range(5):
+        try:
+            ctx.phi_combination(0, 0.05, *vs, y)
+            ctx.sync()
+            names.append("ok")
+        except lib.EtdError as e:
+            names.append(e.name)
+            break
+    assert names[-1] == "ETD_ERR_TIMEOUT", names
+    ctx.set_wait_limit(0)
+    ctx.phi_combination(0, 0.05, *vs, y)
+    ctx.sync()
+    ref = _ctx(lib, g, tol=1e-10)
+    ref.init_domain(0, _dev(ph))
+    y_ref = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    ref.phi_combination(0, 0.05, *vs, y_ref)
+    ref.sync()
+    assert torch.equal(y, y_ref)
+
+
+def test_krylov_failure_is_reported(lib):
+    """A tolerance that no substep can meet (1e-300 with m_max = 5 on a
+    problem far larger than the basis): the controller shrinks tau below
+    tau_min = 1e-6 and reports ETD_ERR_KRYLOV; the context stays usable."""
+    g = Grid((32, 32, 32), (-2.0,) * 3, (2.0,) * 3)
+    ph = g.radius() - 1.4
+    op = EBOperator(g, ph, 1.0)
+    rng = np.random.default_rng(43)
+    vs = [_dev(op.to_grid(rng.standard_normal(op.ncomp))) for _ in range(3)]
+    y = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    for precision in ("fp64", "mixed"):
+        ctx = _ctx(lib, g, tol=1e-300, m_max=5, precision=precision)
+        ctx.init_domain(0, _dev(ph))
+        with pytest.raises(lib.EtdError) as e:
+            ctx.phi_combination(0, 0.5, *vs, y, stats=True)
+        assert e.value.name == "ETD_ERR_KRYLOV"
+        # the domain is still set up and the context answers
+        assert ctx.read_domain(0, arrays=False)["ncomp"] == op.ncomp

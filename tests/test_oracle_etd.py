@@ -3,7 +3,8 @@ ETD3RK and ETD4RK exact for forcing quadratic in t, phi_0 alone for F = 0,
 orders 3 and 4 on a Bernoulli ODE and on a stiff EB system;
 first-order (ETD1) and second-order (ETD2, ETD2RK) convergence for a
 manufactured solution on a fixed circle, and the paper's Table 1 (ETD2 and
-ETD2RK on the peanut domain, Sec. 4.2.1) within a factor of 3."""
+ETD2RK on the peanut domain, Sec. 4.2.1) within a factor of 3; stability of
+ETD2 on the same problem for steps up to dt = 0.1 (Sec. 4.2.2, Fig. 5)."""
 import math
 import os
 
@@ -187,6 +188,72 @@ def test_table1_etd2rk_peanut_641():
     n, _, li, l2 = [r for r in _golden(GOLDEN_RK) if r[0] == 641][0]
     gi, g2 = _peanut(n, scheme="etd2rk")
     assert li / 3 <= gi <= 3 * li and l2 / 3 <= g2 <= 3 * l2
+
+
+def _peanut_stability(n, dts, t_end=0.2, tol=1e-8):
+    """l2 / l-inf errors and max |u| at t_end of ETD2 on the peanut problem
+    (Sec. 4.2.1) for each time step of `dts`, and a lower bound of the
+    spectral radius of -C (Rayleigh quotient after power iterations)."""
+    g = Grid((n, n), (-1.0, -1.0), (1.0, 1.0))
+    x, y = g.coords()
+    rho = 0.5 - np.exp(-20 * (x ** 2 + (y - 0.25) ** 2)) - np.exp(-20 * (x ** 2 + (y + 0.25) ** 2))
+
+    def phi_fn(X):
+        xx, yy = X[..., 0], X[..., 1]
+        e1 = np.exp(-20 * (xx ** 2 + (yy - 0.25) ** 2))
+        e2 = np.exp(-20 * (xx ** 2 + (yy + 0.25) ** 2))
+        return 0.5 - e1 - e2, np.stack([40 * xx * (e1 + e2), 40 * (yy - 0.25) * e1 + 40 * (yy + 0.25) * e2], -1)
+
+    op = EBOperator(g, rho, lambda X: 0.25 - X[..., 0] ** 2 - X[..., 1] ** 2, phi_fn=phi_fn, boundary_data=True)
+    X = np.stack([c.ravel()[op.index] for c in g.coords()], -1)
+    r2 = np.sum(X ** 2, -1)
+
+    def F_of(u, t):
+        return math.exp(-t) * (28 * r2 - 3) / 4 + op.boundary_rhs(lambda P: math.exp(-t) * (np.sum(P ** 2, -1) - 0.25))
+
+    v = np.random.default_rng(0).standard_normal(op.ncomp)
+    for _ in range(60):
+        v = -(op.C @ v)
+        v /= np.linalg.norm(v)
+    lam = float(v @ (-(op.C @ v)))
+    out = []
+    for dt in dts:
+        nst = int(round(t_end / dt))
+        u = etd.run_fixed_domain(op, r2 - 0.25, dt, nst, F_of, tol=tol, m_max=40)
+        e = u - math.exp(-t_end) * (r2 - 0.25)
+        out.append((math.sqrt(np.mean(e * e)), np.max(np.abs(e)), np.max(np.abs(u))))
+    return out, lam, math.exp(-t_end) * np.max(np.abs(r2 - 0.25))
+
+
+def _check_stability(dts, res, lam, umax):
+    for dt, (l2, li, um) in zip(dts, res):
+        # the explicit Euler / RK2 amplification of the stiffest mode exceeds
+        # 1 at every step of the sweep: the problem is stiff there
+        assert dt * lam > 2.0, (dt, lam)
+        # ETD2 stays bounded: error below 1% of max |u|, no growth of u
+        assert l2 <= 1e-2 * umax and li <= 2e-2 * umax, (dt, l2, li)
+        assert um <= 1.05 * umax, (dt, um)
+    # the error does not grow as dt shrinks (down to the spatial error)
+    for a, b in zip(res[:-1], res[1:]):
+        assert b[0] <= 1.05 * a[0]
+
+
+def test_stability_etd2_peanut():
+    """Stability (Sec. 4.2.2, Fig. 5): ETD2 on the peanut problem to t = 0.2
+    stays bounded for steps up to dt = 0.1, far beyond the explicit limit
+    2 / rho(C).  On h = 0.008 (251^2) here; h = 0.004 as printed is the slow
+    test below."""
+    dts = [0.1, 1e-2, 1e-3]
+    res, lam, umax = _peanut_stability(251, dts)
+    _check_stability(dts, res, lam, umax)
+
+
+@pytest.mark.slow
+def test_stability_etd2_peanut_h004():
+    """As above at the paper's h = 0.004 (501^2) with dt = 0.1 ... 1e-4."""
+    dts = [0.1, 1e-2, 1e-3, 1e-4]
+    res, lam, umax = _peanut_stability(501, dts)
+    _check_stability(dts, res, lam, umax)
 
 
 # ---- ETD3RK / ETD4RK (Sec. 3.2)

@@ -1,7 +1,8 @@
 """Pins for oracle.levelset and oracle.freeboundary: WENO5's fifth order and
 exactness on linear data, Godunov |grad phi| = 1 on a distance function,
 reinitialisation of a distance function leaving the interface in place,
-Aslam extension converging, the Stefan speed of a unit-slope profile, the
+Aslam extension converging and, on a planar front, quadratic rather than
+linear (a negative control with u_nn dropped fails the bound), the Stefan speed of a unit-slope profile, the
 advected circle's radius, and for the free-boundary disc: grid (D4) symmetry,
 radial symmetry of the front, and a monotonically growing domain."""
 import math
@@ -76,6 +77,61 @@ def test_extension_converges():
         near = (np.abs(r - R) < 2.5 * g.h) & ~comp
         errs.append(np.max(np.abs(ue - prof)[near]))
     assert errs[1] < errs[0] / 1.5
+
+
+def _planar_extension(n, ndim, prof_ab, drop_unn):
+    """Extension of u = a d + b d^2 across the planar face x = X0 of a box
+    domain (x the last axis, d = X0 - |x| the distance inside); returns the
+    errors of the extended u at the first two nodes beyond the computational
+    set on the middle line, in units of b h^2."""
+    a, b = prof_ab
+    X0 = 0.5123
+    g = Grid((n,) * ndim, (-1.0,) * ndim, (1.0,) * ndim)
+    x = g.coords()
+    phi = np.abs(x[-1]) - X0
+    for dd in range(ndim - 1):
+        phi = np.maximum(phi, np.abs(x[dd]) - 0.6)
+    d = X0 - np.abs(x[-1])
+    prof = a * d + b * d * d
+    _, _, comp = classify(g, phi)
+    ph = ls.clamp(phi, g.h)
+    T = ls.tube(ph, g.h)
+    u = np.where(comp, prof, 0.0)
+    if not drop_unn:
+        ue = ls.extend(u, ph, comp, g.h, T)
+    else:
+        # negative control built here, not in the oracle: linear
+        # extrapolation (the u_nn sweep dropped, u_nn = 0)
+        nrm = ls.normals(ph, g.h)
+        v1 = ls._all_nb(comp)
+        un = np.where(v1, ls._n_dot_grad_central(u, nrm, g.h), 0.0)
+        un = ls._sweep(un, np.zeros_like(u), nrm, g.h, T & ~v1)
+        ue = ls._sweep(u, un, nrm, g.h, T & ~comp)
+    mid = (n // 2,) * (ndim - 1)
+    i0 = int(np.where(comp[mid])[0].max())
+    return [(ue[mid + (i0 + k,)] - prof[mid + (i0 + k,)]) / (b * g.h * g.h) for k in (1, 2)]
+
+
+@pytest.mark.parametrize("ndim,n", [(2, 41), (2, 81), (2, 161), (3, 41)])
+def test_extension_quadratic_planar_front(ndim, n):
+    """Aslam's quadratic extrapolation (Sec. 4.3, Step 2) on a planar front
+    with the normal along a grid axis.  Central differences of a quadratic
+    are exact, so u_n = u' and u_nn = u'' = 2b on their valid sets and the
+    u_nn and u_n sweeps have exact steady states (a constant, a linear
+    function).  The first-order upwind u sweep then gives
+    q_i = q_{i-1} + h u'(x_i), while u(x_i) = u(x_{i-1}) + h u'(x_i) - b h^2:
+    the k-th node beyond the computational set is off by k b h^2.  Linear
+    extrapolation (u_nn dropped) freezes u_n at u'(x_{i0-1}) and is off by
+    -(k^2 + 2k) b h^2.  The finite pseudo-time moves the first two nodes by
+    less than 0.25 b h^2 (the linear variant by less than 0.7 b h^2), so
+    |e_k - k b h^2| <= 0.5 b h^2 separates the two by more than 2 b h^2."""
+    errs = _planar_extension(n, ndim, (0.5, 3.0), drop_unn=False)
+    for k, e in zip((1, 2), errs):
+        assert abs(e - k) <= 0.5, (k, e)
+    lin = _planar_extension(n, ndim, (0.5, 3.0), drop_unn=True)
+    for k, e in zip((1, 2), lin):
+        assert abs(e - k) > 2.5, (k, e)
+        assert abs(e + k * k + 2 * k) <= 1.0, (k, e)
 
 
 def test_stefan_speed_unit_slope():

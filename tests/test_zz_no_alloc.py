@@ -72,6 +72,24 @@ def test_noalloc_matches_context_path_twice():
         a, b = y.cpu().numpy(), y_ref.cpu().numpy()
         assert np.max(np.abs(a - b)) <= 1e-10 * np.max(np.abs(b))
         assert np.all(a[b == 0.0] == 0.0)
+    # the largest documented problem: 32768 nodes (32^3) with m_max = 30
+    shape, lo, hi, phi, vs = _case(3, 32, 2.0, 3)
+    dphi = torch.tensor(phi, dtype=torch.float64, device="cuda")
+    dv = [torch.tensor(v, dtype=torch.float64, device="cuda") for v in vs]
+    ctx = etd.Context(shape, lo, hi, nspecies=1, precision="fp64", tol=1e-10, m_max=30, reaction="none",
+                      beta=(1.0,))
+    y_ref = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    ctx.init_domain(0, dphi)
+    ctx.phi_combination(0, 0.05, dv[0], dv[1], dv[2], y_ref)
+    ctx.sync()
+    y = torch.full(shape, 7.0, dtype=torch.float64, device="cuda")
+    g = _grid_struct(etd, shape, lo, hi)
+    rc = f(ctypes.byref(g), dphi.data_ptr(), 1.0, 0.05, dv[0].data_ptr(), dv[1].data_ptr(), dv[2].data_ptr(),
+           y.data_ptr(), 1e-10, 30, stream.cuda_stream)
+    assert rc == 0
+    a, b = y.cpu().numpy(), y_ref.cpu().numpy()
+    assert np.max(np.abs(a - b)) <= 1e-10 * np.max(np.abs(b))
+    assert np.all(a[b == 0.0] == 0.0)
     # sizes beyond the fixed array are refused before any launch
     big = _grid_struct(etd, (40, 40, 40), (-1.0,) * 3, (1.0,) * 3)
     rc = f(ctypes.byref(big), dphi.data_ptr(), 1.0, 0.01, dv[0].data_ptr(), dv[1].data_ptr(), dv[2].data_ptr(),
