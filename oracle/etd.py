@@ -89,59 +89,67 @@ def combination(op, vs, dt, tol=1e-10, m_max=40, exact=False, forced_trace=None)
     return krylov.phipm(lambda x: dt * (C @ x), vs, tol, m_max, dt * op.gershgorin(), forced_trace=forced_trace)
 
 
-def etd1_step(op, u_n, F_n, dt, tol=1e-10, m_max=40, exact=False):
+def etd1_step(op, u_n, F_n, dt, tol=1e-10, m_max=40, exact=False, forced_trace=None):
     """One ETD1 step: U_{n+1} = phi_0(dt C) U_n + dt phi_1(dt C) F_n."""
-    return combination(op, [u_n, dt * F_n, np.zeros_like(u_n)], dt, tol, m_max, exact)
+    return combination(op, [u_n, dt * F_n, np.zeros_like(u_n)], dt, tol, m_max, exact, forced_trace)
 
 
-def etd2rk_step(op, u_n, F_of, t_n, dt, tol=1e-10, m_max=40, exact=False):
+def _ft(forced, i):
+    """Decision trace of the i-th combination of a step (None: decide)."""
+    return None if forced is None else forced[i]
+
+
+def etd2rk_step(op, u_n, F_of, t_n, dt, tol=1e-10, m_max=40, exact=False, forced_traces=None):
     """One ETD2RK step (Sec. 3.2).  F_of(U, t) -> F vector.  Returns
-    (U_{n+1}, a_n, (trace of the first combination, trace of the second))."""
+    (U_{n+1}, a_n, (trace of the first combination, trace of the second)).
+    forced_traces: None, or one decision trace per combination to replay."""
     F_n = F_of(u_n, t_n)
-    a, tr1 = etd1_step(op, u_n, F_n, dt, tol, m_max, exact)
+    a, tr1 = etd1_step(op, u_n, F_n, dt, tol, m_max, exact, _ft(forced_traces, 0))
     z = np.zeros_like(u_n)
-    d, tr2 = combination(op, [z, z, dt * (F_of(a, t_n + dt) - F_n)], dt, tol, m_max, exact)
+    d, tr2 = combination(op, [z, z, dt * (F_of(a, t_n + dt) - F_n)], dt, tol, m_max, exact, _ft(forced_traces, 1))
     return a + d, a, (tr1, tr2)
 
 
-def etd3rk_step(op, u_n, F_of, t_n, dt, tol=1e-10, m_max=40, exact=False):
-    """One ETD3RK step (Sec. 3.2).  Returns (U_{n+1}, (a_n, b_n), traces)."""
+def etd3rk_step(op, u_n, F_of, t_n, dt, tol=1e-10, m_max=40, exact=False, forced_traces=None):
+    """One ETD3RK step (Sec. 3.2).  Returns (U_{n+1}, (a_n, b_n), traces).
+    forced_traces: None, or one decision trace per combination to replay."""
     z = np.zeros_like(u_n)
     F_n = F_of(u_n, t_n)
     # a_n = U_n + dt/2 phi_1(dt C / 2)(F_n + C U_n)
-    a, tr_a = combination(op, [u_n, 0.5 * dt * F_n, z], 0.5 * dt, tol, m_max, exact)
+    a, tr_a = combination(op, [u_n, 0.5 * dt * F_n, z], 0.5 * dt, tol, m_max, exact, _ft(forced_traces, 0))
     F_a = F_of(a, t_n + 0.5 * dt)
     # b_n = U_n + dt phi_1(dt C)(C U_n + 2 F(a_n) - F_n)
-    b, tr_b = combination(op, [u_n, dt * (2.0 * F_a - F_n), z], dt, tol, m_max, exact)
+    b, tr_b = combination(op, [u_n, dt * (2.0 * F_a - F_n), z], dt, tol, m_max, exact, _ft(forced_traces, 1))
     F_b = F_of(b, t_n + dt)
     # U_{n+1} = U_n + dt phi_1 (C U_n + F_n) + dt phi_2 (-3 F_n + 4 F(a_n) - F(b_n))
     #         + dt phi_3 (2 F_n - 4 F(a_n) + 2 F(b_n)),  the paper's phi_3 = 2 x standard
     v2 = dt * (-3.0 * F_n + 4.0 * F_a - F_b)
     v3 = 2.0 * dt * (2.0 * F_n - 4.0 * F_a + 2.0 * F_b)
-    u, tr_u = combination(op, [u_n, dt * F_n, v2, v3], dt, tol, m_max, exact)
+    u, tr_u = combination(op, [u_n, dt * F_n, v2, v3], dt, tol, m_max, exact, _ft(forced_traces, 2))
     return u, (a, b), (tr_a, tr_b, tr_u)
 
 
-def etd4rk_step(op, u_n, F_of, t_n, dt, tol=1e-10, m_max=40, exact=False):
-    """One ETD4RK step (Sec. 3.2).  Returns (U_{n+1}, (a_n, b_n, c_n), traces)."""
+def etd4rk_step(op, u_n, F_of, t_n, dt, tol=1e-10, m_max=40, exact=False, forced_traces=None):
+    """One ETD4RK step (Sec. 3.2).  Returns (U_{n+1}, (a_n, b_n, c_n), traces).
+    forced_traces: None, or one decision trace per combination to replay."""
     z = np.zeros_like(u_n)
     h2 = 0.5 * dt
     F_n = F_of(u_n, t_n)
     # a_n = U_n + dt/2 phi_1(dt C / 2)(F_n + C U_n)
-    a, tr_a = combination(op, [u_n, h2 * F_n, z], h2, tol, m_max, exact)
+    a, tr_a = combination(op, [u_n, h2 * F_n, z], h2, tol, m_max, exact, _ft(forced_traces, 0))
     F_a = F_of(a, t_n + h2)
     # b_n = U_n + dt/2 phi_1(dt C / 2)(F(a_n) + C U_n)
-    b, tr_b = combination(op, [u_n, h2 * F_a, z], h2, tol, m_max, exact)
+    b, tr_b = combination(op, [u_n, h2 * F_a, z], h2, tol, m_max, exact, _ft(forced_traces, 1))
     F_b = F_of(b, t_n + h2)
     # c_n = a_n + dt/2 phi_1(dt C / 2)(2 F(b_n) - F_n + C a_n)
-    c, tr_c = combination(op, [a, h2 * (2.0 * F_b - F_n), z], h2, tol, m_max, exact)
+    c, tr_c = combination(op, [a, h2 * (2.0 * F_b - F_n), z], h2, tol, m_max, exact, _ft(forced_traces, 2))
     F_c = F_of(c, t_n + dt)
     # U_{n+1} = U_n + dt phi_1 (C U_n + F_n)
     #         + dt phi_2 (-3 F_n + 2 (F(a_n) + F(b_n)) - F(c_n))
     #         + dt phi_3 (2 F_n - 2 (F(a_n) + F(b_n)) + 2 F(c_n)),  the paper's phi_3 = 2 x standard
     v2 = dt * (-3.0 * F_n + 2.0 * (F_a + F_b) - F_c)
     v3 = 2.0 * dt * (2.0 * F_n - 2.0 * (F_a + F_b) + 2.0 * F_c)
-    u, tr_u = combination(op, [u_n, dt * F_n, v2, v3], dt, tol, m_max, exact)
+    u, tr_u = combination(op, [u_n, dt * F_n, v2, v3], dt, tol, m_max, exact, _ft(forced_traces, 3))
     return u, (a, b, c), (tr_a, tr_b, tr_c, tr_u)
 
 
@@ -150,9 +158,9 @@ def etd3_vectors(u_n, F_n, F_nm1, F_nm2, dt):
     return [u_n, dt * F_n, dt * (1.5 * F_n - 2.0 * F_nm1 + 0.5 * F_nm2), dt * (F_n - 2.0 * F_nm1 + F_nm2)]
 
 
-def etd3_step(op, u_n, F_n, F_nm1, F_nm2, dt, tol=1e-10, m_max=40, exact=False):
+def etd3_step(op, u_n, F_n, F_nm1, F_nm2, dt, tol=1e-10, m_max=40, exact=False, forced_trace=None):
     """One multistep ETD3 step.  Returns (U_{n+1}, trace)."""
-    return combination(op, etd3_vectors(u_n, F_n, F_nm1, F_nm2, dt), dt, tol, m_max, exact)
+    return combination(op, etd3_vectors(u_n, F_n, F_nm1, F_nm2, dt), dt, tol, m_max, exact, forced_trace)
 
 
 def run_fixed_domain(op, u0, dt, nsteps, F_of, tol=1e-10, m_max=40, exact=False, scheme="etd2"):

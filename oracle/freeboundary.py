@@ -53,7 +53,9 @@ class FreeBoundary:
             s.u = np.where(inside, s.u, 0.0)
             s.comp = EBOperator(grid, s.phi, s.beta).comp
 
-    def step(self, dt):
+    def step(self, dt, forced_traces=None):
+        """One free-boundary step.  forced_traces: None, or per species a
+        Krylov decision trace to replay (None for a species: decide)."""
         g = self.grid
         do_reinit = self.reinit_every > 0 and (self.k + 1) % self.reinit_every == 0
         exts = []
@@ -76,7 +78,8 @@ class FreeBoundary:
             else:
                 was = s.prev_comp.ravel()[op.index]
                 F_p = np.where(was, s.F_prev.ravel()[op.index], F_n)
-            u_new, tr = etd.etd2_step(op, u_n, F_n, F_p, dt, tol=self.tol, m_max=self.m_max)
+            ft = None if forced_traces is None else forced_traces[i]
+            u_new, tr = etd.etd2_step(op, u_n, F_n, F_p, dt, tol=self.tol, m_max=self.m_max, forced_trace=ft)
             traces.append(tr)
             new_u.append(op.to_grid(u_new))
             s.F_prev = op.to_grid(F_n)

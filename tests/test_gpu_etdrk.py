@@ -1,10 +1,10 @@
 """ETD3RK and ETD4RK on the GPU (Sec. 3.2) and the phi-combination with p = 3
 (Eq. 3.9) through the C ABI, against the FP64 oracle.
 
-1e-10 relative (FP64): the p = 3 combination (with the oracle replaying the
-GPU's decision trace where the two controllers' estimates straddle a
-threshold) and two steps of each scheme from identical inputs; 1e-5 relative
-for the FP32-mixed path.  Two species coupled through the competition
+1e-10 relative (FP64): the p = 3 combination and two steps of each scheme
+from identical inputs, the oracle replaying the GPU's decision trace (per
+stage for the Runge-Kutta schemes); 1e-5 relative for the FP32-mixed path
+against the oracle at tolerance 1e-12.  Two species coupled through the competition
 reaction, and temporal order 4 of ETD4RK on a stiff EB system against a
 tight explicit reference.
 """
@@ -19,6 +19,7 @@ from oracle import etd as oetd  # noqa: E402
 from oracle import krylov  # noqa: E402
 from oracle.eb import EBOperator  # noqa: E402
 from oracle.grid import Grid  # noqa: E402
+from _replay import forced, split_evaluations  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -146,14 +147,19 @@ def test_etd3rk_etd4rk_steps(lib, scheme, precision, tol):
     du = _dev(u0)
     dt = 0.02
     step = oetd.etd3rk_step if scheme == "etd3rk" else oetd.etd4rk_step
+    nev = 3 if scheme == "etd3rk" else 4
     F_of = lambda v, t: v * (1 - v)
     uo = op.from_grid(u0)
+    fp64 = precision == "fp64"
     for _ in range(2):
         st = ctx.step(dt, [du], stats=True)[0]
-        uo, _, traces = step(op, uo, F_of, 0.0, dt, tol=1e-12, m_max=40)
-        assert st["substeps"] >= len(traces) and len(st["trace"]) == min(st["substeps"], 64)
+        assert st["substeps"] >= nev and len(st["trace"]) == st["substeps"]
+        # FP64: the oracle at the GPU's tolerance replays each stage's
+        # decisions; mixed: against the oracle at 1e-12
+        fts = split_evaluations(st["trace"], nev) if fp64 else None
+        uo, _, traces = step(op, uo, F_of, 0.0, dt, tol=1e-10 if fp64 else 1e-12, m_max=40, forced_traces=fts)
         ug = du.cpu().numpy()
-        assert np.max(np.abs(op.from_grid(ug) - uo)) <= tol * np.max(np.abs(uo)) * 10
+        assert np.max(np.abs(op.from_grid(ug) - uo)) <= tol * np.max(np.abs(uo))
         assert np.all(ug[~op.comp] == 0.0)
 
 
@@ -259,13 +265,14 @@ def test_rk34_argument_checks(lib):
         ctx.step(0.01, [torch.zeros_like(z)])
 
 
-def _oracle_etd3(op, uo, hist, F_n, dt):
-    """One step of the oracle's multistep ETD3 with the start-up reading."""
+def _oracle_etd3(op, uo, hist, F_n, dt, tol=1e-12, ft=None):
+    """One step of the oracle's multistep ETD3 with the start-up reading
+    (ft: a decision trace to replay)."""
     hist.insert(0, F_n)
     del hist[3:]
     if len(hist) == 3:
-        return oetd.etd3_step(op, uo, hist[0], hist[1], hist[2], dt, tol=1e-12, m_max=40)[0]
-    return oetd.etd2_step(op, uo, hist[0], hist[-1], dt, tol=1e-12, m_max=40)[0]
+        return oetd.etd3_step(op, uo, hist[0], hist[1], hist[2], dt, tol=tol, m_max=40, forced_trace=ft)[0]
+    return oetd.etd2_step(op, uo, hist[0], hist[-1], dt, tol=tol, m_max=40, forced_trace=ft)[0]
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
@@ -281,11 +288,15 @@ def test_etd3_multistep_steps(lib, precision, tol):
     du = _dev(u0)
     dt = 0.02
     uo, hist = op.from_grid(u0), []
+    fp64 = precision == "fp64"
     for _ in range(4):
-        ctx.step(dt, [du])
-        uo = _oracle_etd3(op, uo, hist, uo * (1 - uo), dt)
+        st = ctx.step(dt, [du], stats=True)[0]
+        if fp64:
+            uo = _oracle_etd3(op, uo, hist, uo * (1 - uo), dt, tol=1e-10, ft=forced(st["trace"]))
+        else:
+            uo = _oracle_etd3(op, uo, hist, uo * (1 - uo), dt)
         ug = du.cpu().numpy()
-        assert np.max(np.abs(op.from_grid(ug) - uo)) <= tol * np.max(np.abs(uo)) * 10
+        assert np.max(np.abs(op.from_grid(ug) - uo)) <= tol * np.max(np.abs(uo))
         assert np.all(ug[~op.comp] == 0.0)
 
 

@@ -7,13 +7,13 @@ result in seconds, and by properties that hold at any size where it cannot.
   bit-exact, D_p and the Gershgorin bound to 1e-12.
 - One ETD step on every workload (first step: ETD1) from the workload's
   initial data: FP64 against the oracle replaying the GPU's substep and basis
-  decisions (1e-9 relative), FP32-mixed against the oracle at 1e-5; the two
+  decisions (1e-10 relative), FP32-mixed against the oracle at 1e-5; the two
   species of twoball3d coupled through the competition reaction.
 - One level-set step (advection, extension, Stefan speed) of star3d 128^3:
-  phi within 1e-9 h (FP64; FP32-mixed 1e-6 h within 2h of the front and
-  1e-4 h beyond), the extended u to 1e-9 relative.
+  phi within 1e-10 h (FP64; FP32-mixed 1e-6 h within 2h of the front and
+  1e-4 h beyond), the extended u to 1e-10 relative.
 - The explicit ETD2 step and one adjoint step of adjoint_ball3d 128^3 (beta
-  field, 299k points) against the oracle (1e-9 relative).
+  field, 299k points) against the oracle (1e-10 relative).
 - 20 free-boundary steps with the bench's schedule (start-up
   reinitialisation where the workload has one, reinitialisation every 5
   steps): the domain grows, 0 <= u <= 1 up to rounding, FP32-mixed within
@@ -123,8 +123,7 @@ def _F(w, ops, us, s):
     return oetd.reaction(w.reaction, w.rparams, [us[s]])[0]
 
 
-@pytest.mark.parametrize("name,precision", [(n, p) for n in WORKLOADS for p in ("fp64", "mixed")
-                                            if not (n == "adjoint_ball3d" and p == "mixed")])
+@pytest.mark.parametrize("name,precision", [(n, p) for n in WORKLOADS for p in ("fp64", "mixed")])
 def test_fullsize_etd_step(lib, name, precision):
     w = _workload(name)
     g, phis, ops = _ops(name)
@@ -140,7 +139,7 @@ def test_fullsize_etd_step(lib, name, precision):
         assert len(forced) == st[s]["substeps"]
         uo, _ = oetd.etd2_step(op, us0[s], F, F, w.dt, tol=tol, m_max=w.m_max, forced_trace=forced)
         ug = du[s].cpu().numpy()
-        bound = 1e-9 if precision == "fp64" else 1e-5
+        bound = 1e-10 if precision == "fp64" else 1e-5
         assert np.max(np.abs(op.from_grid(ug) - uo)) <= bound * np.max(np.abs(uo))
         assert np.all(ug[~op.comp] == 0.0)
 
@@ -167,14 +166,14 @@ def test_fullsize_levelset_step(lib, precision):
     ph_g = dph[0].cpu().numpy()
     assert ((ph_g < 0) == (ph_o < 0)).all()
     if precision == "fp64":
-        assert np.max(np.abs(ph_g - ph_o)) <= 1e-9 * g.h
+        assert np.max(np.abs(ph_g - ph_o)) <= 1e-10 * g.h
     else:
         near = np.abs(ph_o) < 2 * g.h
         assert np.max(np.abs(ph_g - ph_o)[near]) <= 1e-6 * g.h
         assert np.max(np.abs(ph_g - ph_o)) <= 1e-4 * g.h
     # FP32 extension sweeps in the mixed path: at most 11 two-pass updates of
     # at most 14 roundings each, 11 * 14 * 2^-24 = 9.2e-6 of max |u|
-    bound = 1e-9 if precision == "fp64" else 1e-5
+    bound = 1e-10 if precision == "fp64" else 1e-5
     assert np.max(np.abs(du.cpu().numpy() - ue_o)) <= bound * np.max(np.abs(ue_o))
 
 
@@ -193,13 +192,15 @@ def test_fullsize_adjoint_steps(lib):
     u_n = op.to_grid(op.from_grid(w.u0[0]))
     u_nm1 = op.to_grid(rng.uniform(0.2, 0.9, op.ncomp))
     out = torch.zeros(g.n, dtype=torch.float64, device="cuda")
-    ctx.step_explicit(0, w.dt, _dev(u_n), _dev(u_nm1), out)
+    st = ctx.step_explicit(0, w.dt, _dev(u_n), _dev(u_nm1), out, stats=True)
     pe = oadj.PhiEval(op, exact=False, tol=1e-12)
     un_c, unm1_c = op.from_grid(u_n), op.from_grid(u_nm1)
     F = oadj.reaction_ak(un_c, alpha, K)
     Fm = oadj.reaction_ak(unm1_c, alpha, K)
-    ref = pe.comb(w.dt, [un_c, w.dt * F, w.dt * (F - Fm)])
-    assert np.max(np.abs(op.from_grid(out.cpu().numpy()) - ref)) <= 1e-9 * np.max(np.abs(ref))
+    # the oracle replays the GPU's Krylov decisions of the explicit step
+    ref, _ = oetd.combination(op, [un_c, w.dt * F, w.dt * (F - Fm)], w.dt, tol=1e-12, m_max=40,
+                              forced_trace=[(t, m, 0) for t, m in st["trace"]])
+    assert np.max(np.abs(op.from_grid(out.cpu().numpy()) - ref)) <= 1e-10 * np.max(np.abs(ref))
     lam = op.to_grid(rng.standard_normal(op.ncomp))
     acc0 = op.to_grid(rng.standard_normal(op.ncomp))
     dl, da = _dev(lam), _dev(acc0)
@@ -209,11 +210,13 @@ def test_fullsize_adjoint_steps(lib):
     ctx.sync()
     to_n, to_nm1, dalpha, dbeta_o = oadj.adjoint_step(op, pe, w.dt, un_c, unm1_c, op.from_grid(lam), alpha, K, 8)
     lam_ref = to_n + op.from_grid(acc0)
-    assert np.max(np.abs(op.from_grid(dl.cpu().numpy()) - lam_ref)) <= 1e-9 * np.max(np.abs(lam_ref))
-    assert np.max(np.abs(op.from_grid(da.cpu().numpy()) - to_nm1)) <= 1e-9 * np.max(np.abs(to_nm1))
-    assert abs(ga.item() - dalpha) <= 1e-9 * abs(dalpha)
+    # both sides evaluate every phi action to tolerance 1e-12 with their own
+    # decisions: they agree to about 1e-11
+    assert np.max(np.abs(op.from_grid(dl.cpu().numpy()) - lam_ref)) <= 1e-10 * np.max(np.abs(lam_ref))
+    assert np.max(np.abs(op.from_grid(da.cpu().numpy()) - to_nm1)) <= 1e-10 * np.max(np.abs(to_nm1))
+    assert abs(ga.item() - dalpha) <= 1e-10 * abs(dalpha)
     gbo = dbeta_o.ravel()
-    assert np.max(np.abs(gb.cpu().numpy().ravel() - gbo)) <= 1e-9 * np.max(np.abs(gbo))
+    assert np.max(np.abs(gb.cpu().numpy().ravel() - gbo)) <= 1e-10 * np.max(np.abs(gbo))
 
 
 def _run_steps(lib, w, precision, nsteps, tol=None):
@@ -262,3 +265,21 @@ def test_fullsize_multistep_properties(lib, name):
             for ph, u, tol in ((ph64[0], u64[0], 1e-9), (phmx[0], umx[0], 1e-5)):
                 assert np.max(np.abs(u - np.flip(u, axis=d))) <= tol * np.max(np.abs(u))
                 assert np.max(np.abs(ph - np.flip(ph, axis=d))) <= tol * h
+
+
+def test_fullsize_star3d_mixed_operating_point(lib):
+    """The mixed operating point the bench reports (star3d 128^3, Krylov
+    tolerance 1.1e-6): 55 free-boundary steps with the bench's schedule (5
+    warm-up and 50 timed steps), against the FP64 run at the workload's
+    tolerance 1e-7: u within 1e-5 relative where both are inside, the
+    interface within 1e-2 h."""
+    w = _workload("star3d")
+    h = Grid(w.n, w.lo, w.hi).h
+    nsteps = 55
+    ph64, u64, _ = _run_steps(lib, w, "fp64", nsteps)
+    phmx, umx, _ = _run_steps(lib, w, "mixed", nsteps, tol=1.1e-6)
+    both = (ph64[0] < 0) & (phmx[0] < 0)
+    err = np.max(np.abs(u64[0] - umx[0])[both]) / np.max(np.abs(u64[0]))
+    assert err <= 1e-5, err
+    near = np.abs(ph64[0]) < h
+    assert np.max(np.abs(ph64[0] - phmx[0])[near]) <= 1e-2 * h

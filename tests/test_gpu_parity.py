@@ -2,11 +2,12 @@
 
 Bit-exact: node classification and the list of computational points.
 1e-12 relative: row diagonals D_p and the matrix-free operator.
-1e-10 relative (FP64): the phi-combination, the ETD2 step and the level-set
-step, from identical inputs.  Where the two adaptive controllers' error
-estimates straddle a threshold (a different basis size or step), the
-oracle replays the GPU's decision trace and the values are compared again.
-1e-5 relative in u for the FP32-mixed path against the FP64 oracle.
+1e-10 relative (FP64): the phi-combination, the ETD steps, the level-set
+step and whole free-boundary runs, from identical inputs, with the oracle
+replaying the GPU's Krylov decisions (substep sizes and basis sizes) where
+its own controller could straddle a threshold; the interface within
+1e-10 h.  1e-5 relative in u (and the interface within 1e-2 h) for the
+FP32-mixed path against the FP64 oracle.
 """
 import math
 
@@ -19,6 +20,7 @@ from oracle import etd as oetd  # noqa: E402
 from oracle import krylov, levelset  # noqa: E402
 from oracle.eb import EBOperator  # noqa: E402
 from oracle.grid import Grid  # noqa: E402
+from _replay import forced, split_evaluations  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -210,10 +212,16 @@ def test_etd2_step_from_state(lib, precision, tol):
     u2g = du.cpu().numpy()
     F = lambda v: v * (1 - v)
     uc0 = op.from_grid(u0)
-    u1o, _ = oetd.etd2_step(op, uc0, F(uc0), F(uc0), dt, tol=1e-12, m_max=40)
-    u2o, _ = oetd.etd2_step(op, u1o, F(u1o), F(uc0), dt, tol=1e-12, m_max=40)
+    # FP64: the oracle at the GPU's tolerance replays its substep and basis
+    # decisions; mixed: against the oracle at 1e-12
+    fp64 = precision == "fp64"
+    ot = 1e-10 if fp64 else 1e-12
+    ft1 = forced(st1[0]["trace"]) if fp64 else None
+    ft2 = forced(st2[0]["trace"]) if fp64 else None
+    u1o, _ = oetd.etd2_step(op, uc0, F(uc0), F(uc0), dt, tol=ot, m_max=40, forced_trace=ft1)
+    u2o, _ = oetd.etd2_step(op, u1o, F(u1o), F(uc0), dt, tol=ot, m_max=40, forced_trace=ft2)
     for ug, uo in ((u1g, u1o), (u2g, u2o)):
-        assert np.max(np.abs(op.from_grid(ug) - uo)) <= tol * np.max(np.abs(uo)) * 10
+        assert np.max(np.abs(op.from_grid(ug) - uo)) <= tol * np.max(np.abs(uo))
         assert np.all(ug[~op.comp] == 0.0)
 
 
@@ -233,15 +241,19 @@ def test_etd1_etd2rk_steps_from_state(lib, scheme, precision, tol):
     dt = 0.02
     F = lambda v: v * (1 - v)
     uo = op.from_grid(u0)
+    fp64 = precision == "fp64"
+    ot = 1e-10 if fp64 else 1e-12
     for _ in range(2):
         st = ctx.step(dt, [du], stats=True)[0]
         ug = du.cpu().numpy()
         if scheme == "etd1":
-            uo, _ = oetd.etd1_step(op, uo, F(uo), dt, tol=1e-12, m_max=40)
+            ft = forced(st["trace"]) if fp64 else None
+            uo, _ = oetd.etd1_step(op, uo, F(uo), dt, tol=ot, m_max=40, forced_trace=ft)
         else:
-            uo, _, _ = oetd.etd2rk_step(op, uo, lambda v, t: F(v), 0.0, dt, tol=1e-12, m_max=40)
             assert st["substeps"] >= 2 and len(st["trace"]) == st["substeps"]
-        assert np.max(np.abs(op.from_grid(ug) - uo)) <= tol * np.max(np.abs(uo)) * 10
+            fts = split_evaluations(st["trace"], 2) if fp64 else None
+            uo, _, _ = oetd.etd2rk_step(op, uo, lambda v, t: F(v), 0.0, dt, tol=ot, m_max=40, forced_traces=fts)
+        assert np.max(np.abs(op.from_grid(ug) - uo)) <= tol * np.max(np.abs(uo))
         assert np.all(ug[~op.comp] == 0.0)
 
 
@@ -303,18 +315,18 @@ def test_free_boundary_disc_multistep(lib):
     ctx.init_domain(0, dph)
     nsteps = 12
     for k in range(nsteps):
-        fb.step(w.dt)
         ctx.levelset_advance(0, dph, du, w.dt, (k + 1) % w.reinit_every == 0)
         ctx.init_domain(0, dph)
-        ctx.step(w.dt, [du])
+        st = ctx.step(w.dt, [du], stats=True)
+        # the oracle replays the GPU's Krylov decisions of the step
+        fb.step(w.dt, forced_traces=[forced(st[0]["trace"])])
     ctx.sync()
     ph_g, u_g = dph.cpu().numpy(), du.cpu().numpy()
     ph_o, u_o = fb.sp[0].phi, fb.sp[0].u
     both = (ph_g < 0) == (ph_o < 0)
     assert both.all()
-    near = np.abs(ph_o) < g.h
-    assert np.max(np.abs(ph_g - ph_o)[near]) <= 1e-2 * g.h
-    assert np.max(np.abs(u_g - u_o)) <= 1e-8 * np.max(np.abs(u_o))
+    assert np.max(np.abs(ph_g - ph_o)) <= 1e-10 * g.h
+    assert np.max(np.abs(u_g - u_o)) <= 1e-10 * np.max(np.abs(u_o))
 
 
 def test_two_species_competition_multistep(lib):
@@ -342,19 +354,19 @@ def test_two_species_competition_multistep(lib):
         ctx.levelset_prepare(dph[s], False)
         ctx.init_domain(s, dph[s])
     for k in range(nsteps):
-        fb.step(dt)
         for s in range(2):
             ctx.levelset_advance(s, dph[s], du[s], dt, (k + 1) % 5 == 0)
         for s in range(2):
             ctx.init_domain(s, dph[s])
-        ctx.step(dt, du)
+        st = ctx.step(dt, du, stats=True)
+        fb.step(dt, forced_traces=[forced(st[s]["trace"]) for s in range(2)])
     ctx.sync()
     for s in range(2):
         ph_g, u_g = dph[s].cpu().numpy(), du[s].cpu().numpy()
         ph_o, u_o = fb.sp[s].phi, fb.sp[s].u
         assert ((ph_g < 0) == (ph_o < 0)).all()
-        assert np.max(np.abs(ph_g - ph_o)) <= 1e-9 * g.h
-        assert np.max(np.abs(u_g - u_o)) <= 1e-8 * np.max(np.abs(u_o))
+        assert np.max(np.abs(ph_g - ph_o)) <= 1e-10 * g.h
+        assert np.max(np.abs(u_g - u_o)) <= 1e-10 * np.max(np.abs(u_o))
 
 
 def test_levelset_step_mixed_precision(lib):
@@ -409,18 +421,22 @@ def test_star_free_boundary_at_matched_tolerance(lib, precision):
     ctx.levelset_prepare(dph, True)
     ctx.init_domain(0, dph)
     for k in range(10):
-        fb.step(w.dt)
         ctx.levelset_advance(0, dph, du, w.dt, (k + 1) % w.reinit_every == 0)
         ctx.init_domain(0, dph)
-        ctx.step(w.dt, [du])
+        st = ctx.step(w.dt, [du], stats=True)
+        # FP64: the oracle replays the GPU's Krylov decisions; mixed: its own
+        fb.step(w.dt, forced_traces=[forced(st[0]["trace"])] if precision == "fp64" else None)
     ctx.sync()
     ph_g, u_g = dph.cpu().numpy(), du.cpu().numpy()
     ph_o, u_o = fb.sp[0].phi, fb.sp[0].u
     assert ((ph_g < 0) == (ph_o < 0)).all()
     near = np.abs(ph_o) < g.h
-    assert np.max(np.abs(ph_g - ph_o)[near]) <= (1e-6 if precision == "fp64" else 1e-2) * g.h
-    bound = 10 * w.tol if precision == "fp64" else 1e-5
-    assert np.max(np.abs(u_g - u_o)) <= bound * np.max(np.abs(u_o))
+    if precision == "fp64":
+        assert np.max(np.abs(ph_g - ph_o)) <= 1e-10 * g.h
+        assert np.max(np.abs(u_g - u_o)) <= 1e-10 * np.max(np.abs(u_o))
+    else:
+        assert np.max(np.abs(ph_g - ph_o)[near]) <= 1e-2 * g.h
+        assert np.max(np.abs(u_g - u_o)) <= 1e-5 * np.max(np.abs(u_o))
 
 
 @pytest.mark.parametrize("ndim,n", [(2, 944), (3, 139), (4, 56)])
