@@ -99,11 +99,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // thread 0's gpu-scope release add; the waiting thread's gpu-scope acquire
 // load and the following __syncthreads order them before every later access
 // of its CTA.  Every wait is bounded: from the first unsuccessful poll, the
-// clock and the status word are checked every 16 polls; after st->wait_ns
-// (default BARRIER_LIMIT_NS, ~1 s) the status word gets ERRF_TIMEOUT and the
-// call returns false, after which the kernel must return.  A CTA that sees
-// another CTA's ERRF_TIMEOUT stops waiting too, so every CTA returns.
+// clock and the status word are checked every 16 polls (every poll when the
+// limit is below 1 ms); after st->wait_ns (default BARRIER_LIMIT_NS, ~1 s)
+// the status word gets ERRF_TIMEOUT and the call returns false, after which
+// the kernel must return.  A CTA that sees another CTA's ERRF_TIMEOUT stops
+// waiting too, so every CTA returns.
 constexpr unsigned long long BARRIER_LIMIT_NS = 1000000000ull;
+constexpr unsigned long long BARRIER_SHORT_NS = 1000000ull;
 
 __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned& k, int site) {
   __shared__ int s_ok;
@@ -112,17 +114,20 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned& k, int sit
   if (threadIdx.x == 0) {
     int ok = 1;
     red_release_add_u32(&st->barrier, 1u);
+    // the limit's load is issued before the first poll and has returned by
+    // the time that poll's result is known: it adds no latency
+    unsigned long long w = *((volatile unsigned long long*)&st->wait_ns);
     const unsigned target = k * gridDim.x;
-    unsigned long long t0 = 0, w = 0;
+    unsigned long long t0 = 0;
     unsigned polls = 0;
     while (ld_acquire_u32(&st->barrier) < target) {
-      if (polls == 0) {
-        // the limit is loaded here and first used 16 polls later, so that
-        // its load does not delay the next poll
-        t0 = global_ns();
-        w = *((volatile unsigned long long*)&st->wait_ns);
-      }
-      if (((++polls) & 15u) == 0u) {
+      // an opaque update of w: its tests stay after the poll instead of
+      // being hoisted above the first one (which would wait for the load)
+      asm volatile("" : "+l"(w));
+      if (polls == 0) t0 = global_ns();
+      ++polls;
+      const bool short_limit = w != 0ull && w < BARRIER_SHORT_NS;
+      if (short_limit || (polls & 15u) == 0u) {
         if (global_ns() - t0 >= (w != 0ull ? w : BARRIER_LIMIT_NS)) {
           atomicOr(&st->err, ERRF_TIMEOUT);
           atomicExch(&st->timeout_site, site);

@@ -673,9 +673,44 @@ __device__ bool build_quads(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int n
   return true;
 }
 
+// Per launch, for the tiled Lanczos pass: the node classes tk (0 off the
+// computational set; 1 where the FP32 diagonal is the interior value Dint,
+// 2 elsewhere, with the diagonal in Dg) and the tile activity flags.  Two
+// grid barriers.  Returns false if the kernel must stop.
+template <typename T>
+__device__ bool build_tiles(const PhipmArgs<T>& a, const SpeciesDev<T>& S, const TileArgs& ta, int ncomp,
+                            float Dint, unsigned& bar) {
+  const GridDev& g = a.g;
+  const long long ptid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  // the grid size is a multiple of 16 (the last axis is)
+  uint4* tk16 = reinterpret_cast<uint4*>(ta.tk);
+  for (long long i = ptid; i < g.size / 16; i += nth) tk16[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (long long i = ptid; i < ta.ntiles; i += nth) ta.flags[i] = 0;
+  if (!grid_barrier(a.st, bar, 21)) return false;
+  auto tile_of = [&](unsigned p) {
+    const unsigned z = g.sdiv[0].div(p);
+    const unsigned rem = p - z * (unsigned)g.stride[0];
+    const unsigned y = g.sdiv[1].div(rem);
+    const unsigned x = rem - y * (unsigned)g.stride[1];
+    return ((int)(z / TL_Z) * ta.nty + (int)(y / TL_Y)) * ta.ntx + (int)(x / TL_X);
+  };
+  for (long long k = dealt_tid(); k < ncomp; k += nth) {
+    const int p = __ldg(S.idx + k);
+    const float D = __ldg(S.diagf + k);
+    const bool inner = D == Dint;
+    ta.tk[p] = inner ? 1 : 2;
+    if (!inner) ta.Dg[p] = D;
+    const int tp = tile_of((unsigned)p);
+    // one flag store per run of points in the same tile
+    if (k == 0 || tile_of((unsigned)__ldg(S.idx + k - 1)) != tp) ta.flags[tp] = 1;
+  }
+  return grid_barrier(a.st, bar, 22);
+}
+
 template <typename T, int N>
 __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int sidx, Ctl& c, unsigned& bar,
-                              int& red, double ynorm2, double vscale) {
+                              int& red, double ynorm2, double vscale, unsigned& tphase) {
   const GridDev& g = a.g;
   const int ncomp = *S.ncomp;
   const long long gtid = dealt_tid();
@@ -696,6 +731,10 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   const bool quad = sizeof(T) == 4 && split && S.qidx != nullptr && S.beta_field == nullptr &&
                     (g.n[N - 1] & 3) == 0;
   if (quad && !build_quads<T>(a, S, ncomp, c, bar, red)) return false;
+  // 3D: the Lanczos vectors by the tiled pass (one pass each)
+  const bool tiles = quad && N == 3 && a.tile[sidx].enabled != 0;
+  const float Dint = (float)((double)(2 * N) * S.beta_c);
+  if (tiles && !build_tiles<T>(a, S, a.tile[sidx], ncomp, Dint, bar)) return false;
   // the statistics accumulate over the launches of one step (zeroed by the host)
   if (blockIdx.x == 0 && threadIdx.x == 0) c.trace0 = a.stats ? a.stats->trace_len[sidx] : 0;
   double* pb = nullptr;
@@ -879,8 +918,18 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         const T* V2 = S.V + (long long)(j >= 2 ? j - 2 : 0) * vs;
         T* Vj = S.V + (long long)j * vs;
         bool quad_done = false;
+        if constexpr (sizeof(T) == 4 && N == 3) {
+          if (tiles) {
+            TileSums ts;
+            if (!tile_lanczos_pass(a.tile[sidx], g, Vj, j, ca, cb, cc, cfac, bc, Dint, a.st, tphase, ts)) return false;
+            double v[3] = {ts.d1, ts.d2, ts.d3};
+            pb = part_buf(a.part, red);
+            block_partials<3>(v, pb);
+            quad_done = true;
+          }
+        }
         if constexpr (sizeof(T) == 4) {
-          if (quad) {
+          if (quad && !quad_done) {
             const int nq = c.nquad;
             quad_pass_a(Zp, V1, V2, Vj, ca, cb, cc, S.qidx, nq, gtid, gthreads);
             if (!grid_barrier(a.st, bar, 15)) return false;
@@ -1117,10 +1166,22 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
+__global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const __grid_constant__ PhipmArgs<T> a) {
   __shared__ Ctl c;
   unsigned bar = 0;
   int red = 0;
+  // the tiled pass's two stage mbarriers (after the stages in dynamic shared
+  // memory), initialised once per launch; their parities are tracked in tphase
+  unsigned tphase = 0;
+  if (sizeof(T) == 4 && N == 3 && (a.tile[0].enabled || a.tile[1].enabled)) {
+    extern __shared__ __align__(128) unsigned char tl_smem[];
+    if (threadIdx.x == 0) {
+      mbar_init(smem_u32(tl_smem + 2 * TL_STAGE));
+      mbar_init(smem_u32(tl_smem + 2 * TL_STAGE + 8));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+  }
   double* pb = nullptr;
   const GridDev& g = a.g;
   const long long gtid = dealt_tid();
@@ -1269,7 +1330,7 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
   }
   for (int s = 0; s < a.nspecies; ++s) {
     const double vscale = fmax(fmax(sqrt(tot[s][1]), sqrt(tot[s][2])), sqrt(tot[s][3]));
-    if (!phipm_species<T, N>(a, a.sp[s], s, c, bar, red, tot[s][0], vscale)) return;
+    if (!phipm_species<T, N>(a, a.sp[s], s, c, bar, red, tot[s][0], vscale, tphase)) return;
   }
   if (!grid_barrier(a.st, bar, 2)) return;
   // ---- write back: new values at computational points, 0 elsewhere
@@ -1356,8 +1417,18 @@ cudaError_t launch_phipm(const PhipmArgs<T>& a, int nblocks, cudaStream_t stream
   if (nblocks > MAX_BLOCKS) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(&a.st->barrier, 0, sizeof(unsigned), stream);
   if (e != cudaSuccess) return e;
+  size_t dsm = 0;
+  if (sizeof(T) == 4 && a.g.ndim == 3 && (a.tile[0].enabled || a.tile[1].enabled)) {
+    dsm = TL_SMEM;
+    static bool attr_set = false;
+    if (!attr_set) {
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TL_SMEM);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+  }
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel(fn, nblocks, PH_NT, args, 0, stream);
+  return cudaLaunchCooperativeKernel(fn, nblocks, PH_NT, args, dsm, stream);
 }
 
 int phipm_max_blocks(int ndim, bool fp32) {
@@ -1366,7 +1437,13 @@ int phipm_max_blocks(int ndim, bool fp32) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, PH_NT, 0) != cudaSuccess) return 0;
+  // FP32 3D launches may take the tiled pass's dynamic shared memory
+  size_t dsm = 0;
+  if (fp32 && ndim == 3) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TL_SMEM) != cudaSuccess) return 0;
+    dsm = TL_SMEM;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, PH_NT, dsm) != cudaSuccess) return 0;
   return min(per, 1) * sms;
 }
 

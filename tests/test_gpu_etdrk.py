@@ -267,11 +267,17 @@ def test_rk34_argument_checks(lib):
 
 def _oracle_etd3(op, uo, hist, F_n, dt, tol=1e-12, ft=None):
     """One step of the oracle's multistep ETD3 with the start-up reading
-    (ft: a decision trace to replay)."""
+    (ft: a decision trace to replay).  The GPU evaluates the start-up steps
+    (ETD1, ETD2) as p = 3 combinations with v_3 = 0; a replayed trace needs
+    the same Krylov vector w_3, so the replayed start-up uses that form too
+    (the same phi-combination, Eq. 3.9)."""
     hist.insert(0, F_n)
     del hist[3:]
     if len(hist) == 3:
         return oetd.etd3_step(op, uo, hist[0], hist[1], hist[2], dt, tol=tol, m_max=40, forced_trace=ft)[0]
+    if ft is not None:
+        vs = oetd.etd2_vectors(uo, hist[0], hist[-1], dt) + [np.zeros_like(uo)]
+        return oetd.combination(op, vs, dt, tol=tol, m_max=40, forced_trace=ft)[0]
     return oetd.etd2_step(op, uo, hist[0], hist[-1], dt, tol=tol, m_max=40, forced_trace=ft)[0]
 
 

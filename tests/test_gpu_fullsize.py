@@ -283,3 +283,30 @@ def test_fullsize_star3d_mixed_operating_point(lib):
     assert err <= 1e-5, err
     near = np.abs(ph64[0]) < h
     assert np.max(np.abs(ph64[0] - phmx[0])[near]) <= 1e-2 * h
+
+
+def test_fullsize_ball512_mixed_tiled(lib):
+    """The bandwidth stress shape the bench times (ball512: a fixed ball of
+    radius 7 in a 512^3 grid, 46.3M points; the mixed Krylov launch takes
+    the tiled Lanczos pass): two ETD2 steps in FP32-mixed against the FP64
+    GPU path at the same tolerance, within 1e-5 relative in u."""
+    from paper_2209_15095_gb300 import inputs
+
+    w = inputs.ball512()
+    phi = _dev(w.phi0[0])
+    u0 = _dev(w.u0[0])
+    out = {}
+    for precision in ("fp64", "mixed"):
+        ctx = lib.Context(w.n, w.lo, w.hi, nspecies=1, precision=precision, tol=w.tol, m_max=w.m_max,
+                          reaction=w.reaction, beta=w.beta)
+        u = u0.clone()
+        ctx.init_domain(0, phi)
+        for _ in range(2):
+            st = ctx.step(w.dt, [u], stats=True)
+        out[precision] = u
+        assert st[0]["ncomp"] > 46_000_000 and st[0]["krylov_iters"] >= 10
+        del ctx
+        torch.cuda.empty_cache()
+    a, b = out["fp64"], out["mixed"]
+    err = (torch.max(torch.abs(a - b)) / torch.max(torch.abs(a))).item()
+    assert err <= 1e-5, err

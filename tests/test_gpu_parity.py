@@ -463,3 +463,35 @@ def test_phi_combination_mixed_large_layouts(lib, ndim, n):
         yg = op.from_grid(y.cpu().numpy())
         assert np.max(np.abs(yg - yo)) <= 1e-5 * np.max(np.abs(yo))
         assert np.all(y.cpu().numpy()[~op.comp] == 0.0)
+
+
+@pytest.mark.parametrize("shape", [(144, 144, 144), (131, 123, 176)])
+def test_phi_combination_mixed_tiled(lib, shape):
+    """Large 3D FP32 problems whose last axis is a multiple of 16 nodes take
+    the tiled Lanczos pass (64 x 8 x 8 tiles staged by TMA, one pass per
+    Krylov vector); (131, 123, 176) leaves partial tiles along every axis.
+    Against the FP64 oracle at 1e-5, two calls on the same context (the
+    stage barriers' parities carry over between passes and launches)."""
+    box = 2.0
+    h = 2 * box / (shape[2] - 1)
+    lo = tuple(-0.5 * h * (n - 1) for n in shape)
+    g = Grid(shape, lo, tuple(-v for v in lo))
+    x = g.coords()
+    semi = (0.43 * h * shape[0], 0.45 * h * shape[1], 0.40 * h * shape[2])
+    ph = np.sqrt(sum((x[d] / semi[d]) ** 2 for d in range(3))) - 1.0
+    op = EBOperator(g, ph, 1.0)
+    assert op.ncomp >= 1 << 18
+    ctx = _ctx(lib, g, precision="mixed", tol=1e-7, m_max=40)
+    ctx.init_domain(0, _dev(ph))
+    rng = np.random.default_rng(29)
+    u = rng.uniform(0, 1, op.ncomp)
+    dt = g.h * g.h
+    vs = [u, dt * u * (1 - u), 0.1 * dt * u * (1 - u)]
+    yo, _ = krylov.phipm(lambda v: dt * (op.C @ v), vs, 1e-12, 40, dt * op.gershgorin())
+    for _ in range(2):
+        y = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+        st = ctx.phi_combination(0, dt, *[_dev(op.to_grid(v)) for v in vs], y, stats=True)
+        assert st["krylov_iters"] >= 10
+        yg = op.from_grid(y.cpu().numpy())
+        assert np.max(np.abs(yg - yo)) <= 1e-5 * np.max(np.abs(yo))
+        assert np.all(y.cpu().numpy()[~op.comp] == 0.0)
