@@ -542,12 +542,14 @@ etd_status etd_create(const etd_grid* grid, const etd_params* params, void* work
     delete c;
     return ETD_ERR_CUDA;
   }
-  for (int sp = 0; sp < c->par.nspecies; ++sp) tile_setup(c, sp);
   c->nblocks = phipm_max_blocks(c->g.ndim, c->fp32);
   if (c->nblocks <= 0 || c->nblocks > MAX_BLOCKS) {
     delete c;
     return ETD_ERR_CUDA;
   }
+  // the tiled pass keeps each CTA's tile list (at most TL_CAP) in shared memory
+  if (c->tile_tk && tile_count(c->g) <= TL_CAP * c->nblocks)
+    for (int sp = 0; sp < c->par.nspecies; ++sp) tile_setup(c, sp);
   *out = c;
   return ETD_OK;
 }

@@ -735,6 +735,9 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   const bool tiles = quad && N == 3 && a.tile[sidx].enabled != 0;
   const float Dint = (float)((double)(2 * N) * S.beta_c);
   if (tiles && !build_tiles<T>(a, S, a.tile[sidx], ncomp, Dint, bar)) return false;
+  // this CTA's active tiles (the flags are final after build_tiles' barrier)
+  __shared__ int s_tiles[TL_CAP];
+  const int ntl = tiles ? tile_list(a.tile[sidx], s_tiles) : 0;
   // the statistics accumulate over the launches of one step (zeroed by the host)
   if (blockIdx.x == 0 && threadIdx.x == 0) c.trace0 = a.stats ? a.stats->trace_len[sidx] : 0;
   double* pb = nullptr;
@@ -921,7 +924,8 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         if constexpr (sizeof(T) == 4 && N == 3) {
           if (tiles) {
             TileSums ts;
-            if (!tile_lanczos_pass(a.tile[sidx], g, Vj, j, ca, cb, cc, cfac, bc, Dint, a.st, tphase, ts)) return false;
+            if (!tile_lanczos_pass(a.tile[sidx], g, Vj, j, ca, cb, cc, cfac, bc, Dint, a.st, tphase, s_tiles, ntl, ts))
+              return false;
             double v[3] = {ts.d1, ts.d2, ts.d3};
             pb = part_buf(a.part, red);
             block_partials<3>(v, pb);

@@ -111,11 +111,32 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, DevStat
   return true;
 }
 
-// The next active tile of this CTA at or after t (stride gridDim.x), or -1.
-__device__ __forceinline__ int tile_next(const TileArgs& ta, int t) {
-  for (; t < ta.ntiles; t += gridDim.x)
-    if (__ldcg(ta.flags + t)) return t;
-  return -1;
+// Largest number of tiles a CTA takes per pass (its list lives in shared
+// memory): tiles t = blockIdx.x + i gridDim.x, i < TL_CAP.
+constexpr int TL_CAP = 512;
+
+// This CTA's active tiles, in order, into s_list (block-wide, after the
+// flags are final).  Returns their number.
+__device__ __forceinline__ int tile_list(const TileArgs& ta, int* s_list) {
+  __shared__ int s_wc[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int base = 0;
+  for (int i0 = 0; i0 < TL_CAP; i0 += blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    const int t = blockIdx.x + i * gridDim.x;
+    const bool act = i < TL_CAP && t < ta.ntiles && __ldcg(ta.flags + t) != 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, act);
+    if (lane == 0) s_wc[wid] = __popc(bal);
+    __syncthreads();
+    int off = base;
+    for (int w = 0; w < wid; ++w) off += s_wc[w];
+    if (act) s_list[off + __popc(bal & ((1u << lane) - 1u))] = t;
+    int tot = 0;
+    for (int w = 0; w < nw; ++w) tot += s_wc[w];
+    base += tot;
+    __syncthreads();
+  }
+  return base;
 }
 
 // Issues the copies of tile t for Krylov vector j into stage s (one thread).
@@ -139,25 +160,37 @@ struct TileSums {
   double d1, d2, d3;
 };
 
+__device__ __forceinline__ float f4at(const float4& v, int l) {
+  return l == 0 ? v.x : l == 1 ? v.y : l == 2 ? v.z : v.w;
+}
+
 // One Krylov vector by the tiled pass (see the file comment): V_j at the
 // tile nodes and this thread's FP32 Dot2 sums |w_j|^2, <A w_j, w_j>,
 // <A w_j, V_{j-1}>.  The stencil sums follow stencil(): axis 0, then axis 1,
-// then the last axis.  `phase` holds the two stages' mbarrier parities
+// then the last axis.  Threads take groups of 4 nodes along the last axis
+// (16-byte shared-memory accesses); the tile's two boundary columns of the
+// grown region are taken node by node.  s_list / ntl: this CTA's active
+// tiles (tile_list).  `phase` holds the two stages' mbarrier parities
 // (identical in every thread).  Returns false if a copy timed out.
-static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const GridDev& g, float* __restrict__ Vj, int j,
-                                               float ca, float cb, float cc, float cfac, float bc, float Dint,
-                                               DevStatus* st, unsigned& phase, TileSums& out) {
+static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const GridDev& g, float* __restrict__ Vj,
+                                                      int j, float ca, float cb, float cc, float cfac, float bc,
+                                                      float Dint, DevStatus* st, unsigned& phase,
+                                                      const int* s_list, int ntl, TileSums& out) {
   extern __shared__ __align__(128) unsigned char tl_smem[];
   Acc<float> d1, d2, d3;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nx = g.n[2], ny = g.n[1], nz = g.n[0];
   const long long sy = g.stride[1], sz = g.stride[0];
-  int t = tile_next(ta, blockIdx.x);
-  int s = 0;
-  if (t >= 0 && tid == 0) tile_issue(ta, tl_smem, 0, t, j);
-  while (t >= 0) {
-    const int tn = tile_next(ta, t + gridDim.x);
-    if (tn >= 0 && tid == 0) tile_issue(ta, tl_smem, s ^ 1, tn, j);
+  constexpr int RY = TL_Y + 2, RZ = TL_Z + 2;
+  constexpr int AY = TL_AX, AZ = TL_AX * (TL_Y + 4);  // strides in sA (floats)
+  constexpr int BY = TL_AX, BZ = TL_AX * RY;          // strides in sB
+  constexpr int KY = TL_KX, KZ = TL_KX * RY;          // strides in sK (bytes)
+  constexpr int QX = TL_X / 4;                        // 4-node groups per row
+  if (ntl > 0 && tid == 0) tile_issue(ta, tl_smem, 0, s_list[0], j);
+  for (int it = 0; it < ntl; ++it) {
+    const int s = it & 1;
+    const int t = s_list[it];
+    if (it + 1 < ntl && tid == 0) tile_issue(ta, tl_smem, s ^ 1, s_list[it + 1], j);
     if (!mbar_wait(smem_u32(tl_smem + 2 * TL_STAGE + 8 * s), (phase >> s) & 1u, st)) return false;
     phase ^= 1u << s;
     float* sA = reinterpret_cast<float*>(tl_smem + s * TL_STAGE);
@@ -165,61 +198,105 @@ static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const 
     const uint8_t* sK = tl_smem + s * TL_STAGE + TL_A_BYTES + TL_B_BYTES;
     const int tx = t % ta.ntx, r = t / ta.ntx;
     const int x0 = tx * TL_X, y0 = (r % ta.nty) * TL_Y, z0 = (r / ta.nty) * TL_Z;
-    // w_j on the tile grown by one node, in place of V_{j-2} in sB
-    constexpr int RX = TL_X + 2, RY = TL_Y + 2, RZ = TL_Z + 2;
-    constexpr int AY = TL_AX, AZ = TL_AX * (TL_Y + 4);  // strides in sA
-    constexpr int BY = TL_AX, BZ = TL_AX * RY;          // strides in sB
-    for (int q = tid; q < RX * RY * RZ; q += nt) {
-      const int row = q / RX, xi = q - row * RX;  // xi = x + 1
-      const int yi = row % RY, zi = row / RY;     // yi = y + 1, zi = z + 1
-      const int iB = zi * BZ + yi * BY + xi + 3;
-      const uint8_t k = sK[zi * (TL_KX * RY) + yi * TL_KX + xi + 15];
+    // node (x, y, z) of the tile (x in [-4, 68), y, z in [-2, 10)) at
+    // sA[(z + 2) AZ + (y + 2) AY + x + 4], sB[(z + 1) BZ + (y + 1) BY + x + 4],
+    // sK[(z + 1) KZ + (y + 1) KY + x + 16]
+    auto wval = [&](float v, float sacc, float v2, unsigned k, long long p) {
+      float D = Dint;
+      if (k == 2u) D = __ldcg(ta.Dg + p);
+      const float y = cfac * (bc * sacc - D * v);
+      return j >= 2 ? ca * y + cb * v + cc * v2 : ca * y + cb * v;
+    };
+    // 1. w_j on the tile grown by one node (y, z in [-1, 9)), in place of
+    //    V_{j-2} in sB: 4-node groups for x in [0, 64) ...
+    for (int q = tid; q < QX * RY * RZ; q += nt) {
+      const int row = q / QX, x = (q - row * QX) * 4;
+      const int y = row % RY - 1, z = row / RY - 1;
+      const int iA = (z + 2) * AZ + (y + 2) * AY + x + 4;
+      const int iB = (z + 1) * BZ + (y + 1) * BY + x + 4;
+      const unsigned k4 = *reinterpret_cast<const unsigned*>(sK + (z + 1) * KZ + (y + 1) * KY + x + 16);
+      float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k4 != 0u) {
+        const float4 c = *reinterpret_cast<const float4*>(sA + iA);
+        const float4 zm = *reinterpret_cast<const float4*>(sA + iA - AZ);
+        const float4 zp = *reinterpret_cast<const float4*>(sA + iA + AZ);
+        const float4 ym = *reinterpret_cast<const float4*>(sA + iA - AY);
+        const float4 yp = *reinterpret_cast<const float4*>(sA + iA + AY);
+        const float xl = sA[iA - 1], xr = sA[iA + 4];
+        const float4 v2 = *reinterpret_cast<const float4*>(sB + iB);
+        const long long p0 = (long long)(z0 + z) * sz + (long long)(y0 + y) * sy + (x0 + x);
+        float wl[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const unsigned k = (k4 >> (8 * l)) & 0xffu;
+          wl[l] = 0.f;
+          if (k != 0u) {
+            float sacc = -0.f;  // as stencil()
+            sacc += f4at(zm, l) + f4at(zp, l);
+            sacc += f4at(ym, l) + f4at(yp, l);
+            sacc += (l == 0 ? xl : f4at(c, l - 1)) + (l == 3 ? xr : f4at(c, l + 1));
+            wl[l] = wval(f4at(c, l), sacc, f4at(v2, l), k, p0 + l);
+          }
+        }
+        w4 = make_float4(wl[0], wl[1], wl[2], wl[3]);
+      }
+      *reinterpret_cast<float4*>(sB + iB) = w4;
+    }
+    // ... and node by node for the columns x = -1 and x = 64
+    for (int q = tid; q < 2 * RY * RZ; q += nt) {
+      const int row = q >> 1, x = (q & 1) ? TL_X : -1;
+      const int y = row % RY - 1, z = row / RY - 1;
+      const int iB = (z + 1) * BZ + (y + 1) * BY + x + 4;
+      const unsigned k = sK[(z + 1) * KZ + (y + 1) * KY + x + 16];
       float w = 0.f;
-      if (k != 0) {
-        const int iA = (zi + 1) * AZ + (yi + 1) * AY + xi + 3;
-        const float v = sA[iA];
-        float sacc = -0.f;  // as stencil()
+      if (k != 0u) {
+        const int iA = (z + 2) * AZ + (y + 2) * AY + x + 4;
+        float sacc = -0.f;
         sacc += sA[iA - AZ] + sA[iA + AZ];
         sacc += sA[iA - AY] + sA[iA + AY];
         sacc += sA[iA - 1] + sA[iA + 1];
-        float D = Dint;
-        if (k == 2) {
-          const long long p = (long long)(z0 + zi - 1) * sz + (long long)(y0 + yi - 1) * sy + (x0 + xi - 1);
-          D = __ldcg(ta.Dg + p);
-        }
-        const float y = cfac * (bc * sacc - D * v);
-        w = j >= 2 ? ca * y + cb * v + cc * sB[iB] : ca * y + cb * v;
+        const long long p = (long long)(z0 + z) * sz + (long long)(y0 + y) * sy + (x0 + x);
+        w = wval(sA[iA], sacc, sB[iB], k, p);
       }
       sB[iB] = w;
     }
     __syncthreads();
-    // A w_j on the tile, the sums and V_j = w_j
-    for (int q = tid; q < TL_X * TL_Y * TL_Z; q += nt) {
-      const int x = q % TL_X, row = q / TL_X;
+    // 2. A w_j on the tile, the sums and V_j = w_j (4-node groups)
+    for (int q = tid; q < QX * TL_Y * TL_Z; q += nt) {
+      const int row = q / QX, x = (q - row * QX) * 4;
       const int y = row % TL_Y, z = row / TL_Y;
       const int iB = (z + 1) * BZ + (y + 1) * BY + x + 4;
-      const float w = sB[iB];
-      const uint8_t k = sK[(z + 1) * (TL_KX * RY) + (y + 1) * TL_KX + x + 16];
-      if (k != 0) {
-        float sacc = -0.f;
-        sacc += sB[iB - BZ] + sB[iB + BZ];
-        sacc += sB[iB - BY] + sB[iB + BY];
-        sacc += sB[iB - 1] + sB[iB + 1];
-        float D = Dint;
-        const long long p = (long long)(z0 + z) * sz + (long long)(y0 + y) * sy + (x0 + x);
-        if (k == 2) D = __ldcg(ta.Dg + p);
-        const float zz = cfac * (bc * sacc - D * w);
-        const float v1 = sA[(z + 2) * AZ + (y + 2) * AY + x + 4];
-        d1.add(w, w);
-        d2.add(zz, w);
-        d3.add(zz, v1);
+      const float4 c = *reinterpret_cast<const float4*>(sB + iB);
+      const unsigned k4 = *reinterpret_cast<const unsigned*>(sK + (z + 1) * KZ + (y + 1) * KY + x + 16);
+      const long long p0 = (long long)(z0 + z) * sz + (long long)(y0 + y) * sy + (x0 + x);
+      if (k4 != 0u) {
+        const float4 zm = *reinterpret_cast<const float4*>(sB + iB - BZ);
+        const float4 zp = *reinterpret_cast<const float4*>(sB + iB + BZ);
+        const float4 ym = *reinterpret_cast<const float4*>(sB + iB - BY);
+        const float4 yp = *reinterpret_cast<const float4*>(sB + iB + BY);
+        const float xl = sB[iB - 1], xr = sB[iB + 4];
+        const float4 v1 = *reinterpret_cast<const float4*>(sA + (z + 2) * AZ + (y + 2) * AY + x + 4);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const unsigned k = (k4 >> (8 * l)) & 0xffu;
+          if (k != 0u) {
+            float sacc = -0.f;
+            sacc += f4at(zm, l) + f4at(zp, l);
+            sacc += f4at(ym, l) + f4at(yp, l);
+            sacc += (l == 0 ? xl : f4at(c, l - 1)) + (l == 3 ? xr : f4at(c, l + 1));
+            float D = Dint;
+            if (k == 2u) D = __ldcg(ta.Dg + p0 + l);
+            const float w = f4at(c, l);
+            const float zz = cfac * (bc * sacc - D * w);
+            d1.add(w, w);
+            d2.add(zz, w);
+            d3.add(zz, f4at(v1, l));
+          }
+        }
       }
-      if (x0 + x < nx && y0 + y < ny && z0 + z < nz)
-        __stcg(Vj + (long long)(z0 + z) * sz + (long long)(y0 + y) * sy + (x0 + x), w);
+      if (x0 + x < nx && y0 + y < ny && z0 + z < nz) __stcg(reinterpret_cast<float4*>(Vj + p0), c);
     }
     __syncthreads();
-    t = tn;
-    s ^= 1;
   }
   out.d1 = d1.value();
   out.d2 = d2.value();
