@@ -60,7 +60,6 @@ struct etd_ctx {
   // FP32 3D contexts: the tiled Lanczos pass (node classes, diagonals, tile
   // flags shared by the species; tensor maps per species)
   TileArgs tile[2];
-  uint8_t* tile_tk = nullptr;
   float* tile_Dg = nullptr;
   uint8_t* tile_flags = nullptr;
   // adjoint (species 0): phi actions, quadrature vectors, face weights
@@ -177,8 +176,7 @@ bool check_params(const etd_params* p, std::string& why) {
 }
 
 // The tiled Lanczos pass: FP32 vectors, 3D, the last axis a multiple of 16
-// (16-byte rows of the class array for the tensor maps), and a grid large
-// enough for the split passes.
+// nodes, and a grid large enough for the split passes.
 bool tile_capable(const GridDev& g, const etd_params& p) {
   return p.precision == ETD_PRECISION_MIXED && g.ndim == 3 && g.n[2] % 16 == 0 && g.size >= (1ll << 18);
 }
@@ -203,11 +201,11 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // Tensor maps of the tiled pass for species s (V as x, y, z, basis slot;
-// the classes as x, y, z).  Leaves the pass disabled if encoding fails.
+// the diagonals as x, y, z).  Leaves the pass disabled if encoding fails.
 void tile_setup(etd_ctx* c, int s) {
   TileArgs& t = c->tile[s];
   memset(&t, 0, sizeof(t));
-  if (!c->tile_tk) return;
+  if (!c->tile_Dg) return;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return;
   const GridDev& g = c->g;
@@ -217,9 +215,9 @@ void tile_setup(etd_ctx* c, int s) {
   const cuuint32_t boxA[4] = {TL_AX, TL_Y + 4, TL_Z + 4, 1};
   const cuuint32_t boxB[4] = {TL_AX, TL_Y + 2, TL_Z + 2, 1};
   const cuuint32_t one[4] = {1, 1, 1, 1};
-  const cuuint64_t dimK[3] = {nx, ny, nz};
-  const cuuint64_t strK[2] = {nx, nx * ny};
-  const cuuint32_t boxK[3] = {TL_KX, TL_Y + 2, TL_Z + 2};
+  const cuuint64_t dimD[3] = {nx, ny, nz};
+  const cuuint64_t strD[2] = {nx * 4, nx * ny * 4};
+  const cuuint32_t boxD[3] = {TL_AX, TL_Y + 2, TL_Z + 2};
   if (enc(&t.tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->sp[s].V, dimV, strV, boxA, one,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -228,7 +226,7 @@ void tile_setup(etd_ctx* c, int s) {
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return;
-  if (enc(&t.tmK, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, c->tile_tk, dimK, strK, boxK, one,
+  if (enc(&t.tmD, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->tile_Dg, dimD, strD, boxD, one,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return;
@@ -236,7 +234,6 @@ void tile_setup(etd_ctx* c, int s) {
   t.nty = (g.n[1] + TL_Y - 1) / TL_Y;
   t.ntz = (g.n[0] + TL_Z - 1) / TL_Z;
   t.ntiles = tile_count(g);
-  t.tk = c->tile_tk;
   t.Dg = c->tile_Dg;
   t.flags = c->tile_flags;
   t.enabled = 1;
@@ -288,11 +285,9 @@ size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
     if (c) c->sp[sp] = b;
   }
   if (tile_capable(g, p)) {
-    uint8_t* tk = cv.take<uint8_t>(G);
     float* Dg = cv.take<float>(G);
     uint8_t* fl = cv.take<uint8_t>((size_t)tile_count(g));
     if (c) {
-      c->tile_tk = tk;
       c->tile_Dg = Dg;
       c->tile_flags = fl;
     }
@@ -548,7 +543,7 @@ etd_status etd_create(const etd_grid* grid, const etd_params* params, void* work
     return ETD_ERR_CUDA;
   }
   // the tiled pass keeps each CTA's tile list (at most TL_CAP) in shared memory
-  if (c->tile_tk && tile_count(c->g) <= TL_CAP * c->nblocks)
+  if (c->tile_Dg && tile_count(c->g) <= TL_CAP * c->nblocks)
     for (int sp = 0; sp < c->par.nspecies; ++sp) tile_setup(c, sp);
   *out = c;
   return ETD_OK;

@@ -673,19 +673,18 @@ __device__ bool build_quads(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int n
   return true;
 }
 
-// Per launch, for the tiled Lanczos pass: the node classes tk (0 off the
-// computational set; 1 where the FP32 diagonal is the interior value Dint,
-// 2 elsewhere, with the diagonal in Dg) and the tile activity flags.  Two
-// grid barriers.  Returns false if the kernel must stop.
+// Per launch, for the tiled Lanczos pass: the FP32 diagonals on the grid
+// (D_p at the computational points, 0 elsewhere) and the tile activity
+// flags.  Two grid barriers.  Returns false if the kernel must stop.
 template <typename T>
 __device__ bool build_tiles(const PhipmArgs<T>& a, const SpeciesDev<T>& S, const TileArgs& ta, int ncomp,
-                            float Dint, unsigned& bar) {
+                            unsigned& bar) {
   const GridDev& g = a.g;
   const long long ptid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   // the grid size is a multiple of 16 (the last axis is)
-  uint4* tk16 = reinterpret_cast<uint4*>(ta.tk);
-  for (long long i = ptid; i < g.size / 16; i += nth) tk16[i] = make_uint4(0u, 0u, 0u, 0u);
+  float4* d4 = reinterpret_cast<float4*>(ta.Dg);
+  for (long long i = ptid; i < g.size / 4; i += nth) __stcg(d4 + i, make_float4(0.f, 0.f, 0.f, 0.f));
   for (long long i = ptid; i < ta.ntiles; i += nth) ta.flags[i] = 0;
   if (!grid_barrier(a.st, bar, 21)) return false;
   auto tile_of = [&](unsigned p) {
@@ -697,10 +696,7 @@ __device__ bool build_tiles(const PhipmArgs<T>& a, const SpeciesDev<T>& S, const
   };
   for (long long k = dealt_tid(); k < ncomp; k += nth) {
     const int p = __ldg(S.idx + k);
-    const float D = __ldg(S.diagf + k);
-    const bool inner = D == Dint;
-    ta.tk[p] = inner ? 1 : 2;
-    if (!inner) ta.Dg[p] = D;
+    ta.Dg[p] = __ldg(S.diagf + k);
     const int tp = tile_of((unsigned)p);
     // one flag store per run of points in the same tile
     if (k == 0 || tile_of((unsigned)__ldg(S.idx + k - 1)) != tp) ta.flags[tp] = 1;
@@ -733,8 +729,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   if (quad && !build_quads<T>(a, S, ncomp, c, bar, red)) return false;
   // 3D: the Lanczos vectors by the tiled pass (one pass each)
   const bool tiles = quad && N == 3 && a.tile[sidx].enabled != 0;
-  const float Dint = (float)((double)(2 * N) * S.beta_c);
-  if (tiles && !build_tiles<T>(a, S, a.tile[sidx], ncomp, Dint, bar)) return false;
+  if (tiles && !build_tiles<T>(a, S, a.tile[sidx], ncomp, bar)) return false;
   // this CTA's active tiles (the flags are final after build_tiles' barrier)
   __shared__ int s_tiles[TL_CAP];
   const int ntl = tiles ? tile_list(a.tile[sidx], s_tiles) : 0;
@@ -924,7 +919,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         if constexpr (sizeof(T) == 4 && N == 3) {
           if (tiles) {
             TileSums ts;
-            if (!tile_lanczos_pass(a.tile[sidx], g, Vj, j, ca, cb, cc, cfac, bc, Dint, a.st, tphase, s_tiles, ntl, ts))
+            if (!tile_lanczos_pass(a.tile[sidx], g, Vj, j, ca, cb, cc, cfac, bc, a.st, tphase, s_tiles, ntl, ts))
               return false;
             double v[3] = {ts.d1, ts.d2, ts.d3};
             pb = part_buf(a.part, red);

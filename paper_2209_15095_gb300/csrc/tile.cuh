@@ -5,18 +5,17 @@
 // stored Z_{j-1} = A V_{j-1} and then Z_j = A V_j: 8 vector accesses per
 // point and Krylov vector.  Here Z_{j-1} is recomputed from V_{j-1} in shared
 // memory: per 64 x 8 x 8 tile of the grid, TMA copies V_{j-1} on the tile
-// grown by two nodes, V_{j-2} and the node classes on the tile grown by one;
+// grown by two nodes, V_{j-2} and the row diagonals on the tile grown by one;
 // A V_{j-1} and w_j = ca A V_{j-1} + cb V_{j-1} + cc V_{j-2} are formed on the
 // tile grown by one (w_j = 0 off the computational set), then A w_j and the
 // three sums on the tile, and V_j = w_j is stored.  HBM traffic per point is
-// about 3 vectors (V_{j-1}, V_{j-2} read, V_j written) and a class byte; the
-// halos come from L2.  Two stages: the next tile's copies are in flight while
-// this one is computed.
+// 3 vectors (V_{j-1}, V_{j-2} read, V_j written) and the diagonal; the halos
+// come from L2.  Two stages: the next tile's copies are in flight while this
+// one is computed.
 //
-// Node classes (per launch, from the domain set-up): tk = 0 off the
-// computational set, 1 at a computational node whose diagonal is the
-// interior value 2 N beta, 2 at one with any other diagonal, which is then
-// read from the full-grid array Dg.
+// The diagonals (per launch, from the domain set-up): Dg = D_p (FP32) at the
+// computational points and 0 elsewhere, so that Dg != 0 marks the
+// computational set (D_p >= the row's interior faces' beta > 0).
 #pragma once
 #include <cuda.h>
 
@@ -26,25 +25,23 @@ namespace etd {
 
 constexpr int TL_X = 64, TL_Y = 8, TL_Z = 8;   // tile (x the last, fastest axis)
 constexpr int TL_AX = TL_X + 8;                 // x extent of the staged rows (16-byte aligned start x0 - 4)
-constexpr int TL_KX = TL_X + 32;                // x extent of the staged class rows (start x0 - 16)
 constexpr int TL_A_BYTES = TL_AX * (TL_Y + 4) * (TL_Z + 4) * 4;  // V_{j-1}, two-node halo
 constexpr int TL_B_BYTES = TL_AX * (TL_Y + 2) * (TL_Z + 2) * 4;  // V_{j-2}, one-node halo
-constexpr int TL_K_BYTES = TL_KX * (TL_Y + 2) * (TL_Z + 2);      // classes, one-node halo
-constexpr int TL_STAGE = TL_A_BYTES + TL_B_BYTES + TL_K_BYTES;
+constexpr int TL_D_BYTES = TL_B_BYTES;                           // diagonals, one-node halo
+constexpr int TL_STAGE = TL_A_BYTES + TL_B_BYTES + TL_D_BYTES;
 constexpr int TL_SMEM = 2 * TL_STAGE + 128;  // two stages and the two mbarriers
-static_assert(TL_A_BYTES % 128 == 0 && TL_B_BYTES % 128 == 0 && TL_K_BYTES % 128 == 0, "stage alignment");
+static_assert(TL_A_BYTES % 128 == 0 && TL_B_BYTES % 128 == 0, "stage alignment");
 
 // Everything the tiled pass needs: the tensor maps (V as a 4D array x, y,
-// z, basis slot with the two box sizes; the classes as a 3D uint8 array),
-// the class and diagonal arrays and the tile grid with its activity flags.
+// z, basis slot with the two box sizes; the diagonals as a 3D array), the
+// diagonal array and the tile grid with its activity flags.
 struct TileArgs {
   CUtensorMap tmA;  // V, box TL_AX x (TL_Y + 4) x (TL_Z + 4) x 1
   CUtensorMap tmB;  // V, box TL_AX x (TL_Y + 2) x (TL_Z + 2) x 1
-  CUtensorMap tmK;  // tk, box TL_KX x (TL_Y + 2) x (TL_Z + 2)
+  CUtensorMap tmD;  // Dg, box TL_AX x (TL_Y + 2) x (TL_Z + 2)
   int enabled;
   int ntx, nty, ntz, ntiles;
-  uint8_t* tk;     // full grid
-  float* Dg;       // full grid (read where tk == 2)
+  float* Dg;       // full grid: D_p at the computational points, 0 elsewhere
   uint8_t* flags;  // per tile: any computational node
 };
 
@@ -140,20 +137,20 @@ __device__ __forceinline__ int tile_list(const TileArgs& ta, int* s_list) {
 }
 
 // Issues the copies of tile t for Krylov vector j into stage s (one thread).
-// The copies of V_{j-2} are skipped for j == 1 (its coefficient is 0).
+// The copies of V_{j-2} are skipped for j == 1 (its coefficient is 0).  The
+// stage was written by generic stores (w_j in place of V_{j-2}): a proxy
+// fence on shared memory orders them before the copies.
 __device__ __forceinline__ void tile_issue(const TileArgs& ta, unsigned char* base, int s, int t, int j) {
   unsigned char* stg = base + s * TL_STAGE;
   const uint32_t bar = smem_u32(base + 2 * TL_STAGE + 8 * s);
   const int tx = t % ta.ntx, r = t / ta.ntx;
   const int ty = r % ta.nty, tz = r / ta.nty;
   const int x0 = tx * TL_X, y0 = ty * TL_Y, z0 = tz * TL_Z;
-  // the TMA reads data written by generic stores before the last grid
-  // barrier, and overwrites a stage that generic stores wrote
-  asm volatile("fence.proxy.async;" ::: "memory");
-  mbar_expect_tx(bar, TL_A_BYTES + (j >= 2 ? TL_B_BYTES : 0) + TL_K_BYTES);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(bar, TL_A_BYTES + (j >= 2 ? TL_B_BYTES : 0) + TL_D_BYTES);
   tma_load_4d(smem_u32(stg), &ta.tmA, x0 - 4, y0 - 2, z0 - 2, j - 1, bar);
   if (j >= 2) tma_load_4d(smem_u32(stg + TL_A_BYTES), &ta.tmB, x0 - 4, y0 - 1, z0 - 1, j - 2, bar);
-  tma_load_3d(smem_u32(stg + TL_A_BYTES + TL_B_BYTES), &ta.tmK, x0 - 16, y0 - 1, z0 - 1, bar);
+  tma_load_3d(smem_u32(stg + TL_A_BYTES + TL_B_BYTES), &ta.tmD, x0 - 4, y0 - 1, z0 - 1, bar);
 }
 
 struct TileSums {
@@ -168,14 +165,14 @@ __device__ __forceinline__ float f4at(const float4& v, int l) {
 // tile nodes and this thread's FP32 Dot2 sums |w_j|^2, <A w_j, w_j>,
 // <A w_j, V_{j-1}>.  The stencil sums follow stencil(): axis 0, then axis 1,
 // then the last axis.  Threads take groups of 4 nodes along the last axis
-// (16-byte shared-memory accesses); the tile's two boundary columns of the
-// grown region are taken node by node.  s_list / ntl: this CTA's active
-// tiles (tile_list).  `phase` holds the two stages' mbarrier parities
-// (identical in every thread).  Returns false if a copy timed out.
+// (16-byte shared-memory accesses); the grown region's two boundary columns
+// are taken node by node.  s_list / ntl: this CTA's active tiles
+// (tile_list).  `phase` holds the two stages' mbarrier parities (identical in
+// every thread).  Returns false if a copy timed out.
 static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const GridDev& g, float* __restrict__ Vj,
                                                       int j, float ca, float cb, float cc, float cfac, float bc,
-                                                      float Dint, DevStatus* st, unsigned& phase,
-                                                      const int* s_list, int ntl, TileSums& out) {
+                                                      DevStatus* st, unsigned& phase, const int* s_list, int ntl,
+                                                      TileSums& out) {
   extern __shared__ __align__(128) unsigned char tl_smem[];
   Acc<float> d1, d2, d3;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -183,9 +180,11 @@ static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const 
   const long long sy = g.stride[1], sz = g.stride[0];
   constexpr int RY = TL_Y + 2, RZ = TL_Z + 2;
   constexpr int AY = TL_AX, AZ = TL_AX * (TL_Y + 4);  // strides in sA (floats)
-  constexpr int BY = TL_AX, BZ = TL_AX * RY;          // strides in sB
-  constexpr int KY = TL_KX, KZ = TL_KX * RY;          // strides in sK (bytes)
+  constexpr int BY = TL_AX, BZ = TL_AX * RY;          // strides in sB and sD
   constexpr int QX = TL_X / 4;                        // 4-node groups per row
+  // the copies read vectors written by generic stores before the last grid
+  // barrier: one global proxy fence per pass (by the issuing thread)
+  if (tid == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
   if (ntl > 0 && tid == 0) tile_issue(ta, tl_smem, 0, s_list[0], j);
   for (int it = 0; it < ntl; ++it) {
     const int s = it & 1;
@@ -193,30 +192,28 @@ static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const 
     if (it + 1 < ntl && tid == 0) tile_issue(ta, tl_smem, s ^ 1, s_list[it + 1], j);
     if (!mbar_wait(smem_u32(tl_smem + 2 * TL_STAGE + 8 * s), (phase >> s) & 1u, st)) return false;
     phase ^= 1u << s;
-    float* sA = reinterpret_cast<float*>(tl_smem + s * TL_STAGE);
+    const float* sA = reinterpret_cast<const float*>(tl_smem + s * TL_STAGE);
     float* sB = reinterpret_cast<float*>(tl_smem + s * TL_STAGE + TL_A_BYTES);
-    const uint8_t* sK = tl_smem + s * TL_STAGE + TL_A_BYTES + TL_B_BYTES;
+    const float* sD = reinterpret_cast<const float*>(tl_smem + s * TL_STAGE + TL_A_BYTES + TL_B_BYTES);
     const int tx = t % ta.ntx, r = t / ta.ntx;
     const int x0 = tx * TL_X, y0 = (r % ta.nty) * TL_Y, z0 = (r / ta.nty) * TL_Z;
-    // node (x, y, z) of the tile (x in [-4, 68), y, z in [-2, 10)) at
-    // sA[(z + 2) AZ + (y + 2) AY + x + 4], sB[(z + 1) BZ + (y + 1) BY + x + 4],
-    // sK[(z + 1) KZ + (y + 1) KY + x + 16]
-    auto wval = [&](float v, float sacc, float v2, unsigned k, long long p) {
-      float D = Dint;
-      if (k == 2u) D = __ldcg(ta.Dg + p);
+    // node (x, y, z) of the tile (x in [-4, 68)) at sA[(z + 2) AZ + (y + 2) AY
+    // + x + 4] (y, z in [-2, 10)) and sB, sD[(z + 1) BZ + (y + 1) BY + x + 4]
+    // (y, z in [-1, 9))
+    auto wval = [&](float v, float sacc, float v2, float D) {
       const float y = cfac * (bc * sacc - D * v);
       return j >= 2 ? ca * y + cb * v + cc * v2 : ca * y + cb * v;
     };
-    // 1. w_j on the tile grown by one node (y, z in [-1, 9)), in place of
-    //    V_{j-2} in sB: 4-node groups for x in [0, 64) ...
+    // 1. w_j on the tile grown by one node, in place of V_{j-2} in sB:
+    //    4-node groups for x in [0, 64) ...
     for (int q = tid; q < QX * RY * RZ; q += nt) {
       const int row = q / QX, x = (q - row * QX) * 4;
       const int y = row % RY - 1, z = row / RY - 1;
       const int iA = (z + 2) * AZ + (y + 2) * AY + x + 4;
       const int iB = (z + 1) * BZ + (y + 1) * BY + x + 4;
-      const unsigned k4 = *reinterpret_cast<const unsigned*>(sK + (z + 1) * KZ + (y + 1) * KY + x + 16);
+      const float4 D4 = *reinterpret_cast<const float4*>(sD + iB);
       float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (k4 != 0u) {
+      if (D4.x != 0.f || D4.y != 0.f || D4.z != 0.f || D4.w != 0.f) {
         const float4 c = *reinterpret_cast<const float4*>(sA + iA);
         const float4 zm = *reinterpret_cast<const float4*>(sA + iA - AZ);
         const float4 zp = *reinterpret_cast<const float4*>(sA + iA + AZ);
@@ -224,19 +221,15 @@ static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const 
         const float4 yp = *reinterpret_cast<const float4*>(sA + iA + AY);
         const float xl = sA[iA - 1], xr = sA[iA + 4];
         const float4 v2 = *reinterpret_cast<const float4*>(sB + iB);
-        const long long p0 = (long long)(z0 + z) * sz + (long long)(y0 + y) * sy + (x0 + x);
         float wl[4];
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
-          const unsigned k = (k4 >> (8 * l)) & 0xffu;
-          wl[l] = 0.f;
-          if (k != 0u) {
-            float sacc = -0.f;  // as stencil()
-            sacc += f4at(zm, l) + f4at(zp, l);
-            sacc += f4at(ym, l) + f4at(yp, l);
-            sacc += (l == 0 ? xl : f4at(c, l - 1)) + (l == 3 ? xr : f4at(c, l + 1));
-            wl[l] = wval(f4at(c, l), sacc, f4at(v2, l), k, p0 + l);
-          }
+          const float D = f4at(D4, l);
+          float sacc = -0.f;  // as stencil()
+          sacc += f4at(zm, l) + f4at(zp, l);
+          sacc += f4at(ym, l) + f4at(yp, l);
+          sacc += (l == 0 ? xl : f4at(c, l - 1)) + (l == 3 ? xr : f4at(c, l + 1));
+          wl[l] = D != 0.f ? wval(f4at(c, l), sacc, f4at(v2, l), D) : 0.f;
         }
         w4 = make_float4(wl[0], wl[1], wl[2], wl[3]);
       }
@@ -247,16 +240,15 @@ static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const 
       const int row = q >> 1, x = (q & 1) ? TL_X : -1;
       const int y = row % RY - 1, z = row / RY - 1;
       const int iB = (z + 1) * BZ + (y + 1) * BY + x + 4;
-      const unsigned k = sK[(z + 1) * KZ + (y + 1) * KY + x + 16];
+      const float D = sD[iB];
       float w = 0.f;
-      if (k != 0u) {
+      if (D != 0.f) {
         const int iA = (z + 2) * AZ + (y + 2) * AY + x + 4;
         float sacc = -0.f;
         sacc += sA[iA - AZ] + sA[iA + AZ];
         sacc += sA[iA - AY] + sA[iA + AY];
         sacc += sA[iA - 1] + sA[iA + 1];
-        const long long p = (long long)(z0 + z) * sz + (long long)(y0 + y) * sy + (x0 + x);
-        w = wval(sA[iA], sacc, sB[iB], k, p);
+        w = wval(sA[iA], sacc, sB[iB], D);
       }
       sB[iB] = w;
     }
@@ -267,9 +259,8 @@ static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const 
       const int y = row % TL_Y, z = row / TL_Y;
       const int iB = (z + 1) * BZ + (y + 1) * BY + x + 4;
       const float4 c = *reinterpret_cast<const float4*>(sB + iB);
-      const unsigned k4 = *reinterpret_cast<const unsigned*>(sK + (z + 1) * KZ + (y + 1) * KY + x + 16);
-      const long long p0 = (long long)(z0 + z) * sz + (long long)(y0 + y) * sy + (x0 + x);
-      if (k4 != 0u) {
+      const float4 D4 = *reinterpret_cast<const float4*>(sD + iB);
+      if (D4.x != 0.f || D4.y != 0.f || D4.z != 0.f || D4.w != 0.f) {
         const float4 zm = *reinterpret_cast<const float4*>(sB + iB - BZ);
         const float4 zp = *reinterpret_cast<const float4*>(sB + iB + BZ);
         const float4 ym = *reinterpret_cast<const float4*>(sB + iB - BY);
@@ -278,14 +269,12 @@ static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const 
         const float4 v1 = *reinterpret_cast<const float4*>(sA + (z + 2) * AZ + (y + 2) * AY + x + 4);
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
-          const unsigned k = (k4 >> (8 * l)) & 0xffu;
-          if (k != 0u) {
+          const float D = f4at(D4, l);
+          if (D != 0.f) {
             float sacc = -0.f;
             sacc += f4at(zm, l) + f4at(zp, l);
             sacc += f4at(ym, l) + f4at(yp, l);
             sacc += (l == 0 ? xl : f4at(c, l - 1)) + (l == 3 ? xr : f4at(c, l + 1));
-            float D = Dint;
-            if (k == 2u) D = __ldcg(ta.Dg + p0 + l);
             const float w = f4at(c, l);
             const float zz = cfac * (bc * sacc - D * w);
             d1.add(w, w);
@@ -294,7 +283,8 @@ static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const 
           }
         }
       }
-      if (x0 + x < nx && y0 + y < ny && z0 + z < nz) __stcg(reinterpret_cast<float4*>(Vj + p0), c);
+      if (x0 + x < nx && y0 + y < ny && z0 + z < nz)
+        __stcg(reinterpret_cast<float4*>(Vj + (long long)(z0 + z) * sz + (long long)(y0 + y) * sy + (x0 + x)), c);
     }
     __syncthreads();
   }
