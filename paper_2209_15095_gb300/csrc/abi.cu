@@ -62,6 +62,8 @@ struct etd_ctx {
   TileArgs tile[2];
   float* tile_Dg = nullptr;
   uint8_t* tile_flags = nullptr;
+  int* tile_list = nullptr;
+  int* tile_cnt = nullptr;
   // adjoint (species 0): phi actions, quadrature vectors, face weights
   double* adj[8] = {nullptr};
   double* facew = nullptr;
@@ -236,6 +238,8 @@ void tile_setup(etd_ctx* c, int s) {
   t.ntiles = tile_count(g);
   t.Dg = c->tile_Dg;
   t.flags = c->tile_flags;
+  t.list = c->tile_list;
+  t.cnt = c->tile_cnt;
   t.enabled = 1;
 }
 
@@ -287,9 +291,13 @@ size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
   if (tile_capable(g, p)) {
     float* Dg = cv.take<float>(G);
     uint8_t* fl = cv.take<uint8_t>((size_t)tile_count(g));
+    int* tl = cv.take<int>((size_t)tile_count(g));
+    int* tc = cv.take<int>(MAX_BLOCKS);
     if (c) {
       c->tile_Dg = Dg;
       c->tile_flags = fl;
+      c->tile_list = tl;
+      c->tile_cnt = tc;
     }
   }
   LevelsetBufs lb = levelset_carve(g, [&](size_t bytes) { return cv.take<char>(bytes); });

@@ -674,11 +674,14 @@ __device__ bool build_quads(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int n
 }
 
 // Per launch, for the tiled Lanczos pass: the FP32 diagonals on the grid
-// (D_p at the computational points, 0 elsewhere) and the tile activity
-// flags.  Two grid barriers.  Returns false if the kernel must stop.
+// (D_p at the computational points, 0 elsewhere), the tile activity flags
+// and the ordered list of active tiles (CTA b compacts the tiles of its
+// contiguous range after the other CTAs' counts).  Four grid barriers.
+// *ntotal: the number of active tiles.  Returns false if the kernel must
+// stop.
 template <typename T>
 __device__ bool build_tiles(const PhipmArgs<T>& a, const SpeciesDev<T>& S, const TileArgs& ta, int ncomp,
-                            unsigned& bar) {
+                            unsigned& bar, int* ntotal) {
   const GridDev& g = a.g;
   const long long ptid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
@@ -701,7 +704,51 @@ __device__ bool build_tiles(const PhipmArgs<T>& a, const SpeciesDev<T>& S, const
     // one flag store per run of points in the same tile
     if (k == 0 || tile_of((unsigned)__ldg(S.idx + k - 1)) != tp) ta.flags[tp] = 1;
   }
-  return grid_barrier(a.st, bar, 22);
+  if (!grid_barrier(a.st, bar, 22)) return false;
+  // the ordered list: counts per CTA range, then writes at the CTA's offset
+  __shared__ int s_wc[32], s_off;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int range = (ta.ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int t0 = (int)blockIdx.x * range, t1 = min(ta.ntiles, t0 + range);
+  int cnt = 0;
+  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) cnt += __ldcg(ta.flags + t) ? 1 : 0;
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if (lane == 0) s_wc[wid] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int w = 0; w < nw; ++w) tot += s_wc[w];
+    ta.cnt[blockIdx.x] = tot;
+  }
+  if (!grid_barrier(a.st, bar, 23)) return false;
+  if (threadIdx.x == 0) {
+    int off = 0, tot = 0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      const int x = __ldcg(ta.cnt + b);
+      if (b < (int)blockIdx.x) off += x;
+      tot += x;
+    }
+    s_off = off;
+    *ntotal = tot;
+  }
+  __syncthreads();
+  int base = s_off;
+  for (int tb = t0; tb < t1; tb += blockDim.x) {
+    const int t = tb + threadIdx.x;
+    const bool act = t < t1 && __ldcg(ta.flags + t) != 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, act);
+    __syncthreads();  // s_wc of the previous round is read
+    if (lane == 0) s_wc[wid] = __popc(bal);
+    __syncthreads();
+    int off = base, tot = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < wid) off += s_wc[w];
+      tot += s_wc[w];
+    }
+    if (act) ta.list[off + __popc(bal & ((1u << lane) - 1u))] = t;
+    base += tot;
+  }
+  return grid_barrier(a.st, bar, 24);
 }
 
 template <typename T, int N>
@@ -729,10 +776,11 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   if (quad && !build_quads<T>(a, S, ncomp, c, bar, red)) return false;
   // 3D: the Lanczos vectors by the tiled pass (one pass each)
   const bool tiles = quad && N == 3 && a.tile[sidx].enabled != 0;
-  if (tiles && !build_tiles<T>(a, S, a.tile[sidx], ncomp, bar)) return false;
-  // this CTA's active tiles (the flags are final after build_tiles' barrier)
+  __shared__ int s_ntiles;
+  if (tiles && !build_tiles<T>(a, S, a.tile[sidx], ncomp, bar, &s_ntiles)) return false;
+  // this CTA's tiles (the list is final after build_tiles' last barrier)
   __shared__ int s_tiles[TL_CAP];
-  const int ntl = tiles ? tile_list(a.tile[sidx], s_tiles) : 0;
+  const int ntl = tiles ? tile_list(a.tile[sidx], s_ntiles, s_tiles) : 0;
   // the statistics accumulate over the launches of one step (zeroed by the host)
   if (blockIdx.x == 0 && threadIdx.x == 0) c.trace0 = a.stats ? a.stats->trace_len[sidx] : 0;
   double* pb = nullptr;

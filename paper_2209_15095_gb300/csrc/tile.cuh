@@ -43,6 +43,8 @@ struct TileArgs {
   int ntx, nty, ntz, ntiles;
   float* Dg;       // full grid: D_p at the computational points, 0 elsewhere
   uint8_t* flags;  // per tile: any computational node
+  int* list;       // the active tiles in order (ntiles entries)
+  int* cnt;        // per CTA: active tiles in its range (MAX_BLOCKS entries)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -109,31 +111,19 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, DevStat
 }
 
 // Largest number of tiles a CTA takes per pass (its list lives in shared
-// memory): tiles t = blockIdx.x + i gridDim.x, i < TL_CAP.
+// memory).
 constexpr int TL_CAP = 512;
 
-// This CTA's active tiles, in order, into s_list (block-wide, after the
-// flags are final).  Returns their number.
-__device__ __forceinline__ int tile_list(const TileArgs& ta, int* s_list) {
-  __shared__ int s_wc[32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int base = 0;
-  for (int i0 = 0; i0 < TL_CAP; i0 += blockDim.x) {
-    const int i = i0 + threadIdx.x;
-    const int t = blockIdx.x + i * gridDim.x;
-    const bool act = i < TL_CAP && t < ta.ntiles && __ldcg(ta.flags + t) != 0;
-    const unsigned bal = __ballot_sync(0xffffffffu, act);
-    if (lane == 0) s_wc[wid] = __popc(bal);
-    __syncthreads();
-    int off = base;
-    for (int w = 0; w < wid; ++w) off += s_wc[w];
-    if (act) s_list[off + __popc(bal & ((1u << lane) - 1u))] = t;
-    int tot = 0;
-    for (int w = 0; w < nw; ++w) tot += s_wc[w];
-    base += tot;
-    __syncthreads();
-  }
-  return base;
+// This CTA's tiles: entries blockIdx.x + i gridDim.x of the ordered list of
+// active tiles (consecutive CTAs take consecutive tiles, so the tiles in
+// flight at a time are neighbours and share their halos in L2).  Returns
+// their number.
+__device__ __forceinline__ int tile_list(const TileArgs& ta, int ntotal, int* s_list) {
+  const int n = ntotal > (int)blockIdx.x ? (ntotal - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  for (int i = threadIdx.x; i < n && i < TL_CAP; i += blockDim.x)
+    s_list[i] = __ldcg(ta.list + blockIdx.x + (long long)i * gridDim.x);
+  __syncthreads();
+  return n < TL_CAP ? n : TL_CAP;
 }
 
 // Issues the copies of tile t for Krylov vector j into stage s (one thread).
@@ -165,15 +155,17 @@ __device__ __forceinline__ float f4at(const float4& v, int l) {
 // tile nodes and this thread's FP32 Dot2 sums |w_j|^2, <A w_j, w_j>,
 // <A w_j, V_{j-1}>.  The stencil sums follow stencil(): axis 0, then axis 1,
 // then the last axis.  Threads take groups of 4 nodes along the last axis
-// (16-byte shared-memory accesses); the grown region's two boundary columns
-// are taken node by node.  s_list / ntl: this CTA's active tiles
-// (tile_list).  `phase` holds the two stages' mbarrier parities (identical in
-// every thread).  Returns false if a copy timed out.
+// (16-byte shared-memory accesses), in step 1 two groups' loads issued
+// before either is computed; the grown region's two boundary columns are
+// taken node by node.  s_list / ntl: this CTA's tiles
+// (tile_list).  `phase` holds the two stages' mbarrier parities (identical
+// in every thread).  Returns false if a copy timed out.
 static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const GridDev& g, float* __restrict__ Vj,
                                                       int j, float ca, float cb, float cc, float cfac, float bc,
                                                       DevStatus* st, unsigned& phase, const int* s_list, int ntl,
                                                       TileSums& out) {
   extern __shared__ __align__(128) unsigned char tl_smem[];
+  static_assert(TL_X == 64 && TL_Y == 8 && TL_Z == 8, "the offsets below assume 64 x 8 x 8 tiles");
   Acc<float> d1, d2, d3;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nx = g.n[2], ny = g.n[1], nz = g.n[0];
@@ -182,6 +174,36 @@ static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const 
   constexpr int AY = TL_AX, AZ = TL_AX * (TL_Y + 4);  // strides in sA (floats)
   constexpr int BY = TL_AX, BZ = TL_AX * RY;          // strides in sB and sD
   constexpr int QX = TL_X / 4;                        // 4-node groups per row
+  constexpr int N1 = QX * RY * RZ;                    // groups of the grown tile (1600)
+  constexpr int N2 = QX * TL_Y * TL_Z;                // groups of the tile (1024)
+  // node (x, y, z) of the tile (x in [-4, 68)) at sA[(z + 2) AZ + (y + 2) AY
+  // + x + 4] (y, z in [-2, 10)) and sB, sD[(z + 1) BZ + (y + 1) BY + x + 4]
+  // (y, z in [-1, 9)).  This thread's work: step 1 groups q = tid + 512 u
+  // (u < 4), the boundary-column node q = tid (< 200), step 2 groups (u < 2).
+  // step 1 group u of this thread: offsets in sA and sB (-1: none)
+  auto grp1 = [&](int u, int& iA, int& iB) {
+    const int q = tid + u * nt, row = q / QX, x = (q - row * QX) * 4;
+    const int y = row % RY - 1, z = row / RY - 1;
+    iA = q < N1 ? (z + 2) * AZ + (y + 2) * AY + x + 4 : -1;
+    iB = (z + 1) * BZ + (y + 1) * BY + x + 4;
+  };
+  int ah, bh;
+  {
+    const int row = tid >> 1, x = (tid & 1) ? TL_X : -1;
+    const int y = row % RY - 1, z = row / RY - 1;
+    ah = tid < 2 * RY * RZ ? (z + 2) * AZ + (y + 2) * AY + x + 4 : -1;
+    bh = (z + 1) * BZ + (y + 1) * BY + x + 4;
+  }
+  // (the tile-relative grid offset fits 32 bits: z <= 7 and nz >= 8)
+  int b2[2], a2[2], o2[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int q = tid + u * nt, row = q / QX, x = (q - row * QX) * 4;
+    const int y = row % TL_Y, z = row / TL_Y;
+    b2[u] = q < N2 ? (z + 1) * BZ + (y + 1) * BY + x + 4 : -1;
+    a2[u] = (z + 2) * AZ + (y + 2) * AY + x + 4;
+    o2[u] = (int)((long long)z * sz + (long long)y * sy + x);
+  }
   // the copies read vectors written by generic stores before the last grid
   // barrier: one global proxy fence per pass (by the issuing thread)
   if (tid == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -197,94 +219,95 @@ static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const 
     const float* sD = reinterpret_cast<const float*>(tl_smem + s * TL_STAGE + TL_A_BYTES + TL_B_BYTES);
     const int tx = t % ta.ntx, r = t / ta.ntx;
     const int x0 = tx * TL_X, y0 = (r % ta.nty) * TL_Y, z0 = (r / ta.nty) * TL_Z;
-    // node (x, y, z) of the tile (x in [-4, 68)) at sA[(z + 2) AZ + (y + 2) AY
-    // + x + 4] (y, z in [-2, 10)) and sB, sD[(z + 1) BZ + (y + 1) BY + x + 4]
-    // (y, z in [-1, 9))
     auto wval = [&](float v, float sacc, float v2, float D) {
       const float y = cfac * (bc * sacc - D * v);
       return j >= 2 ? ca * y + cb * v + cc * v2 : ca * y + cb * v;
     };
     // 1. w_j on the tile grown by one node, in place of V_{j-2} in sB:
-    //    4-node groups for x in [0, 64) ...
-    for (int q = tid; q < QX * RY * RZ; q += nt) {
-      const int row = q / QX, x = (q - row * QX) * 4;
-      const int y = row % RY - 1, z = row / RY - 1;
-      const int iA = (z + 2) * AZ + (y + 2) * AY + x + 4;
-      const int iB = (z + 1) * BZ + (y + 1) * BY + x + 4;
-      const float4 D4 = *reinterpret_cast<const float4*>(sD + iB);
-      float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (D4.x != 0.f || D4.y != 0.f || D4.z != 0.f || D4.w != 0.f) {
-        const float4 c = *reinterpret_cast<const float4*>(sA + iA);
-        const float4 zm = *reinterpret_cast<const float4*>(sA + iA - AZ);
-        const float4 zp = *reinterpret_cast<const float4*>(sA + iA + AZ);
-        const float4 ym = *reinterpret_cast<const float4*>(sA + iA - AY);
-        const float4 yp = *reinterpret_cast<const float4*>(sA + iA + AY);
-        const float xl = sA[iA - 1], xr = sA[iA + 4];
-        const float4 v2 = *reinterpret_cast<const float4*>(sB + iB);
+    //    4-node groups for x in [0, 64), two at a time ...
+#pragma unroll 1
+    for (int u0 = 0; u0 < 4; u0 += 2) {
+      float4 D4[2], c[2], zm[2], zp[2], ym[2], yp[2], v2[2];
+      float xl[2], xr[2];
+      int gA[2], gB[2];
+      grp1(u0, gA[0], gB[0]);
+      grp1(u0 + 1, gA[1], gB[1]);
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const int iA = gA[v], iB = gB[v];
+        if (iA < 0) continue;
+        D4[v] = *reinterpret_cast<const float4*>(sD + iB);
+        c[v] = *reinterpret_cast<const float4*>(sA + iA);
+        zm[v] = *reinterpret_cast<const float4*>(sA + iA - AZ);
+        zp[v] = *reinterpret_cast<const float4*>(sA + iA + AZ);
+        ym[v] = *reinterpret_cast<const float4*>(sA + iA - AY);
+        yp[v] = *reinterpret_cast<const float4*>(sA + iA + AY);
+        xl[v] = sA[iA - 1];
+        xr[v] = sA[iA + 4];
+        v2[v] = *reinterpret_cast<const float4*>(sB + iB);
+      }
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        if (gA[v] < 0) continue;
         float wl[4];
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
-          const float D = f4at(D4, l);
+          const float D = f4at(D4[v], l);
           float sacc = -0.f;  // as stencil()
+          sacc += f4at(zm[v], l) + f4at(zp[v], l);
+          sacc += f4at(ym[v], l) + f4at(yp[v], l);
+          sacc += (l == 0 ? xl[v] : f4at(c[v], l - 1)) + (l == 3 ? xr[v] : f4at(c[v], l + 1));
+          wl[l] = D != 0.f ? wval(f4at(c[v], l), sacc, f4at(v2[v], l), D) : 0.f;
+        }
+        *reinterpret_cast<float4*>(sB + gB[v]) = make_float4(wl[0], wl[1], wl[2], wl[3]);
+      }
+    }
+    // ... and node by node for the columns x = -1 and x = 64
+    if (ah >= 0) {
+      const float D = sD[bh];
+      float w = 0.f;
+      if (D != 0.f) {
+        float sacc = -0.f;
+        sacc += sA[ah - AZ] + sA[ah + AZ];
+        sacc += sA[ah - AY] + sA[ah + AY];
+        sacc += sA[ah - 1] + sA[ah + 1];
+        w = wval(sA[ah], sacc, sB[bh], D);
+      }
+      sB[bh] = w;
+    }
+    __syncthreads();
+    // 2. A w_j on the tile, the sums and V_j = w_j (one group at a time: the
+    //    4 x 3 Dot2 chains of a group already run side by side)
+    const long long tbase = (long long)z0 * sz + (long long)y0 * sy + x0;
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int iB = b2[v];
+      if (iB < 0) continue;
+      const float4 c = *reinterpret_cast<const float4*>(sB + iB);
+      const float4 D4 = *reinterpret_cast<const float4*>(sD + iB);
+      const float4 zm = *reinterpret_cast<const float4*>(sB + iB - BZ);
+      const float4 zp = *reinterpret_cast<const float4*>(sB + iB + BZ);
+      const float4 ym = *reinterpret_cast<const float4*>(sB + iB - BY);
+      const float4 yp = *reinterpret_cast<const float4*>(sB + iB + BY);
+      const float xl = sB[iB - 1], xr = sB[iB + 4];
+      const float4 v1 = *reinterpret_cast<const float4*>(sA + a2[v]);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const float D = f4at(D4, l);
+        if (D != 0.f) {
+          float sacc = -0.f;
           sacc += f4at(zm, l) + f4at(zp, l);
           sacc += f4at(ym, l) + f4at(yp, l);
           sacc += (l == 0 ? xl : f4at(c, l - 1)) + (l == 3 ? xr : f4at(c, l + 1));
-          wl[l] = D != 0.f ? wval(f4at(c, l), sacc, f4at(v2, l), D) : 0.f;
-        }
-        w4 = make_float4(wl[0], wl[1], wl[2], wl[3]);
-      }
-      *reinterpret_cast<float4*>(sB + iB) = w4;
-    }
-    // ... and node by node for the columns x = -1 and x = 64
-    for (int q = tid; q < 2 * RY * RZ; q += nt) {
-      const int row = q >> 1, x = (q & 1) ? TL_X : -1;
-      const int y = row % RY - 1, z = row / RY - 1;
-      const int iB = (z + 1) * BZ + (y + 1) * BY + x + 4;
-      const float D = sD[iB];
-      float w = 0.f;
-      if (D != 0.f) {
-        const int iA = (z + 2) * AZ + (y + 2) * AY + x + 4;
-        float sacc = -0.f;
-        sacc += sA[iA - AZ] + sA[iA + AZ];
-        sacc += sA[iA - AY] + sA[iA + AY];
-        sacc += sA[iA - 1] + sA[iA + 1];
-        w = wval(sA[iA], sacc, sB[iB], D);
-      }
-      sB[iB] = w;
-    }
-    __syncthreads();
-    // 2. A w_j on the tile, the sums and V_j = w_j (4-node groups)
-    for (int q = tid; q < QX * TL_Y * TL_Z; q += nt) {
-      const int row = q / QX, x = (q - row * QX) * 4;
-      const int y = row % TL_Y, z = row / TL_Y;
-      const int iB = (z + 1) * BZ + (y + 1) * BY + x + 4;
-      const float4 c = *reinterpret_cast<const float4*>(sB + iB);
-      const float4 D4 = *reinterpret_cast<const float4*>(sD + iB);
-      if (D4.x != 0.f || D4.y != 0.f || D4.z != 0.f || D4.w != 0.f) {
-        const float4 zm = *reinterpret_cast<const float4*>(sB + iB - BZ);
-        const float4 zp = *reinterpret_cast<const float4*>(sB + iB + BZ);
-        const float4 ym = *reinterpret_cast<const float4*>(sB + iB - BY);
-        const float4 yp = *reinterpret_cast<const float4*>(sB + iB + BY);
-        const float xl = sB[iB - 1], xr = sB[iB + 4];
-        const float4 v1 = *reinterpret_cast<const float4*>(sA + (z + 2) * AZ + (y + 2) * AY + x + 4);
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-          const float D = f4at(D4, l);
-          if (D != 0.f) {
-            float sacc = -0.f;
-            sacc += f4at(zm, l) + f4at(zp, l);
-            sacc += f4at(ym, l) + f4at(yp, l);
-            sacc += (l == 0 ? xl : f4at(c, l - 1)) + (l == 3 ? xr : f4at(c, l + 1));
-            const float w = f4at(c, l);
-            const float zz = cfac * (bc * sacc - D * w);
-            d1.add(w, w);
-            d2.add(zz, w);
-            d3.add(zz, f4at(v1, l));
-          }
+          const float w = f4at(c, l);
+          const float zz = cfac * (bc * sacc - D * w);
+          d1.add(w, w);
+          d2.add(zz, w);
+          d3.add(zz, f4at(v1, l));
         }
       }
-      if (x0 + x < nx && y0 + y < ny && z0 + z < nz)
-        __stcg(reinterpret_cast<float4*>(Vj + (long long)(z0 + z) * sz + (long long)(y0 + y) * sy + (x0 + x)), c);
+      const int zr = iB / BZ - 1, yr = (iB - (zr + 1) * BZ) / BY - 1;
+      if (x0 < nx && y0 + yr < ny && z0 + zr < nz) __stcg(reinterpret_cast<float4*>(Vj + tbase + o2[v]), c);
     }
     __syncthreads();
   }
