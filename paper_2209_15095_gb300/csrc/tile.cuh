@@ -211,7 +211,6 @@ static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const 
   for (int it = 0; it < ntl; ++it) {
     const int s = it & 1;
     const int t = s_list[it];
-    if (it + 1 < ntl && tid == 0) tile_issue(ta, tl_smem, s ^ 1, s_list[it + 1], j);
     if (!mbar_wait(smem_u32(tl_smem + 2 * TL_STAGE + 8 * s), (phase >> s) & 1u, st)) return false;
     phase ^= 1u << s;
     const float* sA = reinterpret_cast<const float*>(tl_smem + s * TL_STAGE);
@@ -276,6 +275,11 @@ static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const 
       sB[bh] = w;
     }
     __syncthreads();
+    // the next tile's copies, into the other stage (free since the previous
+    // tile's end): they land while step 2 runs.  Issued here rather than
+    // before step 1 because the shared-memory proxy fence waits for the
+    // issuing thread's global stores, none of which are in flight now.
+    if (it + 1 < ntl && tid == 0) tile_issue(ta, tl_smem, s ^ 1, s_list[it + 1], j);
     // 2. A w_j on the tile, the sums and V_j = w_j (one group at a time: the
     //    4 x 3 Dot2 chains of a group already run side by side)
     const long long tbase = (long long)z0 * sz + (long long)y0 * sy + x0;
@@ -306,8 +310,8 @@ static __device__ __noinline__ bool tile_lanczos_pass(const TileArgs& ta, const 
           d3.add(zz, f4at(v1, l));
         }
       }
-      const int zr = iB / BZ - 1, yr = (iB - (zr + 1) * BZ) / BY - 1;
-      if (x0 < nx && y0 + yr < ny && z0 + zr < nz) __stcg(reinterpret_cast<float4*>(Vj + tbase + o2[v]), c);
+      const int zr = iB / BZ - 1, yr = (iB - (zr + 1) * BZ) / BY - 1, xg = iB - (zr + 1) * BZ - (yr + 1) * BY - 4;
+      if (x0 + xg < nx && y0 + yr < ny && z0 + zr < nz) __stcg(reinterpret_cast<float4*>(Vj + tbase + o2[v]), c);
     }
     __syncthreads();
   }
