@@ -1,6 +1,4 @@
 // C ABI: context, workspace carving, argument checks and launches.
-#include <cudaTypedefs.h>
-
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -57,13 +55,6 @@ struct etd_ctx {
   double* pout = nullptr;  // 2 doubles: Poisson solve iterations and residual
   SpeciesBufs sp[2];
   LevelsetBufs ls;
-  // FP32 3D contexts: the tiled Lanczos pass (node classes, diagonals, tile
-  // flags shared by the species; tensor maps per species)
-  TileArgs tile[2];
-  float* tile_Dg = nullptr;
-  uint8_t* tile_flags = nullptr;
-  int* tile_list = nullptr;
-  int* tile_cnt = nullptr;
   // adjoint (species 0): phi actions, quadrature vectors, face weights
   double* adj[8] = {nullptr};
   double* facew = nullptr;
@@ -177,72 +168,6 @@ bool check_params(const etd_params* p, std::string& why) {
   return true;
 }
 
-// The tiled Lanczos pass: FP32 vectors, 3D, the last axis a multiple of 16
-// nodes, and a grid large enough for the split passes.
-bool tile_capable(const GridDev& g, const etd_params& p) {
-  return p.precision == ETD_PRECISION_MIXED && g.ndim == 3 && g.n[2] % 16 == 0 && g.size >= (1ll << 18);
-}
-
-int tile_count(const GridDev& g) {
-  return ((g.n[2] + TL_X - 1) / TL_X) * ((g.n[1] + TL_Y - 1) / TL_Y) * ((g.n[0] + TL_Z - 1) / TL_Z);
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-  }
-  return fn;
-}
-
-// Tensor maps of the tiled pass for species s (V as x, y, z, basis slot;
-// the diagonals as x, y, z).  Leaves the pass disabled if encoding fails.
-void tile_setup(etd_ctx* c, int s) {
-  TileArgs& t = c->tile[s];
-  memset(&t, 0, sizeof(t));
-  if (!c->tile_Dg) return;
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) return;
-  const GridDev& g = c->g;
-  const cuuint64_t nx = g.n[2], ny = g.n[1], nz = g.n[0];
-  const cuuint64_t dimV[4] = {nx, ny, nz, (cuuint64_t)(c->par.m_max + 1)};
-  const cuuint64_t strV[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
-  const cuuint32_t boxA[4] = {TL_AX, TL_Y + 4, TL_Z + 4, 1};
-  const cuuint32_t boxB[4] = {TL_AX, TL_Y + 2, TL_Z + 2, 1};
-  const cuuint32_t one[4] = {1, 1, 1, 1};
-  const cuuint64_t dimD[3] = {nx, ny, nz};
-  const cuuint64_t strD[2] = {nx * 4, nx * ny * 4};
-  const cuuint32_t boxD[3] = {TL_AX, TL_Y + 2, TL_Z + 2};
-  if (enc(&t.tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->sp[s].V, dimV, strV, boxA, one,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return;
-  if (enc(&t.tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->sp[s].V, dimV, strV, boxB, one,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return;
-  if (enc(&t.tmD, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->tile_Dg, dimD, strD, boxD, one,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return;
-  t.ntx = (g.n[2] + TL_X - 1) / TL_X;
-  t.nty = (g.n[1] + TL_Y - 1) / TL_Y;
-  t.ntz = (g.n[0] + TL_Z - 1) / TL_Z;
-  t.ntiles = tile_count(g);
-  t.Dg = c->tile_Dg;
-  t.flags = c->tile_flags;
-  t.list = c->tile_list;
-  t.cnt = c->tile_cnt;
-  t.enabled = 1;
-}
-
 size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
   Carver cv{base};
   const size_t G = (size_t)g.size;
@@ -287,18 +212,6 @@ size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
       b.qk = cv.take<int>(G / 4 + 1);
     }
     if (c) c->sp[sp] = b;
-  }
-  if (tile_capable(g, p)) {
-    float* Dg = cv.take<float>(G);
-    uint8_t* fl = cv.take<uint8_t>((size_t)tile_count(g));
-    int* tl = cv.take<int>((size_t)tile_count(g));
-    int* tc = cv.take<int>(MAX_BLOCKS);
-    if (c) {
-      c->tile_Dg = Dg;
-      c->tile_flags = fl;
-      c->tile_list = tl;
-      c->tile_cnt = tc;
-    }
   }
   LevelsetBufs lb = levelset_carve(g, [&](size_t bytes) { return cv.take<char>(bytes); });
   if (c) c->ls = lb;
@@ -431,14 +344,10 @@ etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int spec
   const bool all = mode == MODE_ETD2 || mode == MODE_RK2 || mode == MODE_STAGE;
   if (all) {
     a.nspecies = c->par.nspecies;
-    for (int s = 0; s < a.nspecies; ++s) {
-      a.sp[s] = species_dev<T>(c, s, u[s], mode == MODE_RK2 ? 1 : 0);
-      if (sizeof(T) == 4) a.tile[s] = c->tile[s];
-    }
+    for (int s = 0; s < a.nspecies; ++s) a.sp[s] = species_dev<T>(c, s, u[s], mode == MODE_RK2 ? 1 : 0);
   } else {
     a.nspecies = 1;
     a.sp[0] = species_dev<T>(c, species, u[0]);
-    if (sizeof(T) == 4) a.tile[0] = c->tile[species];
     for (int i = 0; i <= p; ++i) a.given[i] = given[i];
   }
   if (mode == MODE_EXPLICIT) {
@@ -550,9 +459,6 @@ etd_status etd_create(const etd_grid* grid, const etd_params* params, void* work
     delete c;
     return ETD_ERR_CUDA;
   }
-  // the tiled pass keeps each CTA's tile list (at most TL_CAP) in shared memory
-  if (c->tile_Dg && tile_count(c->g) <= TL_CAP * c->nblocks)
-    for (int sp = 0; sp < c->par.nspecies; ++sp) tile_setup(c, sp);
   *out = c;
   return ETD_OK;
 }

@@ -2,7 +2,6 @@
 // translation units of the library.
 #pragma once
 #include "common.cuh"
-#include "tile.cuh"
 
 namespace etd {
 
@@ -140,7 +139,6 @@ struct PhipmArgs {
   double* part;
   DevStatus* st;
   StatsDev* stats;
-  TileArgs tile[2];        // per species: the tiled Lanczos pass (FP32, 3D; enabled = 0: not used)
 };
 
 template <typename T>

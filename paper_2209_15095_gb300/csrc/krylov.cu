@@ -673,87 +673,9 @@ __device__ bool build_quads(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int n
   return true;
 }
 
-// Per launch, for the tiled Lanczos pass: the FP32 diagonals on the grid
-// (D_p at the computational points, 0 elsewhere), the tile activity flags
-// and the ordered list of active tiles (CTA b compacts the tiles of its
-// contiguous range after the other CTAs' counts).  Four grid barriers.
-// *ntotal: the number of active tiles.  Returns false if the kernel must
-// stop.
-template <typename T>
-__device__ bool build_tiles(const PhipmArgs<T>& a, const SpeciesDev<T>& S, const TileArgs& ta, int ncomp,
-                            unsigned& bar, int* ntotal) {
-  const GridDev& g = a.g;
-  const long long ptid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nth = (long long)gridDim.x * blockDim.x;
-  // the grid size is a multiple of 16 (the last axis is)
-  float4* d4 = reinterpret_cast<float4*>(ta.Dg);
-  for (long long i = ptid; i < g.size / 4; i += nth) __stcg(d4 + i, make_float4(0.f, 0.f, 0.f, 0.f));
-  for (long long i = ptid; i < ta.ntiles; i += nth) ta.flags[i] = 0;
-  if (!grid_barrier(a.st, bar, 21)) return false;
-  auto tile_of = [&](unsigned p) {
-    const unsigned z = g.sdiv[0].div(p);
-    const unsigned rem = p - z * (unsigned)g.stride[0];
-    const unsigned y = g.sdiv[1].div(rem);
-    const unsigned x = rem - y * (unsigned)g.stride[1];
-    return ((int)(z / TL_Z) * ta.nty + (int)(y / TL_Y)) * ta.ntx + (int)(x / TL_X);
-  };
-  for (long long k = dealt_tid(); k < ncomp; k += nth) {
-    const int p = __ldg(S.idx + k);
-    ta.Dg[p] = __ldg(S.diagf + k);
-    const int tp = tile_of((unsigned)p);
-    // one flag store per run of points in the same tile
-    if (k == 0 || tile_of((unsigned)__ldg(S.idx + k - 1)) != tp) ta.flags[tp] = 1;
-  }
-  if (!grid_barrier(a.st, bar, 22)) return false;
-  // the ordered list: counts per CTA range, then writes at the CTA's offset
-  __shared__ int s_wc[32], s_off;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int range = (ta.ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int t0 = (int)blockIdx.x * range, t1 = min(ta.ntiles, t0 + range);
-  int cnt = 0;
-  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) cnt += __ldcg(ta.flags + t) ? 1 : 0;
-  cnt = __reduce_add_sync(0xffffffffu, cnt);
-  if (lane == 0) s_wc[wid] = cnt;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int tot = 0;
-    for (int w = 0; w < nw; ++w) tot += s_wc[w];
-    ta.cnt[blockIdx.x] = tot;
-  }
-  if (!grid_barrier(a.st, bar, 23)) return false;
-  if (threadIdx.x == 0) {
-    int off = 0, tot = 0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      const int x = __ldcg(ta.cnt + b);
-      if (b < (int)blockIdx.x) off += x;
-      tot += x;
-    }
-    s_off = off;
-    *ntotal = tot;
-  }
-  __syncthreads();
-  int base = s_off;
-  for (int tb = t0; tb < t1; tb += blockDim.x) {
-    const int t = tb + threadIdx.x;
-    const bool act = t < t1 && __ldcg(ta.flags + t) != 0;
-    const unsigned bal = __ballot_sync(0xffffffffu, act);
-    __syncthreads();  // s_wc of the previous round is read
-    if (lane == 0) s_wc[wid] = __popc(bal);
-    __syncthreads();
-    int off = base, tot = 0;
-    for (int w = 0; w < nw; ++w) {
-      if (w < wid) off += s_wc[w];
-      tot += s_wc[w];
-    }
-    if (act) ta.list[off + __popc(bal & ((1u << lane) - 1u))] = t;
-    base += tot;
-  }
-  return grid_barrier(a.st, bar, 24);
-}
-
 template <typename T, int N>
 __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int sidx, Ctl& c, unsigned& bar,
-                              int& red, double ynorm2, double vscale, unsigned& tphase) {
+                              int& red, double ynorm2, double vscale) {
   const GridDev& g = a.g;
   const int ncomp = *S.ncomp;
   const long long gtid = dealt_tid();
@@ -774,13 +696,6 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   const bool quad = sizeof(T) == 4 && split && S.qidx != nullptr && S.beta_field == nullptr &&
                     (g.n[N - 1] & 3) == 0;
   if (quad && !build_quads<T>(a, S, ncomp, c, bar, red)) return false;
-  // 3D: the Lanczos vectors by the tiled pass (one pass each)
-  const bool tiles = quad && N == 3 && a.tile[sidx].enabled != 0;
-  __shared__ int s_ntiles;
-  if (tiles && !build_tiles<T>(a, S, a.tile[sidx], ncomp, bar, &s_ntiles)) return false;
-  // this CTA's tiles (the list is final after build_tiles' last barrier)
-  __shared__ int s_tiles[TL_CAP];
-  const int ntl = tiles ? tile_list(a.tile[sidx], s_ntiles, s_tiles) : 0;
   // the statistics accumulate over the launches of one step (zeroed by the host)
   if (blockIdx.x == 0 && threadIdx.x == 0) c.trace0 = a.stats ? a.stats->trace_len[sidx] : 0;
   double* pb = nullptr;
@@ -964,19 +879,8 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         const T* V2 = S.V + (long long)(j >= 2 ? j - 2 : 0) * vs;
         T* Vj = S.V + (long long)j * vs;
         bool quad_done = false;
-        if constexpr (sizeof(T) == 4 && N == 3) {
-          if (tiles) {
-            TileSums ts;
-            if (!tile_lanczos_pass(a.tile[sidx], g, Vj, j, ca, cb, cc, cfac, bc, a.st, tphase, s_tiles, ntl, ts))
-              return false;
-            double v[3] = {ts.d1, ts.d2, ts.d3};
-            pb = part_buf(a.part, red);
-            block_partials<3>(v, pb);
-            quad_done = true;
-          }
-        }
         if constexpr (sizeof(T) == 4) {
-          if (quad && !quad_done) {
+          if (quad) {
             const int nq = c.nquad;
             quad_pass_a(Zp, V1, V2, Vj, ca, cb, cc, S.qidx, nq, gtid, gthreads);
             if (!grid_barrier(a.st, bar, 15)) return false;
@@ -1213,22 +1117,10 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const __grid_constant__ PhipmArgs<T> a) {
+__global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
   __shared__ Ctl c;
   unsigned bar = 0;
   int red = 0;
-  // the tiled pass's two stage mbarriers (after the stages in dynamic shared
-  // memory), initialised once per launch; their parities are tracked in tphase
-  unsigned tphase = 0;
-  if (sizeof(T) == 4 && N == 3 && (a.tile[0].enabled || a.tile[1].enabled)) {
-    extern __shared__ __align__(128) unsigned char tl_smem[];
-    if (threadIdx.x == 0) {
-      mbar_init(smem_u32(tl_smem + 2 * TL_STAGE));
-      mbar_init(smem_u32(tl_smem + 2 * TL_STAGE + 8));
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-  }
   double* pb = nullptr;
   const GridDev& g = a.g;
   const long long gtid = dealt_tid();
@@ -1377,7 +1269,7 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const __grid_constant__
   }
   for (int s = 0; s < a.nspecies; ++s) {
     const double vscale = fmax(fmax(sqrt(tot[s][1]), sqrt(tot[s][2])), sqrt(tot[s][3]));
-    if (!phipm_species<T, N>(a, a.sp[s], s, c, bar, red, tot[s][0], vscale, tphase)) return;
+    if (!phipm_species<T, N>(a, a.sp[s], s, c, bar, red, tot[s][0], vscale)) return;
   }
   if (!grid_barrier(a.st, bar, 2)) return;
   // ---- write back: new values at computational points, 0 elsewhere
@@ -1464,18 +1356,8 @@ cudaError_t launch_phipm(const PhipmArgs<T>& a, int nblocks, cudaStream_t stream
   if (nblocks > MAX_BLOCKS) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(&a.st->barrier, 0, sizeof(unsigned), stream);
   if (e != cudaSuccess) return e;
-  size_t dsm = 0;
-  if (sizeof(T) == 4 && a.g.ndim == 3 && (a.tile[0].enabled || a.tile[1].enabled)) {
-    dsm = TL_SMEM;
-    static bool attr_set = false;
-    if (!attr_set) {
-      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TL_SMEM);
-      if (e != cudaSuccess) return e;
-      attr_set = true;
-    }
-  }
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel(fn, nblocks, PH_NT, args, dsm, stream);
+  return cudaLaunchCooperativeKernel(fn, nblocks, PH_NT, args, 0, stream);
 }
 
 int phipm_max_blocks(int ndim, bool fp32) {
@@ -1484,13 +1366,7 @@ int phipm_max_blocks(int ndim, bool fp32) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // FP32 3D launches may take the tiled pass's dynamic shared memory
-  size_t dsm = 0;
-  if (fp32 && ndim == 3) {
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TL_SMEM) != cudaSuccess) return 0;
-    dsm = TL_SMEM;
-  }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, PH_NT, dsm) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, PH_NT, 0) != cudaSuccess) return 0;
   return min(per, 1) * sms;
 }
 

@@ -285,11 +285,11 @@ def test_fullsize_star3d_mixed_operating_point(lib):
     assert np.max(np.abs(ph64[0] - phmx[0])[near]) <= 1e-2 * h
 
 
-def test_fullsize_ball512_mixed_tiled(lib):
+def test_fullsize_ball512_mixed(lib):
     """The bandwidth stress shape the bench times (ball512: a fixed ball of
-    radius 7 in a 512^3 grid, 46.3M points; the mixed Krylov launch takes
-    the tiled Lanczos pass): two ETD2 steps in FP32-mixed against the FP64
-    GPU path at the same tolerance, within 1e-5 relative in u."""
+    radius 7 in a 512^3 grid, 46.3M points; the split passes on aligned
+    4-node groups): two ETD2 steps in FP32-mixed against the FP64 GPU path at
+    the same tolerance, within 1e-5 relative in u."""
     from paper_2209_15095_gb300 import inputs
 
     w = inputs.ball512()

@@ -466,12 +466,11 @@ def test_phi_combination_mixed_large_layouts(lib, ndim, n):
 
 
 @pytest.mark.parametrize("shape", [(144, 144, 144), (131, 123, 176)])
-def test_phi_combination_mixed_tiled(lib, shape):
-    """Large 3D FP32 problems whose last axis is a multiple of 16 nodes take
-    the tiled Lanczos pass (64 x 8 x 8 tiles staged by TMA, one pass per
-    Krylov vector); (131, 123, 176) leaves partial tiles along every axis.
-    Against the FP64 oracle at 1e-5, two calls on the same context (the
-    stage barriers' parities carry over between passes and launches)."""
+def test_phi_combination_mixed_3d_ragged(lib, shape):
+    """Large 3D FP32 problems (at least 2^18 points, the split passes on
+    aligned 4-node groups) on a cube and on a grid with unequal axes, an
+    ellipsoid close to the box on every axis.  Against the FP64 oracle at
+    1e-5, two calls on the same context."""
     box = 2.0
     h = 2 * box / (shape[2] - 1)
     lo = tuple(-0.5 * h * (n - 1) for n in shape)
