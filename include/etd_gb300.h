@@ -248,17 +248,21 @@ etd_status etd_step_explicit(etd_ctx* ctx, int species, double dt, const double*
 
 /* Adjoint of one etd_step_explicit step on a frozen domain (species 0; needs
  * params->adjoint).  A = dt C is symmetric (Sec. 2), so with
- * lambda = dL/du_{n+1} and Phi_k = phi_k(A) lambda (three Krylov evaluations):
+ * lambda = dL/du_{n+1} and Phi_k = phi_k(A) lambda:
  *   lam  <- Phi_0 + dt F'(u_n)(Phi_1 + Phi_2) + acc        (dL/du_n)
  *   acc  <- -dt F'(u_nm1) Phi_2                              (to dL/du_{n-1})
  *   grad_params[0] += dt <Phi_1 + Phi_2, dF/dalpha(u_n)> - dt <Phi_2, dF/dalpha(u_nm1)>
  *   grad_beta += int_0^1 d(mu(t)^T A y(t))/d beta dt,  mu(t) = e^{(1-t)A} lambda,
  *                y(t) = phi_0(tA) u_n + phi_1(tA) t v_1 + phi_2(tA) t^2 v_2
  * (the step is y(1) of y' = A y + v_1 + t v_2, Eq. 3.10; v_1 = dt F(u_n),
- * v_2 = dt (F(u_n) - F(u_nm1))), by nquad-point Gauss-Legendre in t (2 Krylov
- * evaluations per point) and the face contraction of the symmetric stencil
- * (node field beta, face value the mean of the two nodes; ghost nodes
- * included).  first = 1 for the first step, where u_nm1 = u_n and acc is
+ * v_2 = dt (F(u_n) - F(u_nm1))), by nquad-point Gauss-Legendre in t and the
+ * face contraction of the symmetric stencil (node field beta, face value the
+ * mean of the two nodes; ghost nodes included).  Two Krylov evaluations per
+ * step: Phi_0, Phi_1, Phi_2 and every mu(t_i) from one basis of the Krylov
+ * space of A and lambda (grown until the estimate of exp(A) lambda meets
+ * krylov_tol; if m_max vectors do not, each action is evaluated by its own
+ * time-stepped Krylov evaluation instead), and every y(t_i) from one
+ * time-stepped evaluation of Eq. 3.10, written as its substeps pass the t_i.  first = 1 for the first step, where u_nm1 = u_n and acc is
  * folded into lam.  u_n, u_nm1 (in), lam, acc (in/out), grad_beta (accumulated):
  * device full-grid FP64, zero off the computational set except grad_beta;
  * grad_params: device, 1 double, accumulated (alpha of ETD_REACTION_LOGISTIC_AK).

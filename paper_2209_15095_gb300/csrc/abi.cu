@@ -55,8 +55,11 @@ struct etd_ctx {
   double* pout = nullptr;  // 2 doubles: Poisson solve iterations and residual
   SpeciesBufs sp[2];
   LevelsetBufs ls;
-  // adjoint (species 0): phi actions, quadrature vectors, face weights
+  // adjoint (species 0): phi actions, right-hand sides, face weights, and
+  // mu(t_i), y(t_i) at the quadrature times
   double* adj[8] = {nullptr};
+  double* adj_mu[ADJ_NQ_MAX] = {nullptr};
+  double* adj_y[ADJ_NQ_MAX] = {nullptr};
   double* facew = nullptr;
   int nblocks = 0;
   bool fp32 = false;
@@ -231,6 +234,14 @@ size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
       double* b = cv.take<double>(G);
       if (c) c->adj[i] = b;
     }
+    for (int i = 0; i < ADJ_NQ_MAX; ++i) {
+      double* bm = cv.take<double>(G);
+      double* by = cv.take<double>(G);
+      if (c) {
+        c->adj_mu[i] = bm;
+        c->adj_y[i] = by;
+      }
+    }
     double* fw = cv.take<double>(G * 2 * (size_t)g.ndim);
     if (c) c->facew = fw;
   }
@@ -326,7 +337,8 @@ SpeciesDev<T> species_dev(etd_ctx* c, int s, double* u, int stage = 0) {
 template <typename T>
 etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int species, const double* const* given,
                      etd_step_stats* stats, bool etd1 = false, bool keep_stats = false, int p = 2,
-                     const StageDesc* stage = nullptr) {
+                     const StageDesc* stage = nullptr, int nq = 0, const double* tq = nullptr,
+                     double* const* outs = nullptr) {
   PhipmArgs<T> a;
   memset(&a, 0, sizeof(a));
   a.g = c->g;
@@ -341,6 +353,10 @@ etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int spec
   a.ms3 = mode == MODE_ETD2 && c->par.scheme == ETD_SCHEME_ETD3 ? 1 : 0;
   a.p = a.ms3 ? 3 : p;
   if (stage) a.stage = *stage;
+  a.nq = nq;
+  for (int i = 0; i < nq; ++i) a.tq[i] = tq[i];
+  const int nout = mode == MODE_ADJ_LAMBDA ? 3 + nq : mode == MODE_ADJ_Y ? nq : 0;
+  for (int i = 0; i < nout; ++i) a.out[i] = outs[i];
   const bool all = mode == MODE_ETD2 || mode == MODE_RK2 || mode == MODE_STAGE;
   if (all) {
     a.nspecies = c->par.nspecies;
@@ -348,9 +364,10 @@ etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int spec
   } else {
     a.nspecies = 1;
     a.sp[0] = species_dev<T>(c, species, u[0]);
-    for (int i = 0; i <= p; ++i) a.given[i] = given[i];
+    const int ng = mode == MODE_ADJ_LAMBDA ? 1 : mode == MODE_EXPLICIT || mode == MODE_ADJ_Y ? 2 : p + 1;
+    for (int i = 0; i < ng; ++i) a.given[i] = given[i];
   }
-  if (mode == MODE_EXPLICIT) {
+  if (mode == MODE_EXPLICIT || mode == MODE_ADJ_Y) {
     a.reaction = c->par.reaction;
     for (int i = 0; i < 4; ++i) a.rp[i] = c->par.rp[i];
   }
@@ -695,28 +712,62 @@ etd_status etd_adjoint_step(etd_ctx* c, int species, double dt, const double* u_
   if (!c) return ETD_ERR_ARG;
   if (!c->par.adjoint || !c->facew) return fail(c, ETD_ERR_ARG, "context created without params.adjoint");
   if (species != 0 || !u_n || !u_nm1 || !lam || !acc || !grad_beta || !grad_params || !(dt > 0.0) || nquad < 1 ||
-      nquad > 32)
+      nquad > ADJ_NQ_MAX)
     return fail(c, ETD_ERR_ARG, "bad arguments");
   if (c->par.reaction == ETD_REACTION_COMPETITION) return fail(c, ETD_ERR_ARG, "adjoint is single-species");
   if (!c->sp[0].ready) return fail(c, ETD_ERR_ARG, "etd_init_domain not called");
   double* P0 = c->adj[0];
   double* P1 = c->adj[1];
   double* P2 = c->adj[2];
-  double* B1 = c->adj[3];
-  double* B2 = c->adj[4];
-  double* Yq = c->adj[5];
-  double* Mu = c->adj[6];
   const double* Zero = c->adj[7];  // never written: zero since etd_create
-  auto phi = [&](double s, const double* v0, const double* v1, const double* v2, double* out) {
-    const double* given[3] = {v0, v1, v2};
-    double* o[1] = {out};
-    return c->fp32 ? run_phipm<float>(c, MODE_GIVEN, s, o, 0, given, nullptr)
-                   : run_phipm<double>(c, MODE_GIVEN, s, o, 0, given, nullptr);
-  };
+  double t[ADJ_NQ_MAX], w[ADJ_NQ_MAX], s[ADJ_NQ_MAX];
+  gauss_legendre01(nquad, t, w);
+  for (int i = 0; i < nquad; ++i) s[i] = 1.0 - t[i];
   etd_status rs;
-  if ((rs = phi(dt, lam, Zero, Zero, P0)) != ETD_OK) return rs;
-  if ((rs = phi(dt, Zero, lam, Zero, P1)) != ETD_OK) return rs;
-  if ((rs = phi(dt, Zero, Zero, lam, P2)) != ETD_OK) return rs;
+  // 1. One Krylov basis on lambda: Phi_k = phi_k(A) lambda (k = 0, 1, 2) and
+  //    mu(t_i) = exp((1 - t_i) A) lambda.
+  {
+    double* outs[ADJ_NQ_MAX + 3] = {P0, P1, P2};
+    for (int i = 0; i < nquad; ++i) outs[3 + i] = c->adj_mu[i];
+    const double* given[1] = {lam};
+    double* none[1] = {nullptr};
+    rs = c->fp32 ? run_phipm<float>(c, MODE_ADJ_LAMBDA, dt, none, 0, given, nullptr, false, false, 2, nullptr, nquad, s,
+                                    outs)
+                 : run_phipm<double>(c, MODE_ADJ_LAMBDA, dt, none, 0, given, nullptr, false, false, 2, nullptr, nquad, s,
+                                     outs);
+    if (rs != ETD_OK) return rs;
+  }
+  int missed = 0;
+  cudaError_t e = cudaMemcpyAsync(&missed, &c->stats->single_basis_missed, sizeof(int), cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint basis flag read");
+  if (missed) {
+    // m_max vectors do not reach the tolerance with one basis: each action
+    // by its own time-stepped evaluation
+    auto phi = [&](double sdt, const double* v0, const double* v1, const double* v2, double* out) {
+      const double* given[3] = {v0, v1, v2};
+      double* o[1] = {out};
+      return c->fp32 ? run_phipm<float>(c, MODE_GIVEN, sdt, o, 0, given, nullptr)
+                     : run_phipm<double>(c, MODE_GIVEN, sdt, o, 0, given, nullptr);
+    };
+    if ((rs = phi(dt, lam, Zero, Zero, P0)) != ETD_OK) return rs;
+    if ((rs = phi(dt, Zero, lam, Zero, P1)) != ETD_OK) return rs;
+    if ((rs = phi(dt, Zero, Zero, lam, P2)) != ETD_OK) return rs;
+    for (int i = 0; i < nquad; ++i)
+      if ((rs = phi(s[i] * dt, lam, Zero, Zero, c->adj_mu[i])) != ETD_OK) return rs;
+  }
+  // 2. y(t_i) of Eq. 3.10 (y' = A y + v_1 + t v_2, y(0) = u_n) at every
+  //    quadrature time, from one time-stepped evaluation.
+  {
+    const double* given[2] = {u_n, u_nm1};
+    double* none[1] = {nullptr};
+    rs = c->fp32 ? run_phipm<float>(c, MODE_ADJ_Y, dt, none, 0, given, nullptr, false, false, 2, nullptr, nquad, t,
+                                    c->adj_y)
+                 : run_phipm<double>(c, MODE_ADJ_Y, dt, none, 0, given, nullptr, false, false, 2, nullptr, nquad, t,
+                                     c->adj_y);
+    if (rs != ETD_OK) return rs;
+  }
   AdjointArgs a;
   memset(&a, 0, sizeof(a));
   a.g = c->g;
@@ -737,17 +788,17 @@ etd_status etd_adjoint_step(etd_ctx* c, int species, double dt, const double* u_
   a.acc = acc;
   a.part = c->part;
   a.grad_params = grad_params;
-  double t[32], w[32];
-  gauss_legendre01(nquad, t, w);
+  a.nq = nquad;
   for (int i = 0; i < nquad; ++i) {
-    cudaError_t e = launch_adjoint_rhs(a, t[i], t[i] * t[i], B1, B2, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint rhs");
-    if ((rs = phi(t[i] * dt, u_n, B1, B2, Yq)) != ETD_OK) return rs;
-    if ((rs = phi((1.0 - t[i]) * dt, lam, Zero, Zero, Mu)) != ETD_OK) return rs;
-    e = launch_beta_contract(a, Mu, Yq, w[i] * dt, grad_beta, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "beta contraction");
+    a.muq[i] = c->adj_mu[i];
+    a.yq[i] = c->adj_y[i];
+    a.wq[i] = w[i] * dt;
   }
-  cudaError_t e = launch_adjoint_combine(a, c->stream);
+  // 3. the beta contraction over all quadrature times, then 4. the
+  //    pointwise combination (which overwrites lam)
+  e = launch_beta_contract_multi(a, grad_beta, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "beta contraction");
+  e = launch_adjoint_combine(a, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint combine");
   return ETD_OK;
 }

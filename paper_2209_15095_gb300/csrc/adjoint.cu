@@ -130,6 +130,54 @@ __global__ void __launch_bounds__(ADJ_NT) beta_contract_kernel(const AdjointArgs
   }
 }
 
+// All quadrature times in one pass: per face the weighted sum over i of
+// the face derivative, then one update per node (and one atomic per ghost
+// face).
+template <int N>
+__global__ void __launch_bounds__(ADJ_NT) beta_contract_multi_kernel(const AdjointArgs a, double* grad_beta) {
+  const int ncomp = *a.ncomp;
+  const double inv_h2 = 1.0 / (a.g.h * a.g.h);
+  const int nq = a.nq;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < ncomp;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long p = a.idx[k];
+    double own = 0.0;
+#pragma unroll
+    for (int d = 0; d < N; ++d) {
+#pragma unroll
+      for (int si = 0; si < 2; ++si) {
+        const long long q = p + (si == 0 ? -a.g.stride[d] : a.g.stride[d]);
+        double f = 0.0;
+        if ((a.kind[q] & 3) == K_COMP) {
+          for (int i = 0; i < nq; ++i) {
+            const double* mu = a.muq[i];
+            const double* y = a.yq[i];
+            f = fma(a.wq[i], -(mu[p] - mu[q]) * (y[p] - y[q]), f);
+          }
+          own += 0.5 * (f * inv_h2);
+        } else {
+          const double gw = a.facew[k * (2 * N) + 2 * d + si];
+          for (int i = 0; i < nq; ++i) f = fma(a.wq[i], -gw * a.muq[i][p] * a.yq[i][p], f);
+          const double df = 0.5 * (f * inv_h2);
+          own += df;
+          atomicAdd(grad_beta + q, df);
+        }
+      }
+    }
+    grad_beta[p] += own;
+  }
+}
+
+cudaError_t launch_beta_contract_multi(const AdjointArgs& a, double* grad_beta, cudaStream_t stream) {
+  switch (a.g.ndim) {
+    case 2: beta_contract_multi_kernel<2><<<ADJ_BLOCKS, ADJ_NT, 0, stream>>>(a, grad_beta); break;
+    case 3: beta_contract_multi_kernel<3><<<ADJ_BLOCKS, ADJ_NT, 0, stream>>>(a, grad_beta); break;
+    case 4: beta_contract_multi_kernel<4><<<ADJ_BLOCKS, ADJ_NT, 0, stream>>>(a, grad_beta); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_beta_contract(const AdjointArgs& a, const double* mu, const double* y, double coef,
                                  double* grad_beta, cudaStream_t stream) {
   switch (a.g.ndim) {

@@ -52,6 +52,8 @@ struct StatsDev {
   int trace_len[2];
   int trace_m[2][TRACE_MAX];
   double trace_tau[2][TRACE_MAX];
+  int single_basis_missed;  // MODE_ADJ_LAMBDA: tolerance not met by one basis of m_max vectors
+  int pad;
 };
 
 template <typename T>
@@ -108,7 +110,13 @@ enum : int {
   MODE_RK2 = 3,       // second ETD2RK stage: v0 = v1 = 0, v2 = dt (F(u) - F_prev);
                       // u <- u + result
   MODE_STAGE = 4,     // a stage of ETD3RK / ETD4RK (StageDesc); reaction term only
+  MODE_ADJ_LAMBDA = 5,  // one Krylov basis on given[0] = lambda: out[0..2] = phi_0..2(A) lambda,
+                        // out[3 + i] = exp(tq[i] A) lambda; no time stepping (flags
+                        // single_basis_missed if m_max vectors do not reach the tolerance)
+  MODE_ADJ_Y = 6,       // as MODE_EXPLICIT, writing y(tq[i]) of Eq. 3.10 to out[i] (no u output)
 };
+
+constexpr int ADJ_NQ_MAX = 32;  // quadrature times of the adjoint modes
 
 // One stage of ETD3RK / ETD4RK: fields 0 = u, 1..3 = the stage fields a, b, c.
 // v_0 = field v0_field; v_j = dt sum_i coef[j-1][i] F(field i), j = 1..3;
@@ -136,6 +144,9 @@ struct PhipmArgs {
   int p;                   // highest phi index of the combination: 2 or 3
   int ms3;                 // MODE_ETD2: multistep ETD3 (Eq. 3.8b, s = 3; p = 3)
   StageDesc stage;         // MODE_STAGE
+  int nq;                  // MODE_ADJ_*: number of times tq
+  double tq[ADJ_NQ_MAX];   // MODE_ADJ_LAMBDA: exponent factors s_i; MODE_ADJ_Y: output times t_i
+  double* out[ADJ_NQ_MAX + 3];  // MODE_ADJ_*: output fields (full grid FP64, computational points)
   double* part;
   DevStatus* st;
   StatsDev* stats;
@@ -193,6 +204,11 @@ struct AdjointArgs {
   double* acc;   // in: contribution to dL/du_n from the later step; out: to dL/du_{n-1}
   double* part;  // per-block partial sums of the alpha gradient
   double* grad_params;
+  // the beta contraction over the quadrature times: mu(t_i), y(t_i), weights
+  int nq;
+  const double* muq[ADJ_NQ_MAX];
+  const double* yq[ADJ_NQ_MAX];
+  double wq[ADJ_NQ_MAX];
 };
 cudaError_t launch_adjoint_combine(const AdjointArgs& a, cudaStream_t stream);
 // v1 = dt F(u_n), v2 = dt (F(u_n) - F(u_{n-1})) scaled by (s1, s2) on the computational set
@@ -200,5 +216,7 @@ cudaError_t launch_adjoint_rhs(const AdjointArgs& a, double s1, double s2, doubl
 // grad_beta += coef * d(mu^T C y)/d beta (node field, face mean)
 cudaError_t launch_beta_contract(const AdjointArgs& a, const double* mu, const double* y, double coef,
                                  double* grad_beta, cudaStream_t stream);
+// grad_beta += sum_i wq[i] d(mu_i^T C y_i)/d beta over the quadrature times (one launch)
+cudaError_t launch_beta_contract_multi(const AdjointArgs& a, double* grad_beta, cudaStream_t stream);
 
 }  // namespace etd

@@ -115,7 +115,7 @@ __device__ __forceinline__ void taylor_steps(int m, int s, int deg, const double
   }
 }
 
-__device__ void small_expm_warp(Ctl& c, int m, int p, double tau) {
+__device__ void small_expm_warp(const Ctl& c, int m, int p, double tau, double* yexp) {
   const int lane = threadIdx.x & 31;
   const int M = m + p + 1;
   // Gershgorin interval [L, U] of the augmented matrix (rows m.. have centre
@@ -171,25 +171,40 @@ __device__ void small_expm_warp(Ctl& c, int m, int p, double tau) {
   if (M > 32) taylor_steps<true>(m, s, deg, A, B, C, x);
   else taylor_steps<false>(m, s, deg, A, B, C, x);
   const double emu = exp(dmu);
-  if (lane < m) c.yexp[lane] = x[0] * emu;
-  if (lane + 32 < m) c.yexp[lane + 32] = x[1] * emu;
+  if (lane < m) yexp[lane] = x[0] * emu;
+  if (lane + 32 < m) yexp[lane + 32] = x[1] * emu;
   __syncwarp();
 }
 
-// After small_expm_warp: err and the combination coefficients (warp 0; the
-// coefficients come from phi_p(X) e_1 = X phi_{p+1}(X) e_1 + e_1 / p!).
-__device__ void finish_check(Ctl& c, int m, int p, double tau) {
+// Combination coefficients from yexp = phi_{p+1}(tau H_m) e_1 (one warp):
+// out_r = tau^p beta (phi_p(tau H_m) e_1)_r / |V_r|, with phi_p(X) e_1 =
+// X phi_{p+1}(X) e_1 + e_1 / p!  (p = 0 .. 3).
+__device__ void coef_row(const Ctl& c, int m, int p, double tau, const double* yexp, double* out) {
   const int lane = threadIdx.x & 31;
-  const double taup = p == 3 ? tau * tau * tau : tau * tau;
-  const double invf = p == 3 ? 1.0 / 6.0 : 0.5;
-  for (int r = lane; r < m; r += 32) {
-    double hy = c.alpha[r] * c.yexp[r];
-    if (r > 0) hy = fma(c.low[r - 1], c.yexp[r - 1], hy);
-    if (r + 1 < m) hy = fma(c.up[r + 1], c.yexp[r + 1], hy);
-    const double php = fma(tau, hy, r == 0 ? invf : 0.0);
-    c.coef[r] = taup * c.beta * php * c.scale[r];
+  double taup = 1.0, invf = 1.0;
+  for (int i = 1; i <= p; ++i) {
+    taup *= tau;
+    invf /= (double)i;
   }
-  if (lane == 0) c.err = taup * tau * c.beta * c.hn * fabs(c.yexp[m - 1]);
+  for (int r = lane; r < m; r += 32) {
+    double hy = c.alpha[r] * yexp[r];
+    if (r > 0) hy = fma(c.low[r - 1], yexp[r - 1], hy);
+    if (r + 1 < m) hy = fma(c.up[r + 1], yexp[r + 1], hy);
+    const double php = fma(tau, hy, r == 0 ? invf : 0.0);
+    out[r] = taup * c.beta * php * c.scale[r];
+  }
+  __syncwarp();
+}
+
+// After small_expm_warp: err and the combination coefficients (warp 0):
+// err = tau^{p+1} beta h_{m+1,m} |e_m^T phi_{p+1}(tau H_m) e_1|.
+__device__ void finish_check(Ctl& c, int m, int p, double tau) {
+  coef_row(c, m, p, tau, c.yexp, c.coef);
+  if ((threadIdx.x & 31) == 0) {
+    double taup = 1.0;
+    for (int i = 1; i <= p; ++i) taup *= tau;
+    c.err = taup * tau * c.beta * c.hn * fabs(c.yexp[m - 1]);
+  }
   __syncwarp();
 }
 
@@ -673,7 +688,148 @@ __device__ bool build_quads(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int n
   return true;
 }
 
-template <typename T, int N>
+// Output fields of the adjoint modes: out[r][p] = (y(t_k) + shift_r w_1)[p]
+// (shift == nullptr: 0) + sum_i rows[r][i] V_i[p] at the computational
+// points, rows r0 .. r0 + NC - 1 in one sweep (FP64 accumulation).
+template <typename T, int NC>
+__device__ __forceinline__ void multi_out_sweep(const SpeciesDev<T>& S, int ncomp, int m, const double* rows,
+                                                double* const* outs, const double* shift, long long vs,
+                                                long long gtid, long long gth) {
+  for (long long k = gtid; k < ncomp; k += gth) {
+    const long long p = __ldg(S.idx + k);
+    double acc[NC];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) acc[r] = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double v = to_f64(__ldcg(S.V + (long long)i * vs + p));
+#pragma unroll
+      for (int r = 0; r < NC; ++r) acc[r] = fma(rows[r * 64 + i], v, acc[r]);
+    }
+    if (shift) {
+      const double y0 = __ldcg(S.Yc + k), w1 = to_f64(__ldcg(S.W1g + p));
+#pragma unroll
+      for (int r = 0; r < NC; ++r) acc[r] = fma(shift[r], w1, y0) + acc[r];
+    }
+#pragma unroll
+    for (int r = 0; r < NC; ++r) outs[r][p] = acc[r];
+  }
+}
+
+template <typename T>
+__device__ __noinline__ void multi_out(const SpeciesDev<T>& S, int ncomp, int m, const double* rows, int nr,
+                                       double* const* outs, const double* shift, long long vs, long long gtid,
+                                       long long gth) {
+  for (int rb = 0; rb < nr; rb += 6) {
+    const double* rw = rows + rb * 64;
+    const double* sh = shift ? shift + rb : nullptr;
+    switch (min(6, nr - rb)) {
+      case 1: multi_out_sweep<T, 1>(S, ncomp, m, rw, outs + rb, sh, vs, gtid, gth); break;
+      case 2: multi_out_sweep<T, 2>(S, ncomp, m, rw, outs + rb, sh, vs, gtid, gth); break;
+      case 3: multi_out_sweep<T, 3>(S, ncomp, m, rw, outs + rb, sh, vs, gtid, gth); break;
+      case 4: multi_out_sweep<T, 4>(S, ncomp, m, rw, outs + rb, sh, vs, gtid, gth); break;
+      case 5: multi_out_sweep<T, 5>(S, ncomp, m, rw, outs + rb, sh, vs, gtid, gth); break;
+      default: multi_out_sweep<T, 6>(S, ncomp, m, rw, outs + rb, sh, vs, gtid, gth); break;
+    }
+  }
+}
+
+// Dynamic shared memory of the adjoint modes: coefficient rows, then one
+// small-exponential scratch row per warp.
+constexpr int ADJ_ROWS = ADJ_NQ_MAX + 3;
+constexpr size_t ADJ_SMEM = (size_t)(ADJ_ROWS + PH_NT / 32) * 64 * sizeof(double);
+
+// MODE_ADJ_LAMBDA after the basis on lambda is accepted at tau = 1: rows 0 .. 2
+// = beta phi_k(H_m) e_1 (k = 0, 1, 2; rows 0 and 1 from the accepting check,
+// row 2 from phi_2 = the p = 1 exponential's phi_{p+1}), rows 3 + i = beta
+// exp(tq[i] H_m) e_1, each exponential on its own warp; then the outputs.
+template <typename T>
+__device__ __noinline__ void adj_lambda_outputs(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int sidx, Ctl& c, int ncomp,
+                                   long long vs, long long gtid, long long gth) {
+  extern __shared__ double adj_sm[];
+  double* rows = adj_sm;
+  const int m = c.m, nr = 3 + a.nq;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double* ye = adj_sm + ADJ_ROWS * 64 + wid * 64;
+  if (m > 0) {
+    for (int r = wid; r < nr; r += nw) {
+      double* out = rows + r * 64;
+      if (r == 0) {
+        for (int i = lane; i < m; i += 32) out[i] = c.coef[i];
+        __syncwarp();
+      } else if (r == 1) {
+        for (int i = lane; i < m; i += 32) out[i] = c.beta * c.yexp[i] * c.scale[i];
+        __syncwarp();
+      } else if (r == 2) {
+        small_expm_warp(c, m, 1, 1.0, ye);
+        for (int i = lane; i < m; i += 32) out[i] = c.beta * ye[i] * c.scale[i];
+        __syncwarp();
+      } else {
+        const double sq = a.tq[r - 3];
+        small_expm_warp(c, m, 0, sq, ye);
+        coef_row(c, m, 0, sq, ye, out);
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats) {
+    a.stats->substeps[sidx] += 1;
+    a.stats->iters[sidx] += m;
+    const int ti = a.stats->trace_len[sidx];
+    if (ti < TRACE_MAX) {
+      a.stats->trace_m[sidx][ti] = m;
+      a.stats->trace_tau[sidx][ti] = 1.0;
+      a.stats->trace_len[sidx] = ti + 1;
+    }
+  }
+  __syncthreads();
+  multi_out<T>(S, ncomp, m, rows, nr, const_cast<double* const*>(a.out), nullptr, vs, gtid, gth);
+}
+
+// MODE_ADJ_Y within an accepted substep [t, t1] (basis on w_2, P = 2): for
+// every output time tq[i] in (t, t1], y(tq[i]) = y(t) + s w_1 + s^2 beta V_m
+// phi_2(s H_m) e_1 with s = tq[i] - t (the same basis serves every s <= tau;
+// its error estimate shrinks with s).  Returns false if the kernel must stop.
+template <typename T>
+__device__ __noinline__ bool adj_y_outputs(const PhipmArgs<T>& a, const SpeciesDev<T>& S, Ctl& c, int ncomp, long long vs,
+                              long long gtid, long long gth, unsigned& bar, double t) {
+  extern __shared__ double adj_sm[];
+  __shared__ double s_shift[ADJ_NQ_MAX];
+  __shared__ int s_which[ADJ_NQ_MAX];
+  const double t1 = c.last ? 1.0 : t + c.tau;
+  int nr = 0;
+  for (int i = 0; i < a.nq; ++i) {
+    if (t < a.tq[i] && a.tq[i] <= t1) {
+      if (threadIdx.x == 0) {
+        s_which[nr] = i;
+        s_shift[nr] = a.tq[i] - t;
+      }
+      ++nr;
+    }
+  }
+  if (nr == 0) return true;
+  __syncthreads();
+  double* rows = adj_sm;
+  const int m = c.m;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double* ye = adj_sm + ADJ_ROWS * 64 + wid * 64;
+  __shared__ double* s_out[ADJ_NQ_MAX];
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) s_out[r] = a.out[s_which[r]];
+  for (int r = wid; r < nr; r += nw) {
+    double* out = rows + r * 64;
+    if (m > 0) {
+      small_expm_warp(c, m, 2, s_shift[r], ye);
+      coef_row(c, m, 2, s_shift[r], ye, out);
+    } else {
+      for (int i = lane; i < 64; i += 32) out[i] = 0.0;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  multi_out<T>(S, ncomp, m, rows, nr, s_out, s_shift, vs, gtid, gth);
+  // the substep's combination rewrites y(t) next
+  return grid_barrier(a.st, bar, 25);
+}
+
+template <typename T, int N, bool ADJ>
 __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int sidx, Ctl& c, unsigned& bar,
                               int& red, double ynorm2, double vscale) {
   const GridDev& g = a.g;
@@ -684,7 +840,9 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   const T bc = (T)S.beta_c;
   const double anorm = a.dt * (*S.gersh);
   const int m_max = a.m_max;
-  const int P = a.p == 3 ? 3 : 2;  // highest phi index (any other value: 2)
+  // highest phi index: 2 or 3 (any other value of a.p: 2); 0 for the basis
+  // on lambda of the adjoint (V_0 = lambda, written by the set-up)
+  const int P = ADJ && a.mode == MODE_ADJ_LAMBDA ? 0 : a.p == 3 ? 3 : 2;
   const long long vs = g.size;
   // large problems: split Lanczos pass (see SPLIT_MIN), on aligned groups of
   // 4 nodes where the layout allows
@@ -719,9 +877,9 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
     }
     __syncthreads();
     const double t = c.t;
-    bool qw = false;
+    bool qw = P == 0;  // P = 0: no w_j passes
     if constexpr (sizeof(T) == 4) {
-      if (quad) {
+      if (quad && !qw) {
         // the w_j passes on groups of 4 nodes
         const int nq = c.nquad;
         const float tt = (float)t;
@@ -992,7 +1150,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         const int m = c.m;
         if (m % CHECK_EVERY == 0 || m == m_max || c.breakdown) {
           if (threadIdx.x < 32) {
-            small_expm_warp(c, m, P, c.tau);
+            small_expm_warp(c, m, P, c.tau, c.yexp);
             finish_check(c, m, P, c.tau);
             if (threadIdx.x == 0) {
               if (c.breakdown) c.err = 0.0;
@@ -1003,8 +1161,9 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
           if (c.accepted) break;
         }
       }
-      // rejections at m_max: shrink tau, reuse the basis
-      if (!c.accepted) {
+      // rejections at m_max: shrink tau, reuse the basis (the adjoint's basis
+      // on lambda is not time-stepped: the host falls back instead)
+      if (!c.accepted && !(ADJ && a.mode == MODE_ADJ_LAMBDA)) {
         const int m = c.m;
         for (;;) {
           if (threadIdx.x == 0) {
@@ -1021,7 +1180,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
           __syncthreads();
           if (c.abort) return false;
           if (threadIdx.x < 32) {
-            small_expm_warp(c, m, P, c.tau);
+            small_expm_warp(c, m, P, c.tau, c.yexp);
             finish_check(c, m, P, c.tau);
             if (threadIdx.x == 0) c.accepted = c.err <= a.tol * c.tau * c.ynorm;
           }
@@ -1035,6 +1194,17 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         c.m = 0;
       }
       __syncthreads();
+    }
+    if constexpr (ADJ) {
+      if (a.mode == MODE_ADJ_LAMBDA) {
+        if (c.m > 0 && !c.accepted) {
+          if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats) a.stats->single_basis_missed = 1;
+          return true;
+        }
+        adj_lambda_outputs<T>(a, S, sidx, c, ncomp, vs, gtid, gthreads);
+        return true;
+      }
+      if (a.mode == MODE_ADJ_Y && !adj_y_outputs<T>(a, S, c, ncomp, vs, gtid, gthreads, bar, t)) return false;
     }
     // y <- y + tau w_1 + sum_i coef_i V_i ; |y|^2
     {
@@ -1116,7 +1286,9 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   return true;
 }
 
-template <typename T, int N>
+// ADJ: the instantiation that also runs the adjoint modes (MODE_ADJ_*),
+// kept apart so that their code adds nothing to the other launches.
+template <typename T, int N, bool ADJ>
 __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
   __shared__ Ctl c;
   unsigned bar = 0;
@@ -1190,7 +1362,11 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
             v1[q] = a.given[1][p];
             v2[q] = a.given[2][p];
             if (a.p == 3) v3[q] = a.given[3][p];
-          } else if (a.mode == MODE_EXPLICIT) {
+          } else if (a.mode == MODE_ADJ_LAMBDA) {
+            y[q] = a.given[0][p];
+            v1[q] = 0.0;
+            v2[q] = 0.0;
+          } else if (a.mode == MODE_EXPLICIT || a.mode == MODE_ADJ_Y) {
             const double u = a.given[0][p], um = a.given[1][p];
             const double F = reaction(a.reaction, a.rp, 0, u, 0.0);
             const double Fm = reaction(a.reaction, a.rp, 0, um, 0.0);
@@ -1238,6 +1414,7 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
           S.V1c[k] = (T)v1[q];
           S.V2c[k] = (T)v2[q];
           if (a.p == 3) S.V3c[k] = (T)v3[q];
+          if (a.mode == MODE_ADJ_LAMBDA) S.V[p] = (T)y[q];  // V_0 = lambda
           acc.add(y[q], y[q]);
           acc1.add(v1[q], v1[q]);
           acc2.add(v2[q], v2[q]);
@@ -1269,9 +1446,11 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
   }
   for (int s = 0; s < a.nspecies; ++s) {
     const double vscale = fmax(fmax(sqrt(tot[s][1]), sqrt(tot[s][2])), sqrt(tot[s][3]));
-    if (!phipm_species<T, N>(a, a.sp[s], s, c, bar, red, tot[s][0], vscale)) return;
+    if (!phipm_species<T, N, ADJ>(a, a.sp[s], s, c, bar, red, tot[s][0], vscale)) return;
   }
   if (!grid_barrier(a.st, bar, 2)) return;
+  // the adjoint modes' outputs are written by the species loop
+  if (ADJ && (a.mode == MODE_ADJ_LAMBDA || a.mode == MODE_ADJ_Y)) return;
   // ---- write back: new values at computational points, 0 elsewhere
   for (int s = 0; s < a.nspecies; ++s) {
     const SpeciesDev<T>& S = a.sp[s];
@@ -1330,11 +1509,11 @@ __global__ void __launch_bounds__(PH_NT, 1) phipm_kernel(const PhipmArgs<T> a) {
 }
 
 template <typename T>
-static void* phipm_entry(int ndim) {
+static void* phipm_entry(int ndim, bool adj = false) {
   switch (ndim) {
-    case 2: return (void*)phipm_kernel<T, 2>;
-    case 3: return (void*)phipm_kernel<T, 3>;
-    case 4: return (void*)phipm_kernel<T, 4>;
+    case 2: return adj ? (void*)phipm_kernel<T, 2, true> : (void*)phipm_kernel<T, 2, false>;
+    case 3: return adj ? (void*)phipm_kernel<T, 3, true> : (void*)phipm_kernel<T, 3, false>;
+    case 4: return adj ? (void*)phipm_kernel<T, 4, true> : (void*)phipm_kernel<T, 4, false>;
   }
   return nullptr;
 }
@@ -1351,13 +1530,15 @@ cudaError_t launch_phipm(const PhipmArgs<T>& a, int nblocks, cudaStream_t stream
     if (e != cudaSuccess) return e;
     g_fact_ready = true;
   }
-  void* fn = phipm_entry<T>(a.g.ndim);
+  const bool adj = a.mode == MODE_ADJ_LAMBDA || a.mode == MODE_ADJ_Y;
+  void* fn = phipm_entry<T>(a.g.ndim, adj);
   if (!fn) return cudaErrorInvalidValue;
   if (nblocks > MAX_BLOCKS) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(&a.st->barrier, 0, sizeof(unsigned), stream);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel(fn, nblocks, PH_NT, args, 0, stream);
+  const size_t dsm = adj ? ADJ_SMEM : 0;
+  return cudaLaunchCooperativeKernel(fn, nblocks, PH_NT, args, dsm, stream);
 }
 
 int phipm_max_blocks(int ndim, bool fp32) {
@@ -1367,7 +1548,11 @@ int phipm_max_blocks(int ndim, bool fp32) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, PH_NT, 0) != cudaSuccess) return 0;
-  return min(per, 1) * sms;
+  // the adjoint modes' instantiation with its dynamic shared memory
+  void* fa = fp32 ? phipm_entry<float>(ndim, true) : phipm_entry<double>(ndim, true);
+  int per_a = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_a, fa, PH_NT, ADJ_SMEM) != cudaSuccess) return 0;
+  return min(min(per, per_a), 1) * sms;
 }
 
 template cudaError_t launch_phipm<double>(const PhipmArgs<double>&, int, cudaStream_t);
