@@ -614,8 +614,9 @@ __device__ __noinline__ double quad_combination(const float* __restrict__ chi, c
 // order); a list index starts a group when its group differs from the
 // previous index's.  Counts per warp, one grid barrier for the per-block
 // totals, then ordered writes at the warp's offset (warp ballots, no block
-// barrier in the loop).  Eight 32-index loads in flight per warp.  Returns
-// false if the kernel must stop.
+// barrier in the loop), then a grid barrier: the passes read entries other
+// CTAs wrote.  Eight 32-index loads in flight per warp.  Returns false if
+// the kernel must stop.
 template <typename T>
 __device__ bool build_quads(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int ncomp, Ctl& c, unsigned& bar,
                             int& red) {
@@ -685,7 +686,7 @@ __device__ bool build_quads(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int n
       base += __popc(bal);
     }
   }
-  return true;
+  return grid_barrier(a.st, bar, 26);
 }
 
 // Output fields of the adjoint modes: out[r][p] = (y(t_k) + shift_r w_1)[p]
