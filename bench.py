@@ -663,6 +663,31 @@ def run_adjoint(etd, dev, precision, nsteps=100, every=10, nquad=8):
             "fd_max_rel_err": _r(max(errs)), "fd_entries": len(errs)}
 
 
+# FP64 FMA instructions per second measured on this GPU (a dependent-free
+# FMA loop): 1.005 TFLOP/s; nominal 152 SMs x 2 FP64 FMA per clock x 2.07 GHz.
+FP64_OPS_MEASURED = 502.7e9
+FP64_OPS_NOMINAL = 152 * 2 * 2.07e9
+
+
+def krylov_fp64_ops(ncomp, iters, subs):
+    """FP64 operations (add, mul, fma: 1 each) of one FP64 Krylov launch on a
+    large problem (split passes), as the kernel formulates the method: the
+    ETD2 set-up 8 per point; per substep the w_1 pass 10 (7-point stencil 8,
+    two terms), the w_2 pass 9, P_0 9 (stencil on B = A / cfac 7, two sums),
+    per Krylov vector 13 (V_j = ca Z + cb V_{j-1} + cc V_{j-2}: 3; Z = B V_j:
+    7; three sums), and the combination m + 3."""
+    return ncomp * (8 + subs * 31 + iters * 14)
+
+
+def krylov_bytes_two_pass(ncomp, iters, subs, s):
+    """Algorithmic bytes with the two passes per Krylov vector that the large
+    problems run (7s + b per point and vector: pass A reads Z_{j-1}, V_{j-1},
+    V_{j-2} and writes V_j; pass B reads V_j, V_{j-1}, writes Z_j), the rest
+    as krylov_bytes."""
+    b = (8.0 if s == 8 else 4.0) + 4.0
+    return ncomp * (iters * (7 * s + b) + subs * 2 * (3 * s + b) + (iters + 2 * subs) * s + subs * 16 + 48)
+
+
 def run_stress(etd, stream, dev, steps, n=512, precisions="both"):
     """Bandwidth stress shape: ETD2 steps on a fixed ball of radius 7 in a
     512^3 grid over [-8, 8]^3 (vectors far above L2), FP64 and FP32-mixed.
@@ -690,7 +715,7 @@ def run_stress(etd, stream, dev, steps, n=512, precisions="both"):
             ctx.init_domain(0, phi)
             ctx.step(w.dt, [u])  # warm-up (first step: ETD1)
             ctx.sync()
-            t, bytes_, iters, subs, cells = 0.0, 0.0, 0, 0, 0
+            t, bytes_, bytes2, fops, iters, subs, cells = 0.0, 0.0, 0.0, 0.0, 0, 0, 0
             for _ in range(steps):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -702,13 +727,22 @@ def run_stress(etd, stream, dev, steps, n=512, precisions="both"):
                 iters += st["krylov_iters"]
                 subs += st["substeps"]
                 cells += st["ncomp"]
-                bytes_ += krylov_bytes(st["ncomp"], st["krylov_iters"], st["substeps"], 8 if precision == "fp64" else 4)
+                sb = 8 if precision == "fp64" else 4
+                bytes_ += krylov_bytes(st["ncomp"], st["krylov_iters"], st["substeps"], sb)
+                bytes2 += krylov_bytes_two_pass(st["ncomp"], st["krylov_iters"], st["substeps"], sb)
+                fops += krylov_fp64_ops(st["ncomp"], st["krylov_iters"], st["substeps"])
         del ctx
         torch.cuda.empty_cache()
-        out[precision] = {"ms_per_step": 1e3 * t / steps, "mcell_updates_per_s": cells / t / 1e6,
-                          "krylov_iters_per_step": iters / steps, "substeps_per_step": subs / steps,
-                          "ncomp": cells // steps, "achieved_gbs": bytes_ / t / 1e9,
-                          "frac_of_hbm": bytes_ / t / 1e9 / hbm}
+        out[precision] = {"ms_per_step": _r(1e3 * t / steps), "mcell_updates_per_s": _r(cells / t / 1e6),
+                          "krylov_iters_per_step": _r(iters / steps), "substeps_per_step": _r(subs / steps),
+                          "ncomp": cells // steps, "achieved_gbs": _r(bytes_ / t / 1e9),
+                          "frac_of_hbm": _r(bytes_ / t / 1e9 / hbm),
+                          "frac_of_hbm_two_pass_bytes": _r(bytes2 / t / 1e9 / hbm)}
+        if precision == "fp64":
+            # FP64 issue bounds these passes: against the FP64 operation rate
+            out[precision].update({"fp64_gops": _r(fops / t / 1e9),
+                                   "frac_of_fp64_measured": _r(fops / t / FP64_OPS_MEASURED),
+                                   "frac_of_fp64_nominal": _r(fops / t / FP64_OPS_NOMINAL)})
     out["peak_gbs"] = hbm
     return out
 

@@ -1,4 +1,6 @@
 // C ABI: context, workspace carving, argument checks and launches.
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -70,6 +72,13 @@ struct etd_ctx {
 };
 
 namespace {
+
+// NVTX range over an entry point (a named range on the host timeline of a
+// profiler; header-only NVTX, inert without one)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 struct Carver {
   char* base;
@@ -485,6 +494,7 @@ void etd_destroy(etd_ctx* ctx) { delete ctx; }
 const char* etd_last_error(const etd_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
 etd_status etd_init_domain(etd_ctx* c, int species, const double* phi, const double* beta_field) {
+  Range range("etd_init_domain");
   if (!c) return ETD_ERR_ARG;
   if (species < 0 || species >= c->par.nspecies || !phi) return fail(c, ETD_ERR_ARG, "bad species or phi");
   SpeciesBufs& b = c->sp[species];
@@ -536,6 +546,7 @@ etd_status etd_init_domain(etd_ctx* c, int species, const double* phi, const dou
 }
 
 etd_status etd_step(etd_ctx* c, double dt, double* const* u, etd_step_stats* stats) {
+  Range range("etd_step");
   if (!c) return ETD_ERR_ARG;
   if (!u || !(dt > 0.0)) return fail(c, ETD_ERR_ARG, "u missing or dt <= 0");
   for (int s = 0; s < c->par.nspecies; ++s) {
@@ -560,6 +571,7 @@ etd_status etd_step(etd_ctx* c, double dt, double* const* u, etd_step_stats* sta
 
 etd_status etd_phi_combination(etd_ctx* c, int species, double dt, const double* v0, const double* v1,
                                const double* v2, double* y, etd_step_stats* stats) {
+  Range range("etd_phi_combination");
   if (!c) return ETD_ERR_ARG;
   if (species < 0 || species >= c->par.nspecies || !v0 || !v1 || !v2 || !y || !(dt > 0.0))
     return fail(c, ETD_ERR_ARG, "bad arguments");
@@ -572,6 +584,7 @@ etd_status etd_phi_combination(etd_ctx* c, int species, double dt, const double*
 
 etd_status etd_phi_combination3(etd_ctx* c, int species, double dt, const double* v0, const double* v1,
                                 const double* v2, const double* v3, double* y, etd_step_stats* stats) {
+  Range range("etd_phi_combination3");
   if (!c) return ETD_ERR_ARG;
   if (species < 0 || species >= c->par.nspecies || !v0 || !v1 || !v2 || !v3 || !y || !(dt > 0.0))
     return fail(c, ETD_ERR_ARG, "bad arguments");
@@ -625,6 +638,7 @@ etd_status etd_set_boundary_values(etd_ctx* c, int species, const double* values
 
 etd_status etd_poisson_solve(etd_ctx* c, int species, const double* f, double* u, double tol, int max_iter,
                              int* iters, double* rel_resid) {
+  Range range("etd_poisson_solve");
   if (!c) return ETD_ERR_ARG;
   if (species < 0 || species >= c->par.nspecies || !f || !u || !(tol > 0.0) || max_iter < 1)
     return fail(c, ETD_ERR_ARG, "bad arguments");
@@ -664,6 +678,7 @@ etd_status etd_set_reaction(etd_ctx* c, int reaction, const double* rp) {
 
 etd_status etd_step_explicit(etd_ctx* c, int species, double dt, const double* u_n, const double* u_nm1,
                              double* u_out, etd_step_stats* stats) {
+  Range range("etd_step_explicit");
   if (!c) return ETD_ERR_ARG;
   if (species < 0 || species >= c->par.nspecies || !u_n || !u_nm1 || !u_out || !(dt > 0.0) || u_out == u_n ||
       u_out == u_nm1)
@@ -709,6 +724,7 @@ static void gauss_legendre01(int n, double* t, double* w) {
 
 etd_status etd_adjoint_step(etd_ctx* c, int species, double dt, const double* u_n, const double* u_nm1, int first,
                             double* lam, double* acc, double* grad_beta, double* grad_params, int nquad) {
+  Range range("etd_adjoint_step");
   if (!c) return ETD_ERR_ARG;
   if (!c->par.adjoint || !c->facew) return fail(c, ETD_ERR_ARG, "context created without params.adjoint");
   if (species != 0 || !u_n || !u_nm1 || !lam || !acc || !grad_beta || !grad_params || !(dt > 0.0) || nquad < 1 ||
@@ -804,6 +820,7 @@ etd_status etd_adjoint_step(etd_ctx* c, int species, double dt, const double* u_
 }
 
 etd_status etd_apply_operator(etd_ctx* c, int species, double dt, const double* x, double* y) {
+  Range range("etd_apply_operator");
   if (!c) return ETD_ERR_ARG;
   if (species < 0 || species >= c->par.nspecies || !x || !y) return fail(c, ETD_ERR_ARG, "bad arguments");
   if (!c->sp[species].ready) return fail(c, ETD_ERR_ARG, "etd_init_domain not called");
@@ -843,6 +860,7 @@ etd_status etd_set_wait_limit(etd_ctx* c, double seconds) {
 }
 
 etd_status etd_sync(etd_ctx* c) {
+  Range range("etd_sync");
   if (!c) return ETD_ERR_ARG;
   return read_status(c);
 }
@@ -869,6 +887,7 @@ etd_status etd_read_domain(etd_ctx* c, int species, int* ncomp, int* nclamp, dou
 }
 
 etd_status levelset_advance(etd_ctx* c, int species, double* phi, double* u, double dt, int do_reinit) {
+  Range range("levelset_advance");
   if (!c) return ETD_ERR_ARG;
   if (species < 0 || species >= c->par.nspecies || !phi || !u || !(dt > 0.0))
     return fail(c, ETD_ERR_ARG, "bad arguments");
@@ -888,6 +907,7 @@ etd_status levelset_last_stats(etd_ctx* c, int* info) {
 }
 
 etd_status levelset_prepare(etd_ctx* c, double* phi, int do_reinit) {
+  Range range("levelset_prepare");
   if (!c) return ETD_ERR_ARG;
   if (!phi) return fail(c, ETD_ERR_ARG, "phi is NULL");
   cudaError_t e = launch_levelset_prepare(c->g, c->ls, c->st, phi, do_reinit != 0, c->fp32, c->stream);

@@ -327,6 +327,11 @@ def test_free_boundary_disc_multistep(lib):
     assert both.all()
     assert np.max(np.abs(ph_g - ph_o)) <= 1e-10 * g.h
     assert np.max(np.abs(u_g - u_o)) <= 1e-10 * np.max(np.abs(u_o))
+    # nodes that entered the domain during the run (their F_{n-1} starts as
+    # F_n, the reading for points that were not computational): same values
+    entered = (ph_o < -1e-12) & (w.phi0[0] >= 0)
+    assert entered.sum() > 0
+    assert np.max(np.abs(u_g - u_o)[entered]) <= 1e-10 * np.max(np.abs(u_o))
 
 
 def test_two_species_competition_multistep(lib):
