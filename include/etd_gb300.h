@@ -361,6 +361,15 @@ etd_status etd_phi_combination_noalloc(const etd_grid* grid, const double* phi, 
                                        const double* v0, const double* v1, const double* v2, double* y,
                                        double krylov_tol, int m_max, void* stream);
 
+/* Self-check of the library's FP64 -> FP32 rounding (round to nearest, ties
+ * to even), which the FP32-mixed contexts use on the integer pipe for the
+ * FP32 copies of y, v_1, v_2 and v_3: for i < n, lib[i] = that rounding of
+ * x[i] and hw[i] = the hardware conversion of x[i].  x, lib and hw are device
+ * pointers of n elements (caller-owned); stream is a cudaStream_t (NULL: the
+ * default stream).  Synchronises the stream; ETD_ERR_ARG for n < 0 or a NULL
+ * pointer with n > 0, ETD_ERR_CUDA for a launch failure. */
+etd_status etd_selfcheck_round_f32(const double* x, float* lib, float* hw, long long n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

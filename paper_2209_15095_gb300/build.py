@@ -14,7 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIBNAME = "libetd_gb300.so"
-SOURCES = ["eb.cu", "krylov.cu", "levelset.cu", "adjoint.cu", "poisson.cu", "abi.cu", "noalloc.cu"]
+SOURCES = ["eb.cu", "krylov.cu", "krylov_f64.cu", "krylov_f32.cu", "krylov_f32w.cu", "levelset.cu", "adjoint.cu",
+           "poisson.cu", "abi.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
           "-I" + CSRC, "--expt-relaxed-constexpr"]

@@ -32,6 +32,7 @@ struct SpeciesBufs {
   double* stg[3] = {nullptr, nullptr, nullptr};  // ETD3RK / ETD4RK stage fields
   int* qidx = nullptr;  // FP32 contexts: aligned 4-node groups of the large split passes
   int* qk = nullptr;
+  int* qmeta = nullptr;  // the list's validity flag and length (zeroed by every domain set-up)
   const double* beta_field = nullptr;
   // boundary data (params.boundary_data): per point, face and slot
   double* bco = nullptr;
@@ -222,6 +223,7 @@ size_t carve(const GridDev& g, const etd_params& p, char* base, etd_ctx* c) {
     if (f32) {
       b.qidx = cv.take<int>(G / 4 + 1);
       b.qk = cv.take<int>(G / 4 + 1);
+      b.qmeta = cv.take<int>(2);
     }
     if (c) c->sp[sp] = b;
   }
@@ -340,6 +342,7 @@ SpeciesDev<T> species_dev(etd_ctx* c, int s, double* u, int stage = 0) {
   for (int i = 0; i < 3; ++i) d.stg[i] = b.stg[i];
   d.qidx = sizeof(T) == 4 ? b.qidx : nullptr;
   d.qk = sizeof(T) == 4 ? b.qk : nullptr;
+  d.qmeta = sizeof(T) == 4 ? b.qmeta : nullptr;
   return d;
 }
 
@@ -539,7 +542,11 @@ etd_status etd_init_domain(etd_ctx* c, int species, const double* phi, const dou
   ma.bpts = b.bpts;
   ma.gersh = &c->st->gersh[species];
   ma.st = c->st;
-  cudaError_t e = launch_init_domain(ca, ma, c->tile_count, b.ncomp, c->stream);
+  cudaError_t e = cudaSuccess;
+  // the Krylov kernel's 4-node group list belongs to the previous domain
+  if (b.qmeta) e = cudaMemsetAsync(b.qmeta, 0, 2 * sizeof(int), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "init_domain group list reset");
+  e = launch_init_domain(ca, ma, c->tile_count, b.ncomp, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "init_domain launch");
   b.ready = true;
   return ETD_OK;
@@ -857,6 +864,13 @@ etd_status etd_set_wait_limit(etd_ctx* c, double seconds) {
   e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
   return ETD_OK;
+}
+
+etd_status etd_selfcheck_round_f32(const double* x, float* lib, float* hw, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !lib || !hw))) return ETD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (launch_round_check(x, lib, hw, n, st) != cudaSuccess) return ETD_ERR_CUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? ETD_OK : ETD_ERR_CUDA;
 }
 
 etd_status etd_sync(etd_ctx* c) {

@@ -160,15 +160,19 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Staging area of the block reductions: up to 3 quantities of up to 512
-// threads, one instance per kernel.
-constexpr int RED_MAX_NQ = 3, RED_MAX_NT = 512;
+// Staging area of the block reductions: up to 3 quantities of up to
+// RED_MAX_NT threads, one instance per kernel (a translation unit may raise
+// the thread count by defining ETD_RED_MAX_NT first).
+#ifndef ETD_RED_MAX_NT
+#define ETD_RED_MAX_NT 512
+#endif
+constexpr int RED_MAX_NQ = 3, RED_MAX_NT = ETD_RED_MAX_NT;
 __device__ __forceinline__ double* red_stage() {
   __shared__ double s_stage[RED_MAX_NQ * RED_MAX_NT];
   return s_stage;
 }
 
-// Sum of NQ per-thread values over the block (blockDim.x <= 512); thread 0
+// Sum of NQ per-thread values over the block (blockDim.x <= RED_MAX_NT); thread 0
 // of warp q writes the block's total of quantity q to
 // part[q * MAX_BLOCKS + blockIdx.x].  The values go through shared memory
 // and warp q sums quantity q (lane-strided, then a warp tree): FP64 adds run

@@ -93,6 +93,10 @@ struct SpeciesDev {
   // 4 + 1 entries each; nullptr: no quad path)
   int* qidx;
   int* qk;
+  // qmeta[0] = 1 when qidx / qk hold the list of the current domain (the
+  // host zeroes it with every domain set-up), qmeta[1] = the list length;
+  // nullptr: the list is built by every launch
+  int* qmeta;
   // caller's source (full grid) and boundary data for this launch: F gains
   // src[p] + sum over the point's face slots of bco * bval (nullptr: none)
   const double* src;
@@ -155,6 +159,16 @@ struct PhipmArgs {
 template <typename T>
 cudaError_t launch_phipm(const PhipmArgs<T>& a, int nblocks, cudaStream_t stream);
 int phipm_max_blocks(int ndim, bool fp32);
+// The Krylov kernels of one precision and CTA size (krylov_impl.cuh):
+// fn[ndim - 2][adjoint instantiation], threads per CTA, the adjoint
+// instantiation's dynamic shared memory, and the loader of the unit's
+// constant table.
+struct PhipmKernels {
+  void* fn[3][2];
+  int nt;
+  size_t adj_smem;
+  cudaError_t (*load_consts)();
+};
 
 // Embedded-boundary Poisson solve by conjugate gradients (FP64)
 struct PoissonArgs {
@@ -183,6 +197,7 @@ struct ApplyArgs {
   double* y;
 };
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t stream);
+cudaError_t launch_round_check(const double* x, float* lib, float* hw, long long n, cudaStream_t stream);
 
 // ---------------------------------------------------------------- adjoint
 struct AdjointArgs {

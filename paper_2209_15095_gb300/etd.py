@@ -95,6 +95,7 @@ def library():
         "levelset_prepare": (I, [P, P, I]),
         "etd_sync": (I, [P]),
         "etd_set_wait_limit": (I, [P, D]),
+        "etd_selfcheck_round_f32": (I, [P, P, P, ctypes.c_longlong, P]),
         "etd_last_stats": (I, [P, ctypes.POINTER(StepStats)]),
         "levelset_last_stats": (I, [P, ctypes.POINTER(I)]),
         "etd_read_domain": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), P, P, P, I]),
@@ -124,6 +125,22 @@ def _ptr(t, shape=None, name="tensor"):
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
     return ctypes.c_void_p(t.data_ptr())
+
+
+def selfcheck_round_f32(x):
+    """The library's FP64 -> FP32 rounding (round to nearest, ties to even,
+    on the integer pipe) and the hardware conversion of every element of x
+    (a contiguous float64 CUDA tensor): returns (lib, hw), two float32 tensors
+    of x's shape."""
+    xp = _ptr(x, name="x")
+    lib_out = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    hw_out = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    stream = ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+    rc = library().etd_selfcheck_round_f32(xp, ctypes.c_void_p(lib_out.data_ptr()), ctypes.c_void_p(hw_out.data_ptr()),
+                                           x.numel(), stream)
+    if rc != 0:
+        raise EtdError(rc, "etd_selfcheck_round_f32 failed")
+    return lib_out, hw_out
 
 
 class Context:
