@@ -84,6 +84,7 @@ struct Ctl {
   int trace0;  // trace entries of earlier launches of the step (block 0)
   int nquad, qoff;  // quad list: length, and this block's first entry
   int qcached;      // the list of the current domain is already built
+  int nq_sp[2];     // per species: list length (0: no quad path)
 };
 
 // ---------------------------------------------------------------------------
@@ -942,6 +943,113 @@ __device__ __noinline__ bool adj_y_outputs(const PhipmArgs<T>& a, const SpeciesD
   return grid_barrier(a.st, bar, 25);
 }
 
+// Whether a species takes the quad path: FP32 vectors, at least SPLIT_MIN
+// points, a group list in the workspace, constant beta, the last axis a
+// multiple of 4 nodes.
+template <typename T, int N>
+__device__ __forceinline__ bool use_quads(const SpeciesDev<T>& S, const GridDev& g, int ncomp) {
+  return sizeof(T) == 4 && ncomp >= SPLIT_MIN<T> && S.qidx != nullptr && S.beta_field == nullptr &&
+         (g.n[N - 1] & 3) == 0;
+}
+
+// Makes the species' group list ready and records its length in
+// c.nq_sp[sidx].  The list is built once per domain: the flag is read
+// before this launch's build can set it (block 0 sets it after the build's
+// last grid barrier, which every CTA reaches only after reading it).
+template <typename T>
+__device__ bool ensure_quads(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int sidx, int ncomp, Ctl& c,
+                             unsigned& bar, int& red) {
+  if (threadIdx.x == 0) {
+    c.qcached = S.qmeta != nullptr && __ldcg(S.qmeta) == 1;
+    if (c.qcached) c.nquad = __ldcg(S.qmeta + 1);
+  }
+  __syncthreads();
+  if (!c.qcached) {
+    if (!build_quads<T>(a, S, ncomp, c, bar, red)) return false;
+    if (S.qmeta != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+      S.qmeta[1] = c.nquad;
+      S.qmeta[0] = 1;
+    }
+  }
+  if (threadIdx.x == 0) c.nq_sp[sidx] = c.nquad;
+  __syncthreads();
+  return true;
+}
+
+// The ETD2 set-up (one species, F from the reaction alone, no F_{n-2}) on
+// the groups of 4 nodes: per group 16-byte loads and stores of u, F_{n-1},
+// the validity bytes and the FP32 copy of y, and the compact y, v_1, v_2 at
+// the group's list indices; per computational point the arithmetic of the
+// per-point set-up.  Nodes of the group off the computational set keep
+// their F_{n-1} and validity bytes (rewritten unchanged) and get y = 0 in
+// the FP32 copy.  sums: this thread's |y|^2, |v_1|^2, |v_2|^2 of the stored
+// FP32 values.
+static __device__ __noinline__ void quad_setup_etd2(const PhipmArgs<float>& a, const SpeciesDev<float>& S, int nq,
+                                                    long long gtid, long long gth, double* sums) {
+  const bool u16 = (reinterpret_cast<uintptr_t>(S.u) & 15u) == 0;
+  AccG sy, s1, s2;
+  quad_loop(S.qidx, S.qk, nq, gtid, gth, [&](long long p4, int k0, long long pn4) {
+    if (pn4 >= 0) {
+      prefetch_l2(S.u + pn4);
+      prefetch_l2(S.Fprev + pn4);
+    }
+    const unsigned kw = __ldg(reinterpret_cast<const unsigned*>(S.kind + p4));
+    const unsigned fw = __ldcg(reinterpret_cast<const unsigned*>(S.fvalid + p4));
+    double u[4], fp[4];
+    if (u16) {
+      const double2 u0 = __ldcg(reinterpret_cast<const double2*>(S.u + p4));
+      const double2 u1 = __ldcg(reinterpret_cast<const double2*>(S.u + p4 + 2));
+      u[0] = u0.x;
+      u[1] = u0.y;
+      u[2] = u1.x;
+      u[3] = u1.y;
+    } else {
+#pragma unroll
+      for (int l = 0; l < 4; ++l) u[l] = __ldcg(S.u + p4 + l);
+    }
+    {
+      const double2 f0 = __ldcg(reinterpret_cast<const double2*>(S.Fprev + p4));
+      const double2 f1 = __ldcg(reinterpret_cast<const double2*>(S.Fprev + p4 + 2));
+      fp[0] = f0.x;
+      fp[1] = f0.y;
+      fp[2] = f1.x;
+      fp[3] = f1.y;
+    }
+    float yg[4], v1f[4], v2f[4];
+    unsigned fwn = fw;
+    int r = 0;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      yg[l] = v1f[l] = v2f[l] = 0.f;
+      if (((kw >> (8 * l)) & 3u) != K_COMP) continue;
+      const double F = reaction(a.reaction, a.rp, 0, u[l], 0.0);
+      const double Fp = ((fw >> (8 * l)) & 1u) ? fp[l] : F;
+      const double v1 = a.dt * F;
+      const double v2 = a.etd1 ? 0.0 : a.dt * (F - Fp);
+      const long long k = k0 + r;
+      ++r;
+      yg[l] = to_f32_rn(u[l]);
+      v1f[l] = to_f32_rn(v1);
+      v2f[l] = to_f32_rn(v2);
+      S.Yc[k] = u[l];
+      S.V1c[k] = v1f[l];
+      S.V2c[k] = v2f[l];
+      fp[l] = F;
+      fwn = (fwn & ~(0xffu << (8 * l))) | (1u << (8 * l));
+    }
+    st4(S.Yg + p4, make_float4(yg[0], yg[1], yg[2], yg[3]));
+    __stcg(reinterpret_cast<double2*>(S.Fprev + p4), make_double2(fp[0], fp[1]));
+    __stcg(reinterpret_cast<double2*>(S.Fprev + p4 + 2), make_double2(fp[2], fp[3]));
+    __stcg(reinterpret_cast<unsigned*>(S.fvalid + p4), fwn);
+    sy.add4(yg, yg);
+    s1.add4(v1f, v1f);
+    s2.add4(v2f, v2f);
+  });
+  sums[0] = sy.value();
+  sums[1] = s1.value();
+  sums[2] = s2.value();
+}
+
 template <typename T, int N, bool ADJ>
 __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int sidx, Ctl& c, unsigned& bar,
                               int& red, double ynorm2, double vscale) {
@@ -964,24 +1072,11 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   // per point); the Lanczos scalars take the factor: zfac = cfac
   const bool zb = sizeof(T) == 8 && split;
   const double zfac = zb ? a.cfac : 1.0;
-  const bool quad = sizeof(T) == 4 && split && S.qidx != nullptr && S.beta_field == nullptr &&
-                    (g.n[N - 1] & 3) == 0;
+  // the group list was made ready at kernel start (ensure_quads)
+  const bool quad = use_quads<T, N>(S, g, ncomp);
   if (quad) {
-    // the list is built once per domain: the flag is read before this
-    // launch's build can set it (block 0 sets it after the build's last
-    // grid barrier, which every CTA reaches only after reading it)
-    if (threadIdx.x == 0) {
-      c.qcached = S.qmeta != nullptr && __ldcg(S.qmeta) == 1;
-      if (c.qcached) c.nquad = __ldcg(S.qmeta + 1);
-    }
+    if (threadIdx.x == 0) c.nquad = c.nq_sp[sidx];
     __syncthreads();
-    if (!c.qcached) {
-      if (!build_quads<T>(a, S, ncomp, c, bar, red)) return false;
-      if (S.qmeta != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
-        S.qmeta[1] = c.nquad;
-        S.qmeta[0] = 1;
-      }
-    }
   }
   // the statistics accumulate over the launches of one step (zeroed by the host)
   if (blockIdx.x == 0 && threadIdx.x == 0) c.trace0 = a.stats ? a.stats->trace_len[sidx] : 0;
@@ -1485,10 +1580,28 @@ __global__ void __launch_bounds__(NT, 1) phipm_kernel(const PhipmArgs<T> a) {
   if (a.mode == MODE_STAGE)
     for (int i = 0; i < 4; ++i)
       for (int j = 0; j < 3; ++j) need[i] = need[i] || a.stage.coef[j][i] != 0.0;
+  // the group lists of the species on the quad path (built once per domain)
+  for (int s = 0; s < a.nspecies; ++s) {
+    if (threadIdx.x == 0) c.nq_sp[s] = 0;
+    __syncthreads();
+    if (use_quads<T, N>(a.sp[s], g, *a.sp[s].ncomp) && !ensure_quads<T>(a, a.sp[s], s, *a.sp[s].ncomp, c, bar, red))
+      return;
+  }
   for (int s = 0; s < a.nspecies; ++s) {
     const SpeciesDev<T>& S = a.sp[s];
     const int ncomp = *S.ncomp;
     Acc<double> acc, acc1, acc2, acc3;
+    if constexpr (sizeof(T) == 4) {
+      if (c.nq_sp[s] > 0 && a.mode == MODE_ETD2 && a.nspecies == 1 && !a.ms3 && !S.src && !S.bco) {
+        double q3[3];
+        quad_setup_etd2(a, S, c.nq_sp[s], gtid, gthreads, q3);
+        sums[s][0] = q3[0];
+        sums[s][1] = q3[1];
+        sums[s][2] = q3[2];
+        sums[s][3] = 0.0;
+        continue;
+      }
+    }
     // the other modes: norms of the stored values (FP32 contexts: error-free
     // FP32 pairs, no FP64 work)
     Acc<T> at, at1, at2, at3;
@@ -1659,33 +1772,56 @@ __global__ void __launch_bounds__(NT, 1) phipm_kernel(const PhipmArgs<T> a) {
         if (pp[q] >= 0) dst[pp[q]] = add ? b[q] + y[q] : y[q];
     });
     if (outf != 0) continue;  // stage fields are read at computational points only
-    // Off the computational set: u = 0 and the validity bits cleared.  A
-    // lane per pair of nodes, consecutive pairs on consecutive lanes (2-byte
-    // kind and validity accesses, 16-byte zero stores where u is 16-byte
-    // aligned); a pair with one computational node stores the other alone.
-    const long long npair = g.size >> 1;
+    // Off the computational set: u = 0 and the validity bits cleared (the
+    // set-up wrote those of the computational points).  A lane per block of
+    // 16 consecutive nodes, consecutive blocks on consecutive lanes: one
+    // 16-byte load of their classes, 16-byte zero stores of u by pairs
+    // where u is 16-byte aligned, one 16-byte read-modify-write of their
+    // validity bytes; a block of computational nodes only is skipped.  Per
+    // class word, t has byte i = 1 when node i is not computational (class
+    // bits x = 2 ^ (kind & 3) nonzero).  The last size % 16 nodes, or every
+    // node if the class or validity array is not 16-byte aligned, one per lane.
     const bool u16 = (reinterpret_cast<uintptr_t>(S.u) & 15u) == 0;
-    const uchar2* kind2 = reinterpret_cast<const uchar2*>(S.kind);
-    uchar2* valid2 = reinterpret_cast<uchar2*>(S.fvalid);
+    const bool b16 = ((reinterpret_cast<uintptr_t>(S.kind) | reinterpret_cast<uintptr_t>(S.fvalid)) & 15u) == 0;
+    const long long nblk = b16 ? g.size >> 4 : 0;
     const long long ptid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (long long c = ptid; c < npair; c += gthreads) {
-      const uchar2 kv = __ldg(kind2 + c);
-      const bool c0 = (kv.x & 3) == K_COMP, c1 = (kv.y & 3) == K_COMP;
-      const long long p = c << 1;
-      if (!c0 && !c1 && u16) {
-        reinterpret_cast<double2*>(S.u)[c] = make_double2(0.0, 0.0);
-      } else {
-        if (!c0) S.u[p] = 0.0;
-        if (!c1) S.u[p + 1] = 0.0;
+    for (long long b = ptid; b < nblk; b += gthreads) {
+      const uint4 kv = __ldg(reinterpret_cast<const uint4*>(S.kind) + b);
+      const unsigned kw[4] = {kv.x, kv.y, kv.z, kv.w};
+      unsigned t[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const unsigned x = (kw[j] & 0x03030303u) ^ 0x02020202u;
+        t[j] = (x | (x >> 1)) & 0x01010101u;
       }
-      // the set-up wrote the bits of the computational points; 0 elsewhere
-      if (a.mode == MODE_ETD2 && !(c0 && c1)) {
-        const uchar2 old = valid2[c];
-        valid2[c] = make_uchar2(c0 ? old.x : (unsigned char)0, c1 ? old.y : (unsigned char)0);
+      if ((t[0] | t[1] | t[2] | t[3]) == 0u) continue;
+      double* ub = S.u + (b << 4);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (t[j] == 0u) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const bool n0 = (t[j] >> (16 * h)) & 1u, n1 = (t[j] >> (16 * h + 8)) & 1u;
+          double* up = ub + 4 * j + 2 * h;
+          if (n0 && n1 && u16) {
+            *reinterpret_cast<double2*>(up) = make_double2(0.0, 0.0);
+          } else {
+            if (n0) up[0] = 0.0;
+            if (n1) up[1] = 0.0;
+          }
+        }
+      }
+      if (a.mode == MODE_ETD2) {
+        uint4* vp = reinterpret_cast<uint4*>(S.fvalid) + b;
+        uint4 ov = __ldcg(vp);
+        ov.x &= ~(t[0] * 0xffu);
+        ov.y &= ~(t[1] * 0xffu);
+        ov.z &= ~(t[2] * 0xffu);
+        ov.w &= ~(t[3] * 0xffu);
+        __stcg(vp, ov);
       }
     }
-    if ((g.size & 1) && ptid == 0) {
-      const long long p = g.size - 1;
+    for (long long p = (nblk << 4) + ptid; p < g.size; p += gthreads) {
       if ((__ldg(S.kind + p) & 3) != K_COMP) {
         S.u[p] = 0.0;
         if (a.mode == MODE_ETD2) S.fvalid[p] = 0;

@@ -225,6 +225,39 @@ def test_etd2_step_from_state(lib, precision, tol):
         assert np.all(ug[~op.comp] == 0.0)
 
 
+def test_etd2_steps_large_mixed(lib):
+    """Two ETD2 steps of a large FP32-mixed problem (a ball of at least 2^18
+    points, last axis a multiple of 4): the set-up (F_n, the stored F_{n-1}
+    and its validity bytes, v_1, v_2), the Lanczos basis and the combination
+    all run on the 4-node groups.  Step 1 is ETD1 (no F_{n-1} yet), step 2
+    takes F_{n-1} from step 1; against the oracle at 1e-5."""
+    g, ph = _shape_phi(3, 140, 2.0, "ball")
+    op = EBOperator(g, ph, 1.0)
+    assert op.ncomp >= 1 << 18 and g.n[2] % 4 == 0
+    ctx = _ctx(lib, g, precision="mixed", tol=1e-7, m_max=40)
+    ctx.init_domain(0, _dev(ph))
+    rng = np.random.default_rng(31)
+    u0 = op.to_grid(rng.uniform(0, 1, op.ncomp))
+    du = torch.tensor(u0, device="cuda")
+    dt = 2.0 * g.h * g.h
+    st1 = ctx.step(dt, [du], stats=True)
+    u1g = du.cpu().numpy()
+    st2 = ctx.step(dt, [du], stats=True)
+    u2g = du.cpu().numpy()
+    assert st1[0]["krylov_iters"] >= 5 and st2[0]["krylov_iters"] >= 5
+    F = lambda v: v * (1 - v)
+    uc0 = op.from_grid(u0)
+    u1o, _ = oetd.etd2_step(op, uc0, F(uc0), F(uc0), dt, tol=1e-12, m_max=40)
+    u2o, _ = oetd.etd2_step(op, u1o, F(u1o), F(uc0), dt, tol=1e-12, m_max=40)
+    for ug, uo in ((u1g, u1o), (u2g, u2o)):
+        assert np.max(np.abs(op.from_grid(ug) - uo)) <= 1e-5 * np.max(np.abs(uo))
+        assert np.all(ug[~op.comp] == 0.0)
+    # the ETD2 correction itself (the F_{n-1} term) is resolved: step 2 from
+    # the ETD1 form would differ by more than the bound
+    u2e, _ = oetd.etd2_step(op, u1o, F(u1o), F(u1o), dt, tol=1e-12, m_max=40)
+    assert np.max(np.abs(u2e - u2o)) > 10 * 1e-5 * np.max(np.abs(u2o))
+
+
 @pytest.mark.parametrize("scheme", ["etd1", "etd2rk"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
 def test_etd1_etd2rk_steps_from_state(lib, scheme, precision, tol):
