@@ -85,6 +85,7 @@ struct Ctl {
   int nquad, qoff;  // quad list: length, and this block's first entry
   int qcached;      // the list of the current domain is already built
   int nq_sp[2];     // per species: list length (0: no quad path)
+  int wb_done[2];   // per species: the last combination wrote u (no write-back)
 };
 
 // ---------------------------------------------------------------------------
@@ -454,12 +455,24 @@ constexpr int QP_U = 1;
 
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
+// Top bit of a group's list entry qk: its 4 nodes are computational and
+// have the diagonal of a row whose 2N faces all reach computational
+// points, D = 2N beta (the domain set-up stores exactly that value there,
+// and a ghost face of weight 0 gives it too), so the passes take D without
+// loading it.
+constexpr int QK_FULL = (int)0x80000000u;
+constexpr int QK_INDEX = 0x7fffffff;
+template <typename T, int N>
+__device__ __forceinline__ float quad_d_int(const SpeciesDev<T>& S) {
+  return (float)((double)(2 * N) * S.beta_c);
+}
 // Loop over this thread's entries q = gtid, gtid + gth, ... of the group
 // list.  The entries (the group's index and its first list index) are
 // loaded two iterations ahead, so that an iteration's data loads never wait
-// on its index loads: body(p4, k0, pn4) gets the group's first node, its
-// first list index, and the first node of the thread's next group (-1 if
-// none), whose lines the body prefetches into L2.  With one 512-thread CTA
+// on its index loads: body(p4, k0, full, pn4) gets the group's first node,
+// its first list index, whether it is a full interior group (QK_FULL), and
+// the first node of the thread's next group (-1 if none), whose lines the
+// body prefetches into L2.  With one 512-thread CTA
 // per SM the passes are bound by the bytes in flight: the prefetches add to
 // them without registers.
 template <typename Body>
@@ -471,7 +484,7 @@ __device__ __forceinline__ void quad_loop(const int* __restrict__ qidx, const in
   for (; q < nq; q += gth) {
     const long long q2 = q + 2 * gth;
     const int pc = q2 < nq ? __ldg(qidx + q2) : -1, kc = q2 < nq ? __ldg(qk + q2) : 0;
-    body((long long)pa << 2, ka, pb >= 0 ? (long long)pb << 2 : -1ll);
+    body((long long)pa << 2, ka & QK_INDEX, ka < 0, pb >= 0 ? (long long)pb << 2 : -1ll);
     pa = pb;
     ka = kb;
     pb = pc;
@@ -498,7 +511,7 @@ __device__ __noinline__ QuadSums quad_pass_1(const float* __restrict__ Wp, const
                                              float c3, const uint8_t* __restrict__ kind,
                                              const float* __restrict__ diagf, const int* __restrict__ qidx,
                                              const int* __restrict__ qk, int nq, const GridDev& g, float cfac,
-                                             float bc, long long gtid, long long gth) {
+                                             float bc, float dint, long long gtid, long long gth) {
   constexpr int U = QP_U;
   long long st[N > 1 ? N - 1 : 1];
 #pragma unroll
@@ -524,9 +537,10 @@ __device__ __noinline__ QuadSums quad_pass_1(const float* __restrict__ Wp, const
       const long long q2 = q + (2 * U + u) * gth;
       pf[u] = q2 < nq ? __ldg(qidx + q2) : -1;
       kf[u] = q2 < nq ? __ldg(qk + q2) : 0;
-      if (pn[u] >= 0) {
+      if (pn[u] >= 0 && (pn[u] & 7) == 0) {
         // the next groups' own lines and those of their upper neighbours
-        // along the first axis (the only ones no earlier group brought in)
+        // along the first axis (the only ones no earlier group brought in),
+        // by the lane whose group starts a 128-byte line of the FP32 vectors
         const long long pn4 = (long long)pn[u] << 2;
         prefetch_l2(Wp + pn4);
         prefetch_l2(Vp + pn4);
@@ -541,7 +555,7 @@ __device__ __noinline__ QuadSums quad_pass_1(const float* __restrict__ Wp, const
     for (int u = 0; u < U; ++u) {
       if (pc[u] < 0) continue;
       const long long p4 = (long long)pc[u] << 2;
-      const int k0 = kc[u];
+      const int k0 = kc[u] & QK_INDEX;
       wc[u] = ld4(Wp + p4);
       vc[u] = ld4(Vp + p4);
       wl[u] = __ldcg(Wp + p4 - 1);
@@ -560,7 +574,9 @@ __device__ __noinline__ QuadSums quad_pass_1(const float* __restrict__ Wp, const
       }
       sacc[u] = sa;
       kw[u] = __ldg(reinterpret_cast<const unsigned*>(kind + p4));
-      dg[u] = make_float4(__ldg(diagf + k0), __ldg(diagf + k0 + 1), __ldg(diagf + k0 + 2), __ldg(diagf + k0 + 3));
+      dg[u] = kc[u] < 0 ? make_float4(dint, dint, dint, dint)
+                        : make_float4(__ldg(diagf + k0), __ldg(diagf + k0 + 1), __ldg(diagf + k0 + 2),
+                                      __ldg(diagf + k0 + 3));
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -610,13 +626,14 @@ __device__ __noinline__ QuadSums quad_stencil(const float* __restrict__ X, float
                                               const float* __restrict__ a3, float c2, float c3,
                                               const uint8_t* __restrict__ kind, const float* __restrict__ diagf,
                                               const int* __restrict__ qidx, const int* __restrict__ qk, int nq,
-                                              const GridDev& g, float cfac, float bc, long long gtid, long long gth) {
+                                              const GridDev& g, float cfac, float bc, float dint, long long gtid,
+                                              long long gth) {
   long long st[N > 1 ? N - 1 : 1];
 #pragma unroll
   for (int d = 0; d < N - 1; ++d) st[d] = g.stride[d];
   AccG d1, d2, d3;
-  quad_loop(qidx, qk, nq, gtid, gth, [&](long long p4, int k0, long long pn4) {
-    if (pn4 >= 0) {
+  quad_loop(qidx, qk, nq, gtid, gth, [&](long long p4, int k0, bool full, long long pn4) {
+    if (pn4 >= 0 && (pn4 & 31) == 0) {  // a lane per 128-byte line
       prefetch_l2(X + pn4);
       prefetch_l2(X + pn4 + st[0]);
     }
@@ -635,7 +652,7 @@ __device__ __noinline__ QuadSums quad_stencil(const float* __restrict__ X, float
     float dg[4], t1[4], t2[4], t3[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      dg[r] = __ldg(diagf + k0 + r);
+      dg[r] = full ? dint : __ldg(diagf + k0 + r);
       t1[r] = NT >= 1 ? __ldcg(a1 + k0 + r) : 0.f;
       t2[r] = NT >= 2 ? __ldcg(a2 + k0 + r) : 0.f;
       t3[r] = NT >= 3 ? __ldcg(a3 + k0 + r) : 0.f;
@@ -674,19 +691,22 @@ __device__ __noinline__ QuadSums quad_stencil(const float* __restrict__ X, float
 // multiple of 5 but for m_max or a breakdown (the error check runs every 5
 // vectors).  Measured per launch at 256^3 / 512^3 (10 / 20 vectors): 5 in
 // flight 1.378 / 14.11 ms, 8 1.376 / 14.01, 10 1.342 / 13.51, 16 1.390 / 13.72.  Writes y (compact,
-// FP64) and its FP32 grid copy (0 at the group's other nodes); returns this
-// thread's sum of the squares of the FP32 copy (the controller's scale).
+// FP64) and its FP32 grid copy (0 at the group's other nodes), and, for the
+// last substep, y into ufin at the computational points (the kernel then
+// skips its write-back); returns this thread's sum of the squares of the
+// FP32 copy (the controller's scale).
 static __device__ __noinline__ double quad_combination(const float* __restrict__ chi, const float* __restrict__ clo,
                                                        int m, double tau, const float* __restrict__ V, long long vs,
                                                        const float* __restrict__ W1g, const float* __restrict__ W2g,
                                                        double* __restrict__ Yc, float* __restrict__ Yg,
-                                                       const uint8_t* __restrict__ kind, const int* __restrict__ qidx,
+                                                       double* __restrict__ ufin, const uint8_t* __restrict__ kind,
+                                                       const int* __restrict__ qidx,
                                                        const int* __restrict__ qk, int nq, long long gtid,
                                                        long long gth) {
   Acc<float> yn;  // |y|^2 of the FP32 copy: the controller's scale only
   const double h2 = 0.5 * tau * tau;
-  quad_loop(qidx, qk, nq, gtid, gth, [&](long long p4, int k0, long long pn4) {
-    if (pn4 >= 0)
+  quad_loop(qidx, qk, nq, gtid, gth, [&](long long p4, int k0, bool, long long pn4) {
+    if (pn4 >= 0 && (pn4 & 31) == 0)  // a lane per 128-byte line
       for (int i = 0; i < m; ++i) prefetch_l2(V + (long long)i * vs + pn4);
     const unsigned kw = __ldg(reinterpret_cast<const unsigned*>(kind + p4));
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
@@ -714,12 +734,21 @@ static __device__ __noinline__ double quad_combination(const float* __restrict__
       double y = fma(tau, to_f64(w1l[l]), __ldcg(Yc + k)) + (to_f64(sl[l]) + to_f64(el[l]));
       if (W2g) y = fma(h2, to_f64(w2l[l]), y);
       Yc[k] = y;
+      if (ufin != nullptr) ufin[p4 + l] = y;
       yo[l] = to_f32_rn(y);
       yn.add(yo[l], yo[l]);
     }
     st4(Yg + p4, make_float4(yo[0], yo[1], yo[2], yo[3]));
   });
   return yn.value();
+}
+
+template <typename T, int N>
+__device__ __forceinline__ bool quad_full(const SpeciesDev<T>& S, int ncomp, int q, long long k) {
+  if (k + 3 >= ncomp || __ldg(S.idx + k + 3) != 4 * q + 3) return false;
+  const float di = quad_d_int<T, N>(S);
+  return __ldg(S.diagf + k) == di && __ldg(S.diagf + k + 1) == di && __ldg(S.diagf + k + 2) == di &&
+         __ldg(S.diagf + k + 3) == di;
 }
 
 // Builds the quad list from the sorted list of computational points: each
@@ -730,7 +759,7 @@ static __device__ __noinline__ double quad_combination(const float* __restrict__
 // barrier in the loop), then a grid barrier: the passes read entries other
 // CTAs wrote.  Eight 32-index loads in flight per warp.  Returns false if
 // the kernel must stop.
-template <typename T>
+template <typename T, int N>
 __device__ bool build_quads(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int ncomp, Ctl& c, unsigned& bar,
                             int& red) {
   constexpr int QU = 8;
@@ -793,8 +822,9 @@ __device__ bool build_quads(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int n
       const unsigned bal = __ballot_sync(0xffffffffu, head);
       if (head) {
         const int pos = base + __popc(bal & below);
+        const long long k = kb + u * 32 + lane;
         S.qidx[pos] = q[u];
-        S.qk[pos] = (int)(kb + u * 32 + lane);
+        S.qk[pos] = (int)k | (quad_full<T, N>(S, ncomp, q[u], k) ? QK_FULL : 0);
       }
       base += __popc(bal);
     }
@@ -956,7 +986,7 @@ __device__ __forceinline__ bool use_quads(const SpeciesDev<T>& S, const GridDev&
 // c.nq_sp[sidx].  The list is built once per domain: the flag is read
 // before this launch's build can set it (block 0 sets it after the build's
 // last grid barrier, which every CTA reaches only after reading it).
-template <typename T>
+template <typename T, int N>
 __device__ bool ensure_quads(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int sidx, int ncomp, Ctl& c,
                              unsigned& bar, int& red) {
   if (threadIdx.x == 0) {
@@ -965,7 +995,7 @@ __device__ bool ensure_quads(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int 
   }
   __syncthreads();
   if (!c.qcached) {
-    if (!build_quads<T>(a, S, ncomp, c, bar, red)) return false;
+    if (!build_quads<T, N>(a, S, ncomp, c, bar, red)) return false;
     if (S.qmeta != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
       S.qmeta[1] = c.nquad;
       S.qmeta[0] = 1;
@@ -988,8 +1018,8 @@ static __device__ __noinline__ void quad_setup_etd2(const PhipmArgs<float>& a, c
                                                     long long gtid, long long gth, double* sums) {
   const bool u16 = (reinterpret_cast<uintptr_t>(S.u) & 15u) == 0;
   AccG sy, s1, s2;
-  quad_loop(S.qidx, S.qk, nq, gtid, gth, [&](long long p4, int k0, long long pn4) {
-    if (pn4 >= 0) {
+  quad_loop(S.qidx, S.qk, nq, gtid, gth, [&](long long p4, int k0, bool, long long pn4) {
+    if (pn4 >= 0 && (pn4 & 15) == 0) {  // a lane per 128-byte line of the FP64 fields
       prefetch_l2(S.u + pn4);
       prefetch_l2(S.Fprev + pn4);
     }
@@ -1059,6 +1089,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
   const long long gthreads = (long long)gridDim.x * blockDim.x;
   const T cfac = (T)a.cfac;
   const T bc = (T)S.beta_c;
+  const float dint = quad_d_int<T, N>(S);  // the diagonal of the full groups (QK_FULL)
   const double anorm = a.dt * (*S.gersh);
   const int m_max = a.m_max;
   // highest phi index: 2 or 3 (any other value of a.p: 2); 0 for the basis
@@ -1109,19 +1140,19 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
         const float tt = (float)t;
         if (P == 3) {
           quad_stencil<N, 3, false>(S.Yg, S.W1g, S.V1c, S.V2c, S.V3c, tt, (float)(0.5 * t * t), S.kind, S.diagf,
-                          S.qidx, S.qk, nq, g, cfac, bc, gtid, gthreads);
+                          S.qidx, S.qk, nq, g, cfac, bc, dint, gtid, gthreads);
           if (!grid_barrier(a.st, bar, 10)) return false;
           quad_stencil<N, 2, false>(S.W1g, S.W2g, S.V2c, S.V3c, nullptr, tt, 0.f, S.kind, S.diagf, S.qidx, S.qk, nq, g,
-                          cfac, bc, gtid, gthreads);
+                          cfac, bc, dint, gtid, gthreads);
           if (!grid_barrier(a.st, bar, 16)) return false;
           quad_stencil<N, 1, false>(S.W2g, S.V, S.V3c, nullptr, nullptr, 0.f, 0.f, S.kind, S.diagf, S.qidx, S.qk, nq, g,
-                          cfac, bc, gtid, gthreads);
+                          cfac, bc, dint, gtid, gthreads);
         } else {
           quad_stencil<N, 2, false>(S.Yg, S.W1g, S.V1c, S.V2c, nullptr, tt, 0.f, S.kind, S.diagf, S.qidx, S.qk, nq, g,
-                          cfac, bc, gtid, gthreads);
+                          cfac, bc, dint, gtid, gthreads);
           if (!grid_barrier(a.st, bar, 10)) return false;
           quad_stencil<N, 1, false>(S.W1g, S.V, S.V2c, nullptr, nullptr, 0.f, 0.f, S.kind, S.diagf, S.qidx, S.qk, nq, g,
-                          cfac, bc, gtid, gthreads);
+                          cfac, bc, dint, gtid, gthreads);
         }
         qw = true;
       }
@@ -1189,7 +1220,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
     if constexpr (sizeof(T) == 4) {
       if (quad) {
         const QuadSums qs = quad_stencil<N, 0, true>(S.V, S.Z[0], nullptr, nullptr, nullptr, 0.f, 0.f, S.kind, S.diagf,
-                                            S.qidx, S.qk, c.nquad, g, cfac, bc, gtid, gthreads);
+                                            S.qidx, S.qk, c.nquad, g, cfac, bc, dint, gtid, gthreads);
         double v[3] = {qs.d1, qs.d2, qs.d3};
         pb = part_buf(a.part, red);
         block_partials<3>(v, pb);
@@ -1284,7 +1315,7 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
           const float c1 = (float)(sp / bj), c2 = (float)(-c.alpha[j - 1] * sp / bj), c3 = (float)(-bj * sp);
           const QuadSums qs = quad_pass_1<N>(S.Z[(j - 1) & 1], S.V + (long long)(j - 1) * vs, S.V + (long long)j * vs,
                                              S.Z[j & 1], c1, c2, c3, S.kind, S.diagf, S.qidx, S.qk, c.nquad, g, cfac,
-                                             bc, gtid, gthreads);
+                                             bc, dint, gtid, gthreads);
           double v[3] = {qs.d1, qs.d2, qs.d3};
           pb = part_buf(a.part, red);
           block_partials<3>(v, pb);
@@ -1497,8 +1528,11 @@ __device__ bool phipm_species(const PhipmArgs<T>& a, const SpeciesDev<T>& S, int
       bool qdone = false;
       if constexpr (sizeof(T) == 4) {
         if (quad) {
-          yn.s = quad_combination(c.chi, c.clo, m, tau, S.V, vs, S.W1g, P == 3 ? S.W2g : nullptr, S.Yc, S.Yg, S.kind,
-                                  S.qidx, S.qk, c.nquad, gtid, gthreads);
+          // the last substep of an ETD2 step or a combination writes u itself
+          double* ufin = c.last && (a.mode == MODE_ETD2 || a.mode == MODE_GIVEN) ? S.u : nullptr;
+          yn.s = quad_combination(c.chi, c.clo, m, tau, S.V, vs, S.W1g, P == 3 ? S.W2g : nullptr, S.Yc, S.Yg, ufin,
+                                  S.kind, S.qidx, S.qk, c.nquad, gtid, gthreads);
+          if (ufin != nullptr && threadIdx.x == 0) c.wb_done[sidx] = 1;
           qdone = true;
         }
       }
@@ -1582,9 +1616,12 @@ __global__ void __launch_bounds__(NT, 1) phipm_kernel(const PhipmArgs<T> a) {
       for (int j = 0; j < 3; ++j) need[i] = need[i] || a.stage.coef[j][i] != 0.0;
   // the group lists of the species on the quad path (built once per domain)
   for (int s = 0; s < a.nspecies; ++s) {
-    if (threadIdx.x == 0) c.nq_sp[s] = 0;
+    if (threadIdx.x == 0) {
+      c.nq_sp[s] = 0;
+      c.wb_done[s] = 0;
+    }
     __syncthreads();
-    if (use_quads<T, N>(a.sp[s], g, *a.sp[s].ncomp) && !ensure_quads<T>(a, a.sp[s], s, *a.sp[s].ncomp, c, bar, red))
+    if (use_quads<T, N>(a.sp[s], g, *a.sp[s].ncomp) && !ensure_quads<T, N>(a, a.sp[s], s, *a.sp[s].ncomp, c, bar, red))
       return;
   }
   for (int s = 0; s < a.nspecies; ++s) {
@@ -1758,7 +1795,7 @@ __global__ void __launch_bounds__(NT, 1) phipm_kernel(const PhipmArgs<T> a) {
     // a stage of ETD3RK / ETD4RK may write a stage field instead of u
     const int outf = a.mode == MODE_STAGE ? a.stage.out_field : 0;
     double* const dst = outf == 0 ? S.u : S.stg[outf - 1];
-    node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
+    if (!c.wb_done[s]) node_loop_sized<T>(gtid, gthreads, ncomp, S.idx, [&](const auto& kk, const auto& pp) {
       constexpr int U = NL_U(kk);
       double y[U], b[U];
 #pragma unroll
