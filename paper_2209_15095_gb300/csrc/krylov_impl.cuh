@@ -458,10 +458,13 @@ __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefe
 // Top bit of a group's list entry qk: its 4 nodes are computational and
 // have the diagonal of a row whose 2N faces all reach computational
 // points, D = 2N beta (the domain set-up stores exactly that value there,
-// and a ghost face of weight 0 gives it too), so the passes take D without
-// loading it.
+// and a ghost face of weight 0 gives it too), so the passes take D and the
+// class word without loading them.
 constexpr int QK_FULL = (int)0x80000000u;
 constexpr int QK_INDEX = 0x7fffffff;
+// the class word of a full group (4 computational nodes), not loaded
+constexpr unsigned QK_FULL_KIND = 0x02020202u;
+static_assert(K_COMP == 2, "QK_FULL_KIND holds K_COMP in every byte");
 template <typename T, int N>
 __device__ __forceinline__ float quad_d_int(const SpeciesDev<T>& S) {
   return (float)((double)(2 * N) * S.beta_c);
@@ -573,7 +576,7 @@ __device__ __noinline__ QuadSums quad_pass_1(const float* __restrict__ Wp, const
         sa.w += vnew(wm.w, vm.w) + vnew(wq.w, vq.w);
       }
       sacc[u] = sa;
-      kw[u] = __ldg(reinterpret_cast<const unsigned*>(kind + p4));
+      kw[u] = kc[u] < 0 ? QK_FULL_KIND : __ldg(reinterpret_cast<const unsigned*>(kind + p4));
       dg[u] = kc[u] < 0 ? make_float4(dint, dint, dint, dint)
                         : make_float4(__ldg(diagf + k0), __ldg(diagf + k0 + 1), __ldg(diagf + k0 + 2),
                                       __ldg(diagf + k0 + 3));
@@ -648,7 +651,7 @@ __device__ __noinline__ QuadSums quad_stencil(const float* __restrict__ X, float
       sacc.z += m.z + pq.z;
       sacc.w += m.w + pq.w;
     }
-    const unsigned kw = __ldg(reinterpret_cast<const unsigned*>(kind + p4));
+    const unsigned kw = full ? QK_FULL_KIND : __ldg(reinterpret_cast<const unsigned*>(kind + p4));
     float dg[4], t1[4], t2[4], t3[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -705,10 +708,10 @@ static __device__ __noinline__ double quad_combination(const float* __restrict__
                                                        long long gth) {
   Acc<float> yn;  // |y|^2 of the FP32 copy: the controller's scale only
   const double h2 = 0.5 * tau * tau;
-  quad_loop(qidx, qk, nq, gtid, gth, [&](long long p4, int k0, bool, long long pn4) {
+  quad_loop(qidx, qk, nq, gtid, gth, [&](long long p4, int k0, bool full, long long pn4) {
     if (pn4 >= 0 && (pn4 & 31) == 0)  // a lane per 128-byte line
       for (int i = 0; i < m; ++i) prefetch_l2(V + (long long)i * vs + pn4);
-    const unsigned kw = __ldg(reinterpret_cast<const unsigned*>(kind + p4));
+    const unsigned kw = full ? QK_FULL_KIND : __ldg(reinterpret_cast<const unsigned*>(kind + p4));
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
 #pragma unroll 10
     for (int i = 0; i < m; ++i) {
@@ -1018,12 +1021,12 @@ static __device__ __noinline__ void quad_setup_etd2(const PhipmArgs<float>& a, c
                                                     long long gtid, long long gth, double* sums) {
   const bool u16 = (reinterpret_cast<uintptr_t>(S.u) & 15u) == 0;
   AccG sy, s1, s2;
-  quad_loop(S.qidx, S.qk, nq, gtid, gth, [&](long long p4, int k0, bool, long long pn4) {
+  quad_loop(S.qidx, S.qk, nq, gtid, gth, [&](long long p4, int k0, bool full, long long pn4) {
     if (pn4 >= 0 && (pn4 & 15) == 0) {  // a lane per 128-byte line of the FP64 fields
       prefetch_l2(S.u + pn4);
       prefetch_l2(S.Fprev + pn4);
     }
-    const unsigned kw = __ldg(reinterpret_cast<const unsigned*>(S.kind + p4));
+    const unsigned kw = full ? QK_FULL_KIND : __ldg(reinterpret_cast<const unsigned*>(S.kind + p4));
     const unsigned fw = __ldcg(reinterpret_cast<const unsigned*>(S.fvalid + p4));
     double u[4], fp[4];
     if (u16) {
