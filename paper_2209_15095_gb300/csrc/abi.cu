@@ -69,7 +69,20 @@ struct etd_ctx {
   int last_nspecies = 0;
   int last_species0 = 0;
   unsigned long long wait_ns = 0;  // host copy of the device-wait limit (0: default)
+  // FP32 contexts: each species' computational-point count, copied back
+  // after every domain set-up without a wait (pinned, an event per copy);
+  // the Krylov launch takes the 768-thread kernel when a species with the
+  // latest count that has arrived runs on the 4-node groups
+  int* ncomp_host = nullptr;
+  cudaEvent_t ncomp_ev[2] = {nullptr, nullptr};
+  bool ncomp_pending[2] = {false, false};
+  int ncomp_known[2] = {-1, -1};
   std::string err;
+  ~etd_ctx() {
+    for (cudaEvent_t ev : ncomp_ev)
+      if (ev) cudaEventDestroy(ev);
+    if (ncomp_host) cudaFreeHost(ncomp_host);
+  }
 };
 
 namespace {
@@ -391,7 +404,21 @@ etd_status run_phipm(etd_ctx* c, int mode, double dt, double* const* u, int spec
     e = cudaMemsetAsync(c->stats, 0, sizeof(StatsDev), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "stats reset");
   }
-  e = launch_phipm<T>(a, c->nblocks, c->stream);
+  // the 768-thread FP32 kernel when a species of this launch takes the
+  // 4-node groups (its latest known point count; only the speed depends on it)
+  bool wide = false;
+  if (sizeof(T) == 4 && c->ncomp_host) {
+    const int s0 = all ? 0 : species, s1 = all ? a.nspecies : species + 1;
+    for (int s = s0; s < s1; ++s) {
+      if (c->ncomp_pending[s] && cudaEventQuery(c->ncomp_ev[s]) == cudaSuccess) {
+        c->ncomp_known[s] = c->ncomp_host[s];
+        c->ncomp_pending[s] = false;
+      }
+      wide = wide || (c->ncomp_known[s] >= QUAD_MIN_POINTS && c->sp[s].beta_field == nullptr &&
+                      c->g.n[c->g.ndim - 1] % 4 == 0);
+    }
+  }
+  e = launch_phipm<T>(a, c->nblocks, c->stream, wide);
   if (e != cudaSuccess) return cuda_fail(c, e, "phipm launch");
   c->last_nspecies = a.nspecies;
   c->last_species0 = all ? 0 : species;
@@ -488,6 +515,14 @@ etd_status etd_create(const etd_grid* grid, const etd_params* params, void* work
     delete c;
     return ETD_ERR_CUDA;
   }
+  if (c->fp32) {
+    bool ok = cudaMallocHost(&c->ncomp_host, 2 * sizeof(int)) == cudaSuccess;
+    for (int s = 0; s < 2 && ok; ++s) ok = cudaEventCreateWithFlags(&c->ncomp_ev[s], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      delete c;
+      return ETD_ERR_CUDA;
+    }
+  }
   *out = c;
   return ETD_OK;
 }
@@ -548,6 +583,12 @@ etd_status etd_init_domain(etd_ctx* c, int species, const double* phi, const dou
   if (e != cudaSuccess) return cuda_fail(c, e, "init_domain group list reset");
   e = launch_init_domain(ca, ma, c->tile_count, b.ncomp, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "init_domain launch");
+  if (c->ncomp_host) {
+    e = cudaMemcpyAsync(c->ncomp_host + species, b.ncomp, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ncomp_ev[species], c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "point count copy");
+    c->ncomp_pending[species] = true;
+  }
   b.ready = true;
   return ETD_OK;
 }

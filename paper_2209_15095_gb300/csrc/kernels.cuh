@@ -157,7 +157,11 @@ struct PhipmArgs {
 };
 
 template <typename T>
-cudaError_t launch_phipm(const PhipmArgs<T>& a, int nblocks, cudaStream_t stream);
+cudaError_t launch_phipm(const PhipmArgs<T>& a, int nblocks, cudaStream_t stream, bool wide = false);
+// FP32 problems from this many computational points run the Krylov basis on
+// the 4-node groups (with a constant beta and the last axis a multiple of 4);
+// `wide` picks the 768-thread FP32 kernel for them
+constexpr int QUAD_MIN_POINTS = 1 << 18;
 int phipm_max_blocks(int ndim, bool fp32);
 // The Krylov kernels of one precision and CTA size (krylov_impl.cuh):
 // fn[ndim - 2][adjoint instantiation], threads per CTA, the adjoint

@@ -1,6 +1,7 @@
 // Launch of the adaptive Krylov kernel (krylov_impl.cuh): picks the
-// instantiation by precision and grid size, loads the unit's constants on
-// first use, and runs it as a cooperative launch (one CTA per SM).
+// instantiation by precision and, for FP32, by `wide` (the caller's choice of
+// the 768-thread kernel for problems on the 4-node groups), loads the unit's
+// constants on first use, and runs it as a cooperative launch (one CTA per SM).
 #include "kernels.cuh"
 
 namespace etd {
@@ -10,9 +11,6 @@ PhipmKernels phipm_kernels_f32();
 PhipmKernels phipm_kernels_f32w();
 
 namespace {
-// FP32 grids from this many nodes (256^3) take the 768-thread kernel
-constexpr long long WIDE_MIN_NODES = 1ll << 24;
-
 struct Variant {
   PhipmKernels k;
   bool loaded = false;
@@ -31,15 +29,15 @@ Variant& f32w() {
 }
 
 template <typename T>
-Variant& variant(long long gsize) {
+Variant& variant(bool wide) {
   if (sizeof(T) == 8) return f64();
-  return gsize >= WIDE_MIN_NODES ? f32w() : f32();
+  return wide ? f32w() : f32();
 }
 }  // namespace
 
 template <typename T>
-cudaError_t launch_phipm(const PhipmArgs<T>& a, int nblocks, cudaStream_t stream) {
-  Variant& v = variant<T>(a.g.size);
+cudaError_t launch_phipm(const PhipmArgs<T>& a, int nblocks, cudaStream_t stream, bool wide) {
+  Variant& v = variant<T>(wide);
   if (!v.loaded) {
     cudaError_t e = v.k.load_consts();
     if (e != cudaSuccess) return e;
@@ -81,7 +79,7 @@ int phipm_max_blocks(int ndim, bool fp32) {
   return per * sms;
 }
 
-template cudaError_t launch_phipm<double>(const PhipmArgs<double>&, int, cudaStream_t);
-template cudaError_t launch_phipm<float>(const PhipmArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_phipm<double>(const PhipmArgs<double>&, int, cudaStream_t, bool);
+template cudaError_t launch_phipm<float>(const PhipmArgs<float>&, int, cudaStream_t, bool);
 
 }  // namespace etd

@@ -1,6 +1,6 @@
 // Instantiation of the Krylov kernel with FP32 vectors and 512 threads per
-// CTA (128 registers per thread): the grids below WIDE_MIN_NODES, whose
-// per-point paths are latency-bound and would spill at fewer registers.
+// CTA (128 registers per thread): the problems off the 4-node groups,
+// whose per-point paths are latency-bound and would spill at fewer registers.
 #define ETD_RED_MAX_NT 512
 #include "krylov_impl.cuh"
 

@@ -52,7 +52,7 @@ constexpr int MAX_SUBSTEPS = 20000;  // bounded work per call
 // those sizes, for one more barrier and 2 more vector accesses per point.
 // Each thread then keeps SPLIT_U points in flight.
 template <typename T>
-constexpr int SPLIT_MIN = sizeof(T) == 8 ? (1 << 17) : (1 << 18);
+constexpr int SPLIT_MIN = sizeof(T) == 8 ? (1 << 17) : QUAD_MIN_POINTS;
 template <typename T>
 constexpr int SPLIT_U = sizeof(T) == 8 ? 2 : 4;
 template <typename T>
