@@ -74,6 +74,35 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate_ranks(t_local, cells_local, device):
+    """Whole-job figures of N independent replicas: the timed seconds are the
+    maximum over the ranks (the slowest replica sets the job's time) and the
+    computational-point updates their sum; returns (cells, seconds).  With
+    one process, the local figures."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(cells_local), float(t_local)
+    tt = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    cc = torch.tensor([float(cells_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(cc, op=dist.ReduceOp.SUM)
+    return cc.item(), tt.item()
+
+
+def sync_ranks(device):
+    """Device synchronisation, then a barrier across the replicas (if any):
+    brackets the timed steps so that every rank starts and ends them
+    together."""
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.synchronize(device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
 def workload(name):
     from paper_2209_15095_gb300 import inputs
 
@@ -320,6 +349,7 @@ def main():
                 one_step(ctx, phis, us, k)
                 k += 1
             ctx.sync()
+            sync_ranks(dev)
             times, parts, cells, iters, subs, ls_flops = [], [], 0, 0, 0, 0.0
             nre = 0
             for _ in range(args.steps):
@@ -336,6 +366,7 @@ def main():
                 iters += sum(s_["krylov_iters"] for s_ in st)
                 subs += sum(s_["substeps"] for s_ in st)
         ctx.sync()
+        sync_ranks(dev)
         return {"ctx": ctx, "phis": phis, "us": us, "times": times, "parts": parts, "cells": cells,
                 "iters": iters, "substeps": subs, "k": k, "ls_flops": ls_flops, "reinit_steps": nre}
 
@@ -367,17 +398,8 @@ def main():
         stress = run_stress(etd, stream, dev, args.stress_steps, args.stress_n, args.stress_precision)
     clk = clocks.stop()
 
-    t64 = sum(r64["times"]) / 1e3
-    value = r64["cells"] / t64 / 1e6
-    if ws > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([t64], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        cc = torch.tensor([float(r64["cells"])], device=dev)
-        dist.all_reduce(cc, op=dist.ReduceOp.SUM)
-        value = cc.item() / tt.item() / 1e6
-        t64 = tt.item()
+    cells_all, t64 = aggregate_ranks(sum(r64["times"]) / 1e3, r64["cells"], dev)
+    value = cells_all / t64 / 1e6
     if rank != 0:
         return
     nparts = np.array(r64["parts"])
