@@ -198,7 +198,7 @@ def run_reference(args):
               % (cores, args.workload, res["warm"], res["steps"]))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": res["steps"], "warmup": res["warm"],
+        "steps": min(res["per_replica_steps"]), "warmup": res["warm"],
         "ms_per_step": 1e3 * res["seconds"] / max(1, min(res["per_replica_steps"])),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload},
