@@ -83,7 +83,8 @@ struct SpeciesDev {
   T* V2c;
   T* V3c;   // v_3 (phi_3 combinations only)
   T* W2g;   // full grid: w_2 (phi_3 combinations only; zero off the computational set)
-  T* Z[2];  // full grid: A V_j of the last two basis vectors (unnormalised)
+  T* Z[2];  // full grid: A V_j of the last two basis vectors (unnormalised);
+            // on the 4-node groups u_j = A v_j - beta_j v_{j-1} (quad_pass_1)
   // stage fields a, b, c of the Runge-Kutta schemes (full grid, FP64; only
   // the computational points are written and read)
   double* stg[3];

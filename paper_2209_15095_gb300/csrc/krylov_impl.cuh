@@ -32,8 +32,9 @@
 //
 // This header holds the kernel; krylov_f64.cu, krylov_f32.cu and
 // krylov_f32w.cu instantiate it (FP64 with 512 threads per CTA; FP32 with
-// 512, and with 768 for large grids) and krylov.cu launches it.  A unit may
-// define ETD_RED_MAX_NT (the block-reduction width) before including it.
+// 512, and with 768 for problems on the 4-node groups) and krylov.cu
+// launches it.  A unit may define ETD_RED_MAX_NT (the block-reduction width)
+// before including it.
 #pragma once
 #include "common.cuh"
 #include "kernels.cuh"
@@ -50,7 +51,8 @@ constexpr int MAX_SUBSTEPS = 20000;  // bounded work per call
 // instead of one pass that rebuilds w_j at all 2N + 1 stencil points: about
 // 15 instead of 30 FP64 instructions per point, which is what bounds FP64 at
 // those sizes, for one more barrier and 2 more vector accesses per point.
-// Each thread then keeps SPLIT_U points in flight.
+// Each thread then keeps SPLIT_U points in flight.  FP32 problems of that
+// size on the 4-node groups take one pass per vector instead (quad_pass_1).
 template <typename T>
 constexpr int SPLIT_MIN = sizeof(T) == 8 ? (1 << 17) : QUAD_MIN_POINTS;
 template <typename T>
