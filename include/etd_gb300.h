@@ -74,6 +74,10 @@ enum {
  *               dot products / norms and the basis combination accumulated
  *               error-free in FP32 pairs and summed across the grid in FP64;
  *               H, the small exponential, the controller, u and F stay FP64.
+ *               From 2^18 computational points (constant beta, last axis a
+ *               multiple of 4) the basis is built by the one-pass form of the
+ *               symmetric Lanczos recurrence (C is symmetric), its sums per
+ *               group of 4 nodes in FP32 and accumulated error-free.
  *               In the level set, phi, u and the RK updates stay FP64; the
  *               HJ-WENO5/Godunov arithmetic is FP32 for the advection and,
  *               beyond h from the interface, for the reinitialisation; the
