@@ -508,15 +508,16 @@ __device__ __forceinline__ void quad_loop(const int* __restrict__ qidx, const in
 // AccG sums), from which alpha_j and beta_{j+1} follow without another
 // pass.  Two vectors are read (each with its stencil) and two written.  A
 // V_j value is formed by the same two roundings wherever it is formed, so
-// Z_j is A applied to the stored V_j.  Out of line: the Lanczos loop around
-// the call is near the register limit.
+// Z_j is A applied to the stored V_j.  Inlined into the kernel: out of line
+// its 20-odd register arguments and the saves around the call cost the
+// 768-thread kernel 8% per pass at 512^3 (4.93 against 5.34 ms for 19 passes).
 template <int N>
-__device__ __noinline__ QuadSums quad_pass_1(const float* __restrict__ Wp, const float* __restrict__ Vp,
-                                             float* __restrict__ Vj, float* __restrict__ Wn, float c1, float c2,
-                                             float c3, const uint8_t* __restrict__ kind,
-                                             const float* __restrict__ diagf, const int* __restrict__ qidx,
-                                             const int* __restrict__ qk, int nq, const GridDev& g, float cfac,
-                                             float bc, float dint, long long gtid, long long gth) {
+__device__ __forceinline__ QuadSums quad_pass_1(const float* __restrict__ Wp, const float* __restrict__ Vp,
+                                                float* __restrict__ Vj, float* __restrict__ Wn, float c1, float c2,
+                                                float c3, const uint8_t* __restrict__ kind,
+                                                const float* __restrict__ diagf, const int* __restrict__ qidx,
+                                                const int* __restrict__ qk, int nq, const GridDev& g, float cfac,
+                                                float bc, float dint, long long gtid, long long gth) {
   constexpr int U = QP_U;
   long long st[N > 1 ? N - 1 : 1];
 #pragma unroll
@@ -624,7 +625,8 @@ __device__ __noinline__ QuadSums quad_pass_1(const float* __restrict__ Wp, const
 // out = A X + a1 + c2 a2 + c3 a3 on groups of 4 nodes (the first NT terms;
 // a1, a2, a3 compact, at the group's list indices), 0 at the group's other
 // nodes: the w_j passes and P_0.  With SUMS: |X|^2, <out, X> and |out|^2
-// (this thread's AccG sums).  Out of line, as quad_pass_1.
+// (this thread's AccG sums).  Out of line: inlined, the three w passes took
+// twice as long at 512^3 (register pressure in the kernel).
 template <int N, int NT, bool SUMS>
 __device__ __noinline__ QuadSums quad_stencil(const float* __restrict__ X, float* __restrict__ out,
                                               const float* __restrict__ a1, const float* __restrict__ a2,
@@ -694,20 +696,22 @@ __device__ __noinline__ QuadSums quad_stencil(const float* __restrict__ X, float
 // loop (the same Dot2 basis sum in the same order, so the same bits), with
 // 16-byte loads of the basis vectors, ten in flight: the basis size is a
 // multiple of 5 but for m_max or a breakdown (the error check runs every 5
-// vectors).  Measured per launch at 256^3 / 512^3 (10 / 20 vectors): 5 in
-// flight 1.378 / 14.11 ms, 8 1.376 / 14.01, 10 1.342 / 13.51, 16 1.390 / 13.72.  Writes y (compact,
-// FP64) and its FP32 grid copy (0 at the group's other nodes), and, for the
-// last substep, y into ufin at the computational points (the kernel then
-// skips its write-back); returns this thread's sum of the squares of the
-// FP32 copy (the controller's scale).
-static __device__ __noinline__ double quad_combination(const float* __restrict__ chi, const float* __restrict__ clo,
-                                                       int m, double tau, const float* __restrict__ V, long long vs,
-                                                       const float* __restrict__ W1g, const float* __restrict__ W2g,
-                                                       double* __restrict__ Yc, float* __restrict__ Yg,
-                                                       double* __restrict__ ufin, const uint8_t* __restrict__ kind,
-                                                       const int* __restrict__ qidx,
-                                                       const int* __restrict__ qk, int nq, long long gtid,
-                                                       long long gth) {
+// vectors).  Measured per launch with the earlier two-pass kernel at 256^3 /
+// 512^3 (10 / 20 vectors): 5 in flight 1.378 / 14.11 ms, 8 1.376 / 14.01,
+// 10 1.342 / 13.51, 16 1.390 / 13.72.  Writes y (compact, FP64) and its FP32
+// grid copy (0 at the group's other nodes), and, for the last substep, y
+// into ufin at the computational points (the kernel then skips its
+// write-back); returns this thread's sum of the squares of the FP32 copy
+// (the controller's scale).  Inlined into the kernel: 1.59 against 1.80 ms
+// at 512^3 out of line.
+static __device__ __forceinline__ double quad_combination(const float* __restrict__ chi,
+                                                          const float* __restrict__ clo, int m, double tau,
+                                                          const float* __restrict__ V, long long vs,
+                                                          const float* __restrict__ W1g, const float* __restrict__ W2g,
+                                                          double* __restrict__ Yc, float* __restrict__ Yg,
+                                                          double* __restrict__ ufin, const uint8_t* __restrict__ kind,
+                                                          const int* __restrict__ qidx, const int* __restrict__ qk,
+                                                          int nq, long long gtid, long long gth) {
   Acc<float> yn;  // |y|^2 of the FP32 copy: the controller's scale only
   const double h2 = 0.5 * tau * tau;
   quad_loop(qidx, qk, nq, gtid, gth, [&](long long p4, int k0, bool full, long long pn4) {
