@@ -418,7 +418,13 @@ def main():
         "gpu_launches": args.steps * (2 * nsp + 1),
         "breakdown_ms": {n: float(v) for n, v in zip(names, avg_parts)},
         "krylov": {"iters_per_step": r64["iters"] / args.steps, "substeps_per_step": r64["substeps"] / args.steps,
-                   "ncomp_mean": r64["cells"] / args.steps},
+                   "ncomp_mean": r64["cells"] / args.steps,
+                   # point-iterations of the Krylov basis per second of Krylov launches
+                   "cell_iters_per_s": (r64["cells"] / args.steps) * (r64["iters"] / args.steps)
+                                       / (float(avg_parts[2]) / 1e3)},
+        # the whole grid's nodes per second of the full step (n^N / t)
+        "grid_nodes_per_s": math.prod(w.n) / (t64 / args.steps),
+        "etd_only_ms_per_step": float(avg_parts[2]),
     }
     if e2e is not None:
         out["e2e"] = e2e
