@@ -141,62 +141,97 @@ __device__ __forceinline__ long long nbr(const GridDev& g, long long p, const in
 // of the usual weighted form with eps = 1e-6 (on divided differences), so
 // eps' = 4 eps (times h^2 on undivided ones) gives the same weights; the
 // usual weighted sum of the three candidate stencils is the same number up
-// to rounding.  Shared by the two sides: the second differences, c, the
-// squares (a-b)^2 of common pairs and b - 2c + d (equal on both sides).
-// With W = w0 + w1 + w2 (unnormalised): Phi = (2 w0 (a-b-(b-c)) +
-// (w2 - W/2)(b - 2c + d)) / (6 W).  In FP64 the two sides share one
-// division.
+// to rounding.
+//
+// The terms are kept scaled by 12, which leaves no constant factor to
+// multiply by: with d_k = (eps' + I_k)^2, A = d1 d2, B = d0 d2, C = d0 d1,
+// W = A + 6B + 3C (the sum of the alphas times d0 d1 d2) and
+// V = 3C - A - 6B (= 4 (w2 - 1/2) W in alpha units),
+//   12 Phi = 4 (A X + V Y / 4) / W,   X = (a-b) - (b-c),  Y = b - 2c + d,
+//   12 c   = 7 (q2 + q3) - (q1 + q4).
+// The two sides share the differences, 12 c, the squares (a-b)^2 of common
+// pairs and Y (the same on both).
 template <typename C>
-__device__ __forceinline__ void weno5_pair(const C* q, C epsw, C& dm, C& dp) {
+struct Weno5Terms {
+  C cen;     // 12 c
+  C num[2];  // A X + V Y / 4 of the minus and plus sides
+  C W[2];
+};
+
+template <typename C>
+__device__ __forceinline__ Weno5Terms<C> weno5_terms(const C* q, C epsw) {
   constexpr C k13 = C(13.0 / 3.0);
   const C e0 = q[1] - q[0], e1 = q[2] - q[1], e2 = q[3] - q[2], e3 = q[4] - q[3], e4 = q[5] - q[4];
-  const C cen = (C(7) * (q[2] + q[3]) - (q[1] + q[4])) * C(1.0 / 12.0);
-  // minus side (a,b,c,d) = (e0,e1,e2,e3): t = (ta, tb, tc);
-  // plus side (e4,e3,e2,e1): t = (td, -tc, -tb)
+  Weno5Terms<C> t;
+  t.cen = fma(C(7), q[2] + q[3], -(q[1] + q[4]));
+  // minus side (a,b,c,d) = (e0,e1,e2,e3): third differences (ta, tb, tc);
+  // plus side (e4,e3,e2,e1): (td, -tc, -tb)
   const C ta = e0 - e1, tb = e1 - e2, tc = e2 - e3, td = e4 - e3;
   const C sa = ta * ta, sb = tb * tb, sc = tc * tc, sd = td * td;
-  const C e2x3 = C(3) * e2;
-  const C um0 = e0 - C(3) * e1, um1 = e1 + e2, um2 = e2x3 - e3;
-  const C up0 = e4 - C(3) * e3, up1 = e3 + e2, up2 = e2x3 - e1;
-  const C Y = tb - tc;
-  C num[2], den[2];
+  const C um0 = fma(C(-3), e1, e0), um1 = e1 + e2, um2 = fma(C(3), e2, -e3);
+  const C up0 = fma(C(-3), e3, e4), up1 = e3 + e2, up2 = fma(C(3), e2, -e1);
+  const C Y4 = C(0.25) * (tb - tc);
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
-    const C i0 = side == 0 ? k13 * sa + um0 * um0 : k13 * sd + up0 * up0;
-    const C i1 = side == 0 ? k13 * sb + um1 * um1 : k13 * sc + up1 * up1;
-    const C i2 = side == 0 ? k13 * sc + um2 * um2 : k13 * sb + up2 * up2;
+    // eps' + I_k
+    const C s0 = side == 0 ? fma(k13, sa, fma(um0, um0, epsw)) : fma(k13, sd, fma(up0, up0, epsw));
+    const C s1 = side == 0 ? fma(k13, sb, fma(um1, um1, epsw)) : fma(k13, sc, fma(up1, up1, epsw));
+    const C s2 = side == 0 ? fma(k13, sc, fma(um2, um2, epsw)) : fma(k13, sb, fma(up2, up2, epsw));
     const C X = side == 0 ? ta - tb : td + tc;
-    const C s0 = epsw + i0, s1 = epsw + i1, s2 = epsw + i2;
     const C d0 = s0 * s0, d1 = s1 * s1, d2 = s2 * s2;
-    const C w0 = d1 * d2, w1 = C(6) * (d0 * d2), w2 = C(3) * (d0 * d1);
-    const C W = w0 + w1 + w2;
-    den[side] = C(6) * W;
-    num[side] = w0 * (X + X) + (w2 - C(0.5) * W) * Y;
+    const C A = d1 * d2, B = d0 * d2, Cc = d0 * d1;
+    const C AB = fma(C(6), B, A);
+    t.W[side] = fma(C(3), Cc, AB);
+    t.num[side] = fma(A, X, fma(C(3), Cc, -AB) * Y4);
   }
-  if constexpr (sizeof(C) == 8) {
-    // den >= 60 eps'^4 (> 1e-60 for h > 1e-6) and for |q| < 1e18 the
-    // product stays finite: it neither underflows nor overflows in FP64
-    const C r = C(1) / (den[0] * den[1]);
-    dm = cen - num[0] * (den[1] * r);
-    dp = cen + num[1] * (den[0] * r);
-  } else {
-    dm = cen - num[0] / den[0];
-    dp = cen + num[1] / den[1];
-  }
+  return t;
 }
 
-// One axis of the Godunov |grad phi| (godunov, below): max(d-, -d+, 0) (outward) or its
-// mirror image, from the WENO5 pair on the seven values along axis d.
-// inv_h = 1/h; epsw the WENO epsilon of the arithmetic (see godunov).
+// max(a, b, 0) of doubles on the integer pipe: as signed 64-bit integers,
+// the bit patterns of non-negative doubles order like their values and those
+// of negative ones lie below that of +0.
+__device__ __forceinline__ double max0(double a, double b) {
+  const long long m = max(__double_as_longlong(a), __double_as_longlong(b));
+  return __longlong_as_double(max(m, 0LL));
+}
+__device__ __forceinline__ float max0(float a, float b) { return fmaxf(fmaxf(a, b), 0.f); }
+
+// 12 max(d-, -d+, 0) (outward) or its mirror image, with r_s = 4 / W_s.
+// outward: max(max(d-, 0)^2, min(d+, 0)^2) = max(d-, -d+, 0)^2 (a square is
+// monotone on the non-negatives); inward: the mirror image.  Exact sign
+// flips and no branch, so that no work of the other case is issued
+// predicated off.
+template <typename C>
+__device__ __forceinline__ C weno5_upwind(const Weno5Terms<C>& t, C r0, C r1, bool positive) {
+  const C dm = fma(-t.num[0], r0, t.cen), dp = fma(t.num[1], r1, t.cen);
+  return max0(positive ? dm : -dm, positive ? -dp : dp);
+}
+
+// Constants of the Godunov evaluations of one grid, computed once.
+struct WenoK {
+  double epsw;     // eps' on undivided FP64 differences: 4 eps h^2
+  double inv_h;    // 1 / h
+  double inv_h12;  // 1 / (12 h): the scale of the FP64 result
+};
+
+__device__ __forceinline__ WenoK weno_k(double h) {
+  WenoK k;
+  k.epsw = 4.0 * WENO_EPS * h * h;
+  k.inv_h = 1.0 / h;
+  k.inv_h12 = 1.0 / (12.0 * h);
+  return k;
+}
+
+// The seven values along axis d as six differences: FP64 undivided, or
+// FP32-mixed (values rounded to FP32, differences divided by h in FP32; an
+// eps' scaled by h^2 would leave the FP32 normal range).
 template <typename C, int N>
-__device__ __forceinline__ C godunov_mx(const GridDev& g, const double* __restrict__ src, long long p, const int* ix,
-                                        int d, bool positive, double inv_h, C epsw) {
-  constexpr bool RAW = sizeof(C) == 8;
+__device__ __forceinline__ void axis_diffs(const GridDev& g, const double* __restrict__ src, long long p, const int* ix,
+                                           int d, double inv_h, C* q) {
   double f[7];
 #pragma unroll
   for (int k = -3; k <= 3; ++k) f[k + 3] = __ldcg(src + nbr(g, p, ix, d, k));
-  C q[6];
-  if constexpr (RAW) {
+  if constexpr (sizeof(C) == 8) {
 #pragma unroll
     for (int k = -2; k <= 3; ++k) q[k + 2] = f[k + 3] - f[k + 2];
   } else {
@@ -207,34 +242,94 @@ __device__ __forceinline__ C godunov_mx(const GridDev& g, const double* __restri
 #pragma unroll
     for (int k = -2; k <= 3; ++k) q[k + 2] = (fc[k + 3] - fc[k + 2]) * ih;
   }
-  C dm, dp;
-  weno5_pair<C>(q, epsw, dm, dp);
-  // outward: max(max(d-, 0)^2, min(d+, 0)^2) = max(d-, -d+, 0)^2 (a square
-  // is monotone on the non-negatives); inward: the mirror image.  Exact
-  // sign flips and no branch, so that no FP64 work of the other case is
-  // issued predicated off.
-  return fmax(fmax(positive ? dm : -dm, positive ? -dp : dp), C(0));
+}
+
+// One axis of the Godunov |grad phi| (godunov, below), scaled by 12: the
+// upwind value from the WENO5 pair on the seven values along axis d.
+template <typename C, int N>
+__device__ __forceinline__ C godunov_mx(const GridDev& g, const double* __restrict__ src, long long p, const int* ix,
+                                        int d, bool positive, const WenoK& k) {
+  C q[6];
+  axis_diffs<C, N>(g, src, p, ix, d, k.inv_h, q);
+  const C epsw = sizeof(C) == 8 ? C(k.epsw) : C(4.0 * WENO_EPS);
+  const Weno5Terms<C> t = weno5_terms<C>(q, epsw);
+  if constexpr (sizeof(C) == 8) {
+    // W_s >= 10 eps'^4 (> 1e-70 for h > 1e-6) and for |q| < 1e18 the
+    // product stays finite: it neither underflows nor overflows in FP64
+    const C r = C(4) / (t.W[0] * t.W[1]);
+    return weno5_upwind<C>(t, t.W[1] * r, t.W[0] * r, positive);
+  } else {
+    return weno5_upwind<C>(t, C(4) / t.W[0], C(4) / t.W[1], positive);
+  }
+}
+
+// 4 / (W0 W1) of every axis.  When each product lies within 2^(+-1000/N)
+// one division serves all axes (prefix and suffix products of the others);
+// otherwise one division per axis.
+template <int N>
+__device__ __forceinline__ void weno5_recips(const Weno5Terms<double>* t, double* r) {
+  constexpr unsigned LIM = 1000 / N;
+  double D[N];
+  bool shared = true;
+#pragma unroll
+  for (int d = 0; d < N; ++d) {
+    D[d] = t[d].W[0] * t[d].W[1];
+    const unsigned e = (unsigned)__double2hiint(D[d]) >> 20;  // biased exponent (D > 0)
+    shared = shared && e - (1023u - LIM) <= 2u * LIM;
+  }
+  if (shared) {
+    double pre[N];
+    pre[0] = 1.0;
+#pragma unroll
+    for (int d = 1; d < N; ++d) pre[d] = pre[d - 1] * D[d - 1];
+    const double rP = 4.0 / (pre[N - 1] * D[N - 1]);
+    double suf = 1.0;
+#pragma unroll
+    for (int d = N - 1; d >= 0; --d) {
+      r[d] = (rP * pre[d]) * suf;
+      suf *= D[d];
+    }
+  } else {
+#pragma unroll
+    for (int d = 0; d < N; ++d) r[d] = 4.0 / D[d];
+  }
 }
 
 // Godunov |grad phi| at node p from array src; positive: outward motion.
-// FP64 (C = double): undivided differences, eps scaled by h^2, one factor
-// 1/h at the end.  FP32-mixed (C = float): the seven values rounded to FP32,
-// differences divided by h in FP32 (an eps scaled by h^2 would leave the
-// FP32 normal range), then WENO5 and Godunov in FP32; no FP64 arithmetic
-// (this GPU issues one FP64 warp instruction per ~20 cycles per SM).
+// FP64 (C = double): undivided differences, eps' scaled by h^2, every axis's
+// terms first so that one division serves the node, one factor 1/(12 h) at
+// the end.  FP32-mixed (C = float): WENO5 and Godunov in FP32, no FP64
+// arithmetic (this GPU issues one FP64 warp instruction per ~80 cycles per
+// SM sub-partition).
 template <typename C, int N>
 __device__ double godunov(const GridDev& g, const double* __restrict__ src, long long p, const int* ix,
-                          bool positive) {
-  constexpr bool RAW = sizeof(C) == 8;
-  const double inv_h = 1.0 / g.h;
-  const C epsw = RAW ? C(4.0 * WENO_EPS * g.h * g.h) : C(4.0 * WENO_EPS);
-  C acc = C(0);
+                          bool positive, const WenoK& k) {
+  if constexpr (sizeof(C) == 8) {
+    Weno5Terms<double> t[N];
 #pragma unroll
-  for (int d = 0; d < N; ++d) {
-    const C mx = godunov_mx<C, N>(g, src, p, ix, d, positive, inv_h, epsw);
-    acc = fma(mx, mx, acc);
+    for (int d = 0; d < N; ++d) {
+      double q[6];
+      axis_diffs<double, N>(g, src, p, ix, d, k.inv_h, q);
+      t[d] = weno5_terms<double>(q, k.epsw);
+    }
+    double r[N];
+    weno5_recips<N>(t, r);
+    double acc = 0.0;
+#pragma unroll
+    for (int d = 0; d < N; ++d) {
+      const double mx = weno5_upwind<double>(t[d], t[d].W[1] * r[d], t[d].W[0] * r[d], positive);
+      acc = fma(mx, mx, acc);
+    }
+    return sqrt(acc) * k.inv_h12;
+  } else {
+    float acc = 0.f;
+#pragma unroll
+    for (int d = 0; d < N; ++d) {
+      const float mx = godunov_mx<float, N>(g, src, p, ix, d, positive, k);
+      acc = fma(mx, mx, acc);
+    }
+    return (double)(sqrtf(acc) * (1.f / 12.f));
   }
-  return RAW ? (double)sqrt(acc) * inv_h : (double)sqrt(acc);
 }
 
 // ------------------------------------------------------------ work lists
@@ -862,28 +957,39 @@ __device__ __forceinline__ void stage_push(const LsArgs& a, int i, bool front) {
   else a.b.slist[a.g.size - 1 - atomicAdd(&a.b.count[2], 1)] = i;
 }
 
-// With SPLIT, the FP64 entries (the front of the stage list) have their N
-// axes evaluated on N lanes each (32 / N entries per warp): the per-axis
-// terms come back by shuffles and are summed in axis order as in godunov,
-// so the result is the same; a warp then issues a third (3D) of the FP64
-// instructions of a warp of whole entries.  This GPU issues about one FP64
-// warp instruction per 80 cycles per SM sub-partition, so a warp of FP64
-// entries sets the stage time on its sub-partition whatever its active lanes:
-// LAx(src, p, ix, i, d) gives the axis term, LFin(i, acc) the update value.
-template <int N, bool SPLIT, typename LFn, typename LAx, typename LFin>
-__device__ bool rk3(const LsArgs& a, LsCtx& c, double dt, bool clamp_last, LFn L, LAx LAxis, LFin LFinal) {
+// How the front entries of the stage list (the FP64 ones) are dealt to warps:
+// a lane per entry, or an axis per lane.
+enum : int { SPLIT_NONE = 0, SPLIT_ALL = 1 };
+
+// One TVD-RK3 step over the stage list.  Front entries go a lane per entry
+// (SPLIT_NONE) or have their N axes evaluated on N lanes each (SPLIT_ALL,
+// 32 / N entries per warp): the per-axis terms come back by shuffles and are
+// summed in axis order as in godunov (which differs only in sharing one
+// division among the axes, i.e. in rounding), and a warp issues a third (3D)
+// of the FP64 instructions of a warp of whole entries.  This GPU issues about
+// one FP64 warp instruction per 80 cycles per SM sub-partition whatever the
+// warp's active lanes, so where few FP64 entries leave at most a warp or two
+// per sub-partition, split warps finish sooner.  Back entries (FP32 ones) go
+// a lane per entry.  L(src, p, ix, i, front) gives the update value of a
+// whole entry, LAx(src, p, ix, i, d) the axis term of a split one and
+// LFin(i, acc) its update value.
+template <int N, typename LFn, typename LAx, typename LFin>
+__device__ bool rk3(const LsArgs& a, LsCtx& c, double dt, bool clamp_last, int split, LFn L, LAx LAxis,
+                    LFin LFinal) {
   const GridDev& g = a.g;
   const int nf = __ldcg(a.b.count + 1), nb = __ldcg(a.b.count + 2);
   const double G = BAND * g.h;
   // 32-entry chunks dealt round-robin over the CTAs: every SM gets its share
-  // of both kinds while a warp reads 32 consecutive entries
+  // of each kind while a warp reads 32 consecutive entries.  Chunk order:
+  // whole front, split front, back.
   const int lane = threadIdx.x & 31;
   const long long warp0 = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5);
   const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
-  constexpr int NPW = 32 / N;  // split FP64 entries per warp
-  const long long cf = SPLIT ? ((long long)nf + NPW - 1) / NPW : 0;
-  const long long nfe = SPLIT ? nf : 0;
-  const long long nchunk = cf + ((long long)nf + nb - nfe + 31) / 32;
+  constexpr int NPW = 32 / N;  // split entries per warp
+  const long long nwf = split == SPLIT_NONE ? nf : 0;
+  const long long cw = (nwf + 31) / 32;
+  const long long cf = ((long long)nf - nwf + NPW - 1) / NPW;
+  const long long nchunk = cw + cf + ((long long)nb + 31) / 32;
   for (int stage = 0; stage < 3; ++stage) {
     const double* src = stage == 0 ? a.phi : (stage == 1 ? a.b.p1 : a.b.p2);
     auto update = [&](long long p, double Lv) {
@@ -893,15 +999,15 @@ __device__ bool rk3(const LsArgs& a, LsCtx& c, double dt, bool clamp_last, LFn L
       } else if (stage == 1) {
         a.b.p2[p] = 0.75 * ph + 0.25 * (__ldcg(a.b.p1 + p) + dt * Lv);
       } else {
-        double v = ph / 3.0 + 2.0 / 3.0 * (__ldcg(a.b.p2 + p) + dt * Lv);
+        double v = fma(1.0 / 3.0, ph, 2.0 / 3.0 * (__ldcg(a.b.p2 + p) + dt * Lv));
         if (clamp_last) v = fmin(fmax(v, -G), G);
         a.phi[p] = v;
       }
     };
     for (long long chunk = warp0; chunk < nchunk; chunk += wstride) {
-      if (SPLIT && chunk < cf) {
+      if (chunk >= cw && chunk < cw + cf) {
         const int sub = lane / N, d = lane - sub * N;
-        const long long j = chunk * NPW + sub;
+        const long long j = nwf + (chunk - cw) * NPW + sub;
         const bool valid = sub < NPW && j < nf;
         long long i = 0, p = 0;
         double mx = 0.0;
@@ -921,10 +1027,10 @@ __device__ bool rk3(const LsArgs& a, LsCtx& c, double dt, bool clamp_last, LFn L
         if (valid && d == 0) update(p, LFinal(i, acc));
         continue;
       }
-      const long long j = nfe + 32 * (chunk - cf) + lane;
-      if (j >= (long long)nf + nb) continue;
-      const bool front = j < nf;
-      const long long i = __ldcg(a.b.slist + (front ? j : g.size - 1 - (j - nf)));
+      const bool front = chunk < cw;
+      const long long j = front ? 32 * chunk + lane : 32 * (chunk - cw - cf) + lane;
+      if (j >= (front ? nwf : (long long)nb)) continue;
+      const long long i = __ldcg(a.b.slist + (front ? j : g.size - 1 - j));
       const long long p = __ldcg(a.b.list + i);
       int ix[N];
       unpack<N>(a.b.lcoord[i], ix);
@@ -975,25 +1081,24 @@ __device__ bool reinitialise(const LsArgs& a, LsCtx& c) {
   if (!grid_barrier(a.st, c.bar, 40)) return false;
   const int K = (int)ceil(12.0 * sqrt((double)N));
   const double dtau = 0.5 * h / sqrt((double)N);
+  const WenoK wk = weno_k(h);
   auto L = [&](const double* src, long long p, const int* ix, long long i, bool fp64) {
     const double S = __ldcg(a.b.S0 + i);
-    const double gr = fp64 ? godunov<double, N>(g, src, p, ix, S > 0.0) : godunov<float, N>(g, src, p, ix, S > 0.0);
-    return -S * (gr - 1.0);
+    const double gr =
+        fp64 ? godunov<double, N>(g, src, p, ix, S > 0.0, wk) : godunov<float, N>(g, src, p, ix, S > 0.0, wk);
+    return fma(-S, gr, S);  // -S (|grad phi| - 1)
   };
-  // the FP64 entries of the mixed path, an axis per lane (see rk3)
-  const double inv_h = 1.0 / h;
-  const double epsw = 4.0 * WENO_EPS * h * h;
+  // FP64 entries an axis per lane (see rk3)
   auto LAx = [&](const double* src, long long p, const int* ix, long long i, int d) {
-    return godunov_mx<double, N>(g, src, p, ix, d, __ldcg(a.b.S0 + i) > 0.0, inv_h, epsw);
+    return godunov_mx<double, N>(g, src, p, ix, d, __ldcg(a.b.S0 + i) > 0.0, wk);
   };
   auto LFin = [&](long long i, double acc) {
     const double S = __ldcg(a.b.S0 + i);
-    return -S * (sqrt(acc) * inv_h - 1.0);
+    return fma(-S, sqrt(acc) * wk.inv_h12, S);
   };
+  const int split = a.mixed ? SPLIT_ALL : SPLIT_NONE;
   for (int it = 0; it < K; ++it) {
-    if (!(a.mixed ? rk3<N, true>(a, c, dtau, it == K - 1, L, LAx, LFin)
-                  : rk3<N, false>(a, c, dtau, it == K - 1, L, LAx, LFin)))
-      return false;
+    if (!rk3<N>(a, c, dtau, it == K - 1, split, L, LAx, LFin)) return false;
   }
   return true;
 }
@@ -1273,14 +1378,15 @@ __global__ void __launch_bounds__(LS_NT, 1) levelset_kernel(const LsArgs a) {
       a.b.info[2] = nsub;
     }
     const double dts = a.dt / nsub;
+    const WenoK wk = weno_k(h);
     auto L = [&](const double* s, long long p, const int* ix, long long i, bool) {
-      const double gr = a.mixed ? godunov<float, N>(g, s, p, ix, true) : godunov<double, N>(g, s, p, ix, true);
+      const double gr = a.mixed ? godunov<float, N>(g, s, p, ix, true, wk) : godunov<double, N>(g, s, p, ix, true, wk);
       return -__ldcg(a.b.V + i) * gr;
     };
     for (int sub = 0; sub < nsub; ++sub) {
       auto LAx = [&](const double*, long long, const int*, long long, int) { return 0.0; };
       auto LFin = [&](long long, double) { return 0.0; };
-      if (!rk3<N, false>(a, c, dts, sub == nsub - 1, L, LAx, LFin)) return;
+      if (!rk3<N>(a, c, dts, sub == nsub - 1, SPLIT_NONE, L, LAx, LFin)) return;
     }
   }
   if (a.reinit) reinitialise<N>(a, c);
