@@ -333,6 +333,34 @@ def test_levelset_step_matches_nd(lib, ndim):
     assert np.max(np.abs(du.cpu().numpy() - ue_o)) <= 1e-10 * np.max(np.abs(ue_o))
 
 
+@pytest.mark.parametrize("kind", ["plane", "ellipsoid"])
+def test_reinit_fine_spacing(lib, kind):
+    """Reinitialisation (Sec. 4.3) on a 3D grid with h ~ 1e-4.  On flat data
+    the WENO5 weight sums W are ~10 eps'^4 with eps' = 4e-6 h^2, so their
+    products per axis fall below 2^-333 and the kernel divides once per axis
+    instead of once per node (the plane, |grad phi| = 1.3, is flat wherever it
+    is not clamped); the ellipsoid's curved stencils keep the one shared
+    division.  Both must match the oracle at 1e-10 h."""
+    n, box = 24, 1.2e-3
+    g = Grid((n,) * 3, (-box,) * 3, (box,) * 3)
+    x = g.coords()
+    if kind == "plane":
+        nv = np.array([0.48, 0.6, 0.64])
+        nv /= np.linalg.norm(nv)
+        ph0 = 1.3 * (nv[0] * x[0] + nv[1] * x[1] + nv[2] * x[2] - 0.1 * box)
+    else:
+        a = (0.7, 0.55, 0.5)
+        ph0 = box * (np.sqrt(sum((x[d] / (a[d] * box)) ** 2 for d in range(3))) - 1.0)
+    ph = levelset.clamp(ph0, g.h)
+    ref = levelset.reinit(ph, g.h)
+    assert np.max(np.abs(ref - ph)) > 1e-3 * g.h  # the reinitialisation moves phi
+    ctx = _ctx(lib, g)
+    dph = _dev(ph)
+    ctx.levelset_prepare(dph, True)
+    ctx.sync()
+    assert np.max(np.abs(dph.cpu().numpy() - ref)) <= 1e-10 * g.h
+
+
 def test_free_boundary_disc_multistep(lib):
     from oracle.freeboundary import FreeBoundary, Species
     from paper_2209_15095_gb300 import inputs
