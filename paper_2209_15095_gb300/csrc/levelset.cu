@@ -146,7 +146,7 @@ __device__ __forceinline__ long long nbr(const GridDev& g, long long p, const in
 // The terms are kept scaled by 12, which leaves no constant factor to
 // multiply by: with d_k = (eps' + I_k)^2, A = d1 d2, B = d0 d2, C = d0 d1,
 // W = A + 6B + 3C (the sum of the alphas times d0 d1 d2) and
-// V = 3C - A - 6B (= 4 (w2 - 1/2) W in alpha units),
+// V = 3C - A - 6B (= 2 W (w2 - 1/2) with w2 the normalised weight),
 //   12 Phi = 4 (A X + V Y / 4) / W,   X = (a-b) - (b-c),  Y = b - 2c + d,
 //   12 c   = 7 (q2 + q3) - (q1 + q4).
 // The two sides share the differences, 12 c, the squares (a-b)^2 of common
